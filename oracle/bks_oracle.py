@@ -1,0 +1,639 @@
+"""Plain FP64 numpy oracle of the BKS / HOOI hot path (test infrastructure).
+
+Only tests, the smoke check and the benchmark's CPU-baseline legs use this
+module.  Every function cites the passage of the paper it follows.
+
+Pins (what fixes each function other than itself) live in
+``tests/test_oracle_*.py``:
+
+* ``symmetrise``          -- dict model of the mirror/sum rule, bitwise.
+* ``mode1/mode3/core``    -- brute-force dense ``einsum`` on tiny tensors.
+* ``orth_block``          -- orthonormality, reconstruction B = Q H + Qn R,
+                             exact rank drops on planted dependent columns.
+* ``schedule_counts``     -- every k1/k3 printed in Tables 1-3 and in the
+                             figure captions of Section 6.2 (three printed
+                             values disagree with the rule; see the tests).
+* ``gradient_prop2``      -- equals ``gradient_global`` (two derivations).
+* ``inner_solve``/``bks``/``hooi`` -- closed forms n=1 (Eckart-Young) and
+                             rank-one slices, exact recovery of a planted
+                             multilinear-rank tensor, monotone ||F||, and
+                             BKS/HOOI agreement.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "SymTensor", "symmetrise", "mode1", "mode3", "core", "core_dense_check",
+    "orth_block", "schedule_counts", "expand", "gradient_prop2",
+    "gradient_global", "inner_solve", "bks", "hooi", "sin_theta_max",
+    "top_left_singular", "unfold1", "unfold3", "s_values", "tri_index",
+    "BKSResult",
+]
+
+
+# ----------------------------------------------------------------------------
+# Storage (Definition 2.1: A(i,j,k) = A(j,i,k))
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class SymTensor:
+    """Canonical stored form: entries sorted by (i, k, j), duplicates summed,
+    both halves present.  ``v`` keeps the input value dtype (the sums are
+    taken in that dtype); arithmetic below promotes to float64."""
+    m: int
+    n: int
+    i: np.ndarray
+    j: np.ndarray
+    k: np.ndarray
+    v: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.i.shape[0])
+
+    def vf(self) -> np.ndarray:
+        return self.v.astype(np.float64)
+
+    def fro2(self) -> float:
+        x = self.vf()
+        return float(np.dot(x, x))
+
+    def dense(self) -> np.ndarray:
+        T = np.zeros((self.m, self.m, self.n))
+        np.add.at(T, (self.i, self.j, self.k), self.vf())
+        return T
+
+
+def symmetrise(m, n, i, j, k, v, mirror=True, validate=False) -> SymTensor:
+    """Store a (1,2)-symmetric tensor (Definition 2.1).
+
+    The paper does not say how a sparse list becomes (1,2)-symmetric; this
+    library's reading: with ``mirror`` the stored list is every input entry
+    in input order followed by the mirror (j, i, k, v) of every input entry
+    with i != j, again in input order (diagonal entries are not mirrored).
+    The list is stably sorted by the key (i, k, j) and entries with equal
+    keys are summed left to right in the value dtype; exact zeros are kept.
+    Without ``mirror`` the input must already hold both halves; with
+    ``validate`` the summed tensor must satisfy A(i,j,k) == A(j,i,k)
+    bitwise, else ValueError.
+    """
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    k = np.asarray(k, dtype=np.int64)
+    v = np.asarray(v)
+    if m <= 0 or n <= 0:
+        raise ValueError("m and n must be positive")
+    if i.size and (i.min() < 0 or j.min() < 0 or k.min() < 0 or i.max() >= m
+                   or j.max() >= m or k.max() >= n):
+        raise ValueError("index out of range")
+    if mirror:
+        off = i != j
+        ii = np.concatenate([i, j[off]])
+        jj = np.concatenate([j, i[off]])
+        kk = np.concatenate([k, k[off]])
+        vv = np.concatenate([v, v[off]])
+    else:
+        ii, jj, kk, vv = i, j, k, v
+    order = np.lexsort((jj, kk, ii))          # stable: primary i, then k, then j
+    ii, jj, kk, vv = ii[order], jj[order], kk[order], vv[order]
+    if ii.size == 0:
+        return SymTensor(m, n, ii.astype(np.int32), jj.astype(np.int32),
+                         kk.astype(np.int32), vv.copy())
+    new = np.ones(ii.size, dtype=bool)
+    new[1:] = (ii[1:] != ii[:-1]) | (kk[1:] != kk[:-1]) | (jj[1:] != jj[:-1])
+    starts = np.nonzero(new)[0]
+    lengths = np.diff(np.append(starts, ii.size))
+    # left-to-right sum inside each run of equal keys, in the value dtype:
+    # acc = v[s]; acc = acc + v[s+1]; ... (one vector step per position)
+    acc = vv[starts].copy()
+    for d in range(1, int(lengths.max())):
+        sel = lengths > d
+        acc[sel] = acc[sel] + vv[starts[sel] + d]
+    out = SymTensor(m, n, ii[starts].astype(np.int32), jj[starts].astype(np.int32),
+                    kk[starts].astype(np.int32), acc)
+    if validate:
+        key = {}
+        for a, b, c, x in zip(out.i.tolist(), out.j.tolist(), out.k.tolist(),
+                              out.v.tolist()):
+            key[(a, b, c)] = x
+        for (a, b, c), x in key.items():
+            y = key.get((b, a, c))
+            if y is None or np.float64(y).tobytes() != np.float64(x).tobytes():
+                raise ValueError("input is not (1,2)-symmetric")
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Contractions (Section 2.2; Algorithm 3 step (i); Section 4.3.1)
+# ----------------------------------------------------------------------------
+def tri_index(a: int, b: int) -> int:
+    """Column of the pair a <= b in triunfold_3 (Section 4.3.1): the upper
+    triangle in column-major order, a + b(b+1)/2."""
+    assert a <= b
+    return a + b * (b + 1) // 2
+
+
+def mode1(A: SymTensor, X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """unfold_1 of A.(X,Y)_{2,3} (Algorithm 3 step (i)):
+    Out[i, a + p*b] = sum over stored (i,j,k) of v * X[j,a] * Y[k,b].
+    X is m x p, Y is n x q; Out is m x (p*q)."""
+    p, q = X.shape[1], Y.shape[1]
+    out = np.zeros((A.m, p * q))
+    v = A.vf()
+    for b in range(q):
+        vy = v * Y[A.k, b]
+        for a in range(p):
+            out[:, a + p * b] = np.bincount(A.i, weights=vy * X[A.j, a], minlength=A.m)
+    return out
+
+
+def mode3(A: SymTensor, X: np.ndarray, X2: np.ndarray | None = None) -> np.ndarray:
+    """unfold_3 of A.(X,X2)_{1,2} (Section 4.3.1).  Full form:
+    Out[k, a + p*b] = sum v * X[i,a] * X2[j,b]  (n x p*q).
+    Triangle form (X2 is None, i.e. X2 = X): only the columns a <= b of the
+    full form, at column a + b(b+1)/2 (triunfold_3)."""
+    v = A.vf()
+    p = X.shape[1]
+    if X2 is None:
+        out = np.zeros((A.n, p * (p + 1) // 2))
+        for b in range(p):
+            vb = v * X[A.j, b]
+            for a in range(b + 1):
+                out[:, tri_index(a, b)] = np.bincount(A.k, weights=vb * X[A.i, a],
+                                                      minlength=A.n)
+        return out
+    q = X2.shape[1]
+    out = np.zeros((A.n, p * q))
+    for b in range(q):
+        vb = v * X2[A.j, b]
+        for a in range(p):
+            out[:, a + p * b] = np.bincount(A.k, weights=vb * X[A.i, a], minlength=A.n)
+    return out
+
+
+def core(A: SymTensor, U: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """F = A.(U,U,W) (eq. (Rayleigh)), r1 x r1 x r3 with
+    F[a,b,c] = sum v U[i,a] U[j,b] W[k,c].  Computed as U^T (A.(U,W)_{2,3})
+    (mode products in different modes commute, Section 2.2)."""
+    r1, r3 = U.shape[1], W.shape[1]
+    M = mode1(A, U, W)                     # m x (r1*r3), column b + r1*c
+    F1 = U.T @ M                           # unfold_1(F): r1 x (r1*r3)
+    return F1.reshape(r1, r1, r3, order="F")
+
+
+def core_dense_check(T: np.ndarray, U: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """Brute force A.(U,U,W) on a dense array (the definition of Section 2.2)."""
+    return np.einsum("ijk,ia,jb,kc->abc", T, U, U, W, optimize=True)
+
+
+def unfold1(F: np.ndarray) -> np.ndarray:
+    """Mode-1 unfolding, column index b + r2*c (first remaining index fastest)."""
+    return F.reshape(F.shape[0], -1, order="F")
+
+
+def unfold3(F: np.ndarray) -> np.ndarray:
+    """Mode-3 unfolding, column index a + r1*b."""
+    return F.reshape(-1, F.shape[2], order="F").T
+
+
+# ----------------------------------------------------------------------------
+# Block Gram-Schmidt + thin QR (Algorithm 3 (ii)-(iv), Appendix B)
+# ----------------------------------------------------------------------------
+def orth_block(Q: np.ndarray, B: np.ndarray, drop_tol: float, max_total: int | None = None):
+    """Orthogonalise the new block B (m x b) against the orthonormal basis
+    Q (m x K) and orthonormalise it (Algorithm 3 steps (ii)-(iv); Appendix B
+    replaces the tensor form by a QR of the matrix form).
+
+    Reading of this library: the block is projected against Q twice
+    (classical Gram-Schmidt with one reorthogonalisation); then its columns
+    are orthonormalised left to right, each projected twice against Q and
+    the new columns kept so far.  A column whose residual norm is not above
+    ``drop_tol`` times its raw norm (or that would take the basis past
+    ``max_total`` columns) is dropped.
+
+    Returns (Qn, H, R, kept): B = Q H + Qn R up to the dropped residuals,
+    H is K x b, R is b' x b (b' = len(kept)) and R[t, c] = 0 whenever
+    kept[t] > c.
+    """
+    m, b = B.shape
+    K = Q.shape[1]
+    raw = np.linalg.norm(B, axis=0)
+    H = np.zeros((K, b))
+    Bt = B.copy()
+    for _ in range(2):
+        h = Q.T @ Bt
+        Bt -= Q @ h
+        H += h
+    cap = b if max_total is None else max(0, min(b, max_total - K))
+    cols, kept = [], []
+    R = np.zeros((b, b))
+    for c in range(b):
+        x = Bt[:, c].copy()
+        P = np.concatenate([Q] + [cc[:, None] for cc in cols], axis=1)
+        g = np.zeros(P.shape[1])
+        for _ in range(2):
+            h = P.T @ x
+            x -= P @ h
+            g += h
+        H[:, c] += g[:K]
+        R[: len(cols), c] = g[K:]
+        nx = float(np.linalg.norm(x))
+        if len(cols) < cap and raw[c] > 0.0 and nx > drop_tol * raw[c]:
+            R[len(cols), c] = nx
+            cols.append(x / nx)
+            kept.append(c)
+    bp = len(cols)
+    Qn = np.stack(cols, axis=1) if cols else np.zeros((m, 0))
+    return Qn, H, R[:bp].copy(), kept
+
+
+# ----------------------------------------------------------------------------
+# Block schedules (Tables 1-3, Algorithm 4, Section 4.3.4)
+# ----------------------------------------------------------------------------
+def _stage_pairs(variant: str, stage: int, nU: int, nW: int, done_u: set, done_w: set):
+    """The (left, right, triangle) block pairs of one stage, U-blocks first
+    then W-blocks, each list in the order of the paper's diagrams.
+
+    BK (Table 3): stage 1 uses (U0,W0) and the triangle (U0,U0).  At stage
+    t >= 2 with q = t-1 the U-blocks come from (U0,Wq), (Uq,W0), (U1,Wq),
+    (Uq,W1), ..., (U_{q-1},Wq), (Uq,W_{q-1}) (the diagonal (Uq,Wq) is left
+    out) and the W-blocks from (U0,Uq), (U1,Uq), ..., (U_{q-1},Uq).  Blocks
+    are numbered in generation order; bars (first p columns) are applied by
+    the caller.
+    min-BK (Algorithm 4, Table 1): stage t uses (U_{t-1},W_{t-1}) and the
+    triangle (U_{t-1},U_{t-1}).
+    max-BK (Table 2): every not yet used pair of whole blocks that exist at
+    the start of the stage, by shells max(i,j) = s with (i,s),(s,i) for
+    i < s then (s,s); W pairs i <= j, diagonal pairs as triangles.
+    """
+    us, ws = [], []
+    if stage == 1:
+        return [(0, 0, False)], [(0, 0, True)]
+    if variant == "bk":
+        q = stage - 1
+        if q >= nU or q >= nW:
+            return [], []
+        for t in range(q):
+            us.append((t, q, False))
+            us.append((q, t, False))
+        for t in range(q):
+            ws.append((t, q, False))
+        return us, ws
+    if variant == "min":
+        q = stage - 1
+        if q >= nU or q >= nW:
+            return [], []
+        return [(q, q, False)], [(q, q, True)]
+    if variant == "max":
+        top = max(nU, nW)
+        for s in range(top):
+            for t in range(s):
+                for (a, b_) in ((t, s), (s, t)):
+                    if a < nU and b_ < nW and (a, b_) not in done_u:
+                        us.append((a, b_, False))
+            if s < nU and s < nW and (s, s) not in done_u:
+                us.append((s, s, False))
+        for s in range(nU):
+            for t in range(s + 1):
+                if (t, s) not in done_w:
+                    ws.append((t, s, t == s))
+        return us, ws
+    raise ValueError(variant)
+
+
+def schedule_counts(r1: int, r3: int, s: int, p: int, variant: str = "bk",
+                    m: int | None = None, n: int | None = None):
+    """(k1, k3) after each of the s stages when no column is dropped, with
+    the caps k1 <= m and k3 <= n of Section 4.3.4 (bookkeeping of Tables
+    1-3).  Bars take min(p, width) leading columns except for U0 and W0,
+    which are always used whole (Section 4.3.2)."""
+    uw, ww = [r1], [r3]
+    done_u, done_w = set(), set()
+    out = []
+    k1, k3 = r1, r3
+    for st in range(1, s + 1):
+        us, ws = _stage_pairs(variant, st, len(uw), len(ww), done_u, done_w)
+        nu, nw = list(uw), list(ww)
+        for (a, b_, _) in us:
+            wa = _bar(variant, a, uw[a], p)
+            wb = _bar(variant, b_, ww[b_], p)
+            cols = wa * wb
+            if m is not None:
+                cols = max(0, min(cols, m - k1))
+            nu.append(cols)
+            k1 += cols
+            done_u.add((a, b_))
+        for (a, b_, tri) in ws:
+            wa = _bar(variant, a, uw[a], p)
+            wb = _bar(variant, b_, uw[b_], p)
+            cols = wa * (wa + 1) // 2 if tri else wa * wb
+            if n is not None:
+                cols = max(0, min(cols, n - k3))
+            nw.append(cols)
+            k3 += cols
+            done_w.add((a, b_))
+        uw, ww = nu, nw
+        out.append((k1, k3))
+    return out
+
+
+def _bar(variant, idx, width, p):
+    if variant == "max" or idx == 0:
+        return width
+    return min(p, width)
+
+
+def expand(A: SymTensor, U0: np.ndarray, W0: np.ndarray, s: int, p: int,
+           variant: str = "bk", drop_tol: float = 1e-12):
+    """Expand (U0, W0) to the bases X = [U0 U1 ...] (m x k1) and
+    Z = [W0 W1 ...] (n x k3) with s stages of the chosen block schedule
+    (Algorithm 5 steps (iii) and (v)).  Within a stage all U-blocks are made
+    first, then all W-blocks, each in diagram order; every contraction of a
+    stage uses only blocks that existed when the stage began.
+
+    Returns (X, Z, info) with info holding the stage-1 factors used by
+    Proposition 2: H1 = U0^T A.(U0,W0)_{2,3}, R1 (its residual's R factor),
+    H3 and R3 for the triangle (U0,U0) block.
+    """
+    m, n = A.m, A.n
+    Ub = [U0.copy()]
+    Wb = [W0.copy()]
+    X = U0.copy()
+    Z = W0.copy()
+    done_u, done_w = set(), set()
+    info = {}
+    for st in range(1, s + 1):
+        us, ws = _stage_pairs(variant, st, len(Ub), len(Wb), done_u, done_w)
+        newU, newW = [], []
+        for (a, b_, _) in us:
+            L = Ub[a] if (variant == "max" or a == 0) else Ub[a][:, :p]
+            Rr = Wb[b_] if (variant == "max" or b_ == 0) else Wb[b_][:, :p]
+            done_u.add((a, b_))
+            if L.shape[1] == 0 or Rr.shape[1] == 0:
+                newU.append(np.zeros((m, 0)))
+                continue
+            Bm = mode1(A, L, Rr)
+            Qn, H, R, kept = orth_block(X, Bm, drop_tol, max_total=m)
+            if st == 1:
+                info["H1"], info["R1"] = H, R
+            X = np.concatenate([X, Qn], axis=1)
+            newU.append(Qn)
+        for (a, b_, tri) in ws:
+            L = Ub[a] if (variant == "max" or a == 0) else Ub[a][:, :p]
+            Rr = Ub[b_] if (variant == "max" or b_ == 0) else Ub[b_][:, :p]
+            done_w.add((a, b_))
+            if L.shape[1] == 0 or Rr.shape[1] == 0:
+                newW.append(np.zeros((n, 0)))
+                continue
+            Bm = mode3(A, L) if tri else mode3(A, L, Rr)
+            Qn, H, R, kept = orth_block(Z, Bm, drop_tol, max_total=n)
+            if st == 1:
+                info["H3"], info["R3"] = H, R
+            Z = np.concatenate([Z, Qn], axis=1)
+            newW.append(Qn)
+        Ub.extend(newU)
+        Wb.extend(newW)
+        if st == 1:
+            info["stage1_done"] = True
+    return X, Z, info
+
+
+# ----------------------------------------------------------------------------
+# Gradient (Section 2.5; Proposition 2)
+# ----------------------------------------------------------------------------
+def _tri_weights_F3(F: np.ndarray) -> np.ndarray:
+    """r3 x r1(r1+1)/2 matrix with column tri(a,b) = w_ab * F[a,b,:],
+    w_aa = 1, w_ab = 2 (a < b): the mode-3 partial contraction of F with a
+    (1,2)-symmetric tensor stored as its triangle."""
+    r1, _, r3 = F.shape
+    out = np.zeros((r3, r1 * (r1 + 1) // 2))
+    for b in range(r1):
+        for a in range(b + 1):
+            out[:, tri_index(a, b)] = (1.0 if a == b else 2.0) * F[a, b, :]
+    return out
+
+
+def gradient_prop2(H1, R1, H3, R3, r1, r3):
+    """||grad|| and ||F|| at (U0,U0,W0) from the first block-Krylov step
+    (Proposition 2).  H1 = unfold_1(F) (r1 x r1 r3); R1 is the R factor of
+    the mode-1 residual so <H0, H1^1>_{-1} = H1 R1^T; R3 is the R factor of
+    the triangle mode-3 residual, so <H0,H1^3>_{-3} = F3w R3^T with F3w the
+    weighted triangle of F.  For a (1,2)-symmetric tensor the mode-2 term
+    equals the mode-1 term, hence ||grad||^2 = 2||H1 R1^T||^2 + ||F3w R3^T||^2
+    (this library's reading of Proposition 2 with V = U)."""
+    F = H1.reshape(r1, r1, r3, order="F")
+    g1 = np.linalg.norm(H1 @ R1.T) if R1.size else 0.0
+    g3 = np.linalg.norm(_tri_weights_F3(F) @ R3.T) if R3.size else 0.0
+    grad = math.sqrt(2.0 * g1 * g1 + g3 * g3)
+    return grad, float(np.linalg.norm(F)), F
+
+
+def gradient_global(A: SymTensor, U: np.ndarray, W: np.ndarray):
+    """||grad||, ||F|| in global coordinates (Section 2.5):
+    mode 1: (I - U U^T) Gamma1, Gamma1 = <A.(U,W)_{2,3}, F>_{-1};
+    mode 3: (I - W W^T) Gamma3, Gamma3 = <A.(U,U)_{1,2}, F>_{-3};
+    mode 2 equals mode 1 by (1,2)-symmetry."""
+    r1, r3 = U.shape[1], W.shape[1]
+    T1 = mode1(A, U, W)
+    F1 = U.T @ T1
+    F = F1.reshape(r1, r1, r3, order="F")
+    G1 = T1 @ F1.T
+    G1 -= U @ (U.T @ G1)
+    T3 = mode3(A, U, U)                    # n x r1^2, column a + r1*b
+    G3 = T3 @ unfold3(F).T
+    G3 -= W @ (W.T @ G3)
+    g = math.sqrt(2.0 * np.linalg.norm(G1) ** 2 + np.linalg.norm(G3) ** 2)
+    return g, float(np.linalg.norm(F)), F
+
+
+def s_values(F: np.ndarray):
+    """S-values of Section 2.6: s_i^(k) = sqrt(lambda_i(<F,F>_{-k}))."""
+    out = []
+    for k in range(3):
+        Fk = np.moveaxis(F, k, 0).reshape(F.shape[k], -1)
+        ev = np.linalg.eigvalsh(Fk @ Fk.T)[::-1]
+        out.append(np.sqrt(np.maximum(ev, 0.0)))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Small dense helpers
+# ----------------------------------------------------------------------------
+def top_left_singular(M: np.ndarray, r: int) -> np.ndarray:
+    """The r leading left singular vectors of M (descending singular
+    values), by the library SVD."""
+    u, s, vt = np.linalg.svd(M, full_matrices=False)
+    return u[:, :r].copy()
+
+
+def _top_eig(G: np.ndarray, r: int) -> np.ndarray:
+    w, V = np.linalg.eigh(G)
+    return V[:, ::-1][:, :r].copy()
+
+
+def sin_theta_max(Ua: np.ndarray, Ub: np.ndarray) -> float:
+    """sin of the largest principal angle between span(Ua) and span(Ub):
+    ||(I - Ua Ua^T) Ub||_2 for orthonormal Ua, Ub."""
+    D = Ub - Ua @ (Ua.T @ Ub)
+    return float(np.linalg.norm(D, 2)) if D.size else 0.0
+
+
+# ----------------------------------------------------------------------------
+# Inner solve on the dense core (Algorithm 5 step (i); Section 6.2)
+# ----------------------------------------------------------------------------
+def _c_t1(C, Uh, Wh):
+    # unfold_1(C x_2 Uh^T x_3 Wh^T): k1 x (r1 r3), column b + r1 c
+    T = np.einsum("abc,bi,cj->aij", C, Uh, Wh, optimize=True)
+    return T.reshape(C.shape[0], -1, order="F")
+
+
+def _c_t3(C, Uh):
+    # unfold_3(C x_1 Uh^T x_2 Uh^T): k3 x r1^2, column a + r1 b
+    T = np.einsum("abc,ai,bj->ijc", C, Uh, Uh, optimize=True)
+    return T.reshape(-1, C.shape[2], order="F").T
+
+
+def _inner_grad(Uh, Wh, T1, T3):
+    F1 = Uh.T @ T1
+    F3 = Wh.T @ T3
+    G1 = T1 @ F1.T
+    G1 -= Uh @ (Uh.T @ G1)
+    G3 = T3 @ F3.T
+    G3 -= Wh @ (Wh.T @ G3)
+    g = math.sqrt(2.0 * np.sum(G1 * G1) + np.sum(G3 * G3))
+    return g, float(np.linalg.norm(F1)), F1
+
+
+def _hooi_sweeps(C, Uh, Wh, sweeps, tol):
+    """Symmetric HOOI sweeps on the dense core (Section 6.1 applied to C):
+    Uh <- top r1 left singular vectors of unfold_1(C.(Uh,Wh)_{2,3}) (old Uh),
+    then Wh <- top r3 of unfold_3(C.(Uh,Uh)_{1,2}) (new Uh).  The G-gradient
+    is checked before each sweep; stops at ||grad|| <= tol ||F|| or after
+    ``sweeps`` sweeps.  Returns (Uh, Wh, grad, normF, sweeps_done)."""
+    r1, r3 = Uh.shape[1], Wh.shape[1]
+    T3 = _c_t3(C, Uh)
+    done = 0
+    while True:
+        T1 = _c_t1(C, Uh, Wh)
+        g, nf, _ = _inner_grad(Uh, Wh, T1, T3)
+        if done >= sweeps or g <= tol * nf:
+            return Uh, Wh, g, nf, done
+        Uh = top_left_singular(T1, r1)
+        T3 = _c_t3(C, Uh)
+        Wh = top_left_singular(T3, r3)
+        done += 1
+
+
+def inner_solve(C: np.ndarray, r1: int, r3: int, tol: float, max_inner: int = 1000,
+                init_sweeps: int = 5):
+    """Best rank-(r1,r1,r3) approximation of the dense (1,2)-symmetric core
+    C (k1 x k1 x k3), Algorithm 5 step (i).
+
+    Section 6.2 starts from the truncated HOSVD of C followed by 5 HOOI
+    sweeps and then runs Newton-Grassmann.  This library's reading: the
+    truncated HOSVD start and the current point (Uh = [I;0], Wh = [I;0],
+    which is (U0, W0) in the bases) each get ``init_sweeps`` HOOI sweeps; the
+    one with the larger ||F|| continues with HOOI sweeps until its G-gradient
+    is below ``tol`` relative to ||F|| or ``max_inner`` sweeps.  Keeping the
+    current point as a candidate makes ||F|| non-decreasing over the outer
+    iterations (eq. (Fnon-decr)).
+    Returns (Uh, Wh, info)."""
+    k1, _, k3 = C.shape
+    C1 = C.reshape(k1, -1, order="F")
+    C3 = unfold3(C)
+    Uh_a = _top_eig(C1 @ C1.T, r1)
+    Wh_a = _top_eig(C3 @ C3.T, r3)
+    Uh_b = np.eye(k1, r1)
+    Wh_b = np.eye(k3, r3)
+    A_ = _hooi_sweeps(C, Uh_a, Wh_a, init_sweeps, 0.0)
+    B_ = _hooi_sweeps(C, Uh_b, Wh_b, init_sweeps, 0.0)
+    start = A_ if A_[3] >= B_[3] else B_
+    Uh, Wh, g, nf, done = _hooi_sweeps(C, start[0], start[1], max_inner, tol)
+    return Uh, Wh, {"grad": g, "normF": nf, "sweeps": done + init_sweeps,
+                    "hosvd_won": start is A_}
+
+
+# ----------------------------------------------------------------------------
+# Tensor Krylov-Schur (Algorithm 5) and HOOI (Section 6.1)
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class BKSResult:
+    U: np.ndarray
+    W: np.ndarray
+    F: np.ndarray
+    converged: bool
+    iters: int
+    grad_rel: float
+    normF: float
+    history: list
+
+
+def bks(A: SymTensor, U0: np.ndarray, W0: np.ndarray, s: int = 2, p: int = 4,
+        tol: float = 1e-10, max_outer: int = 500, variant: str = "bk",
+        drop_tol: float = 1e-12, inner_tol: float | None = None,
+        max_inner: int = 1000) -> BKSResult:
+    """Tensor Krylov-Schur for a (1,2)-symmetric tensor (Algorithm 5 with
+    U = V, X = Y, Section 5).  Each outer iteration: one BK stage from
+    (U0, W0) gives the G-gradient by Proposition 2 (steps (iii)-(iv)); stop
+    if ||grad||/||F|| <= tol; else finish the s-stage expansion (step (v)),
+    form C = A.(X,X,Z) (eq. (tkd)), solve the inner problem (step (i)) and
+    restart from U0 = X Uh, W0 = Z Wh (eq. (tks1), step (ii))."""
+    r1, r3 = U0.shape[1], W0.shape[1]
+    U, W = U0.copy(), W0.copy()
+    hist = []
+    itol = tol if inner_tol is None else inner_tol
+    F = None
+    for it in range(max_outer + 1):
+        X, Z, info = expand(A, U, W, 1, p, variant, drop_tol)
+        g, nf, F = gradient_prop2(info["H1"], info["R1"], info["H3"], info["R3"], r1, r3)
+        hist.append({"grad_rel": g / nf if nf > 0 else math.inf, "normF": nf})
+        if nf > 0 and g <= tol * nf:
+            return BKSResult(U, W, F, True, it, g / nf, nf, hist)
+        if it == max_outer:
+            break
+        X, Z, _ = expand(A, U, W, s, p, variant, drop_tol)
+        hist[-1]["k1"], hist[-1]["k3"] = X.shape[1], Z.shape[1]
+        Cc = core(A, X, Z)
+        Uh, Wh, iinfo = inner_solve(Cc, r1, r3, itol, max_inner)
+        hist[-1]["inner_sweeps"] = iinfo["sweeps"]
+        U = X @ Uh
+        W = Z @ Wh
+    return BKSResult(U, W, F, False, max_outer, hist[-1]["grad_rel"], hist[-1]["normF"], hist)
+
+
+def hooi(A: SymTensor, U0: np.ndarray, W0: np.ndarray, tol: float = 1e-10,
+         max_iter: int = 5000, grad_every: int = 10) -> BKSResult:
+    """HOOI for a (1,2)-symmetric tensor (Section 6.1): U <- the r1 leading
+    left singular vectors of unfold_1(A.(U,W)_{2,3}) with the previous U,
+    then W <- the r3 leading left singular vectors of unfold_3(A.(U,U)_{1,2})
+    with the new U.  The G-gradient (global coordinates, Section 2.5) is
+    evaluated every ``grad_every`` iterations, at the start of the
+    iteration, from the contractions that iteration needs anyway."""
+    r1, r3 = U0.shape[1], W0.shape[1]
+    U, W = U0.copy(), W0.copy()
+    T3 = mode3(A, U, U)
+    hist = []
+    F1 = None
+    for it in range(max_iter + 1):
+        T1 = mode1(A, U, W)
+        if it % grad_every == 0 or it == max_iter:
+            F1 = U.T @ T1
+            F3 = W.T @ T3
+            G1 = T1 @ F1.T
+            G1 -= U @ (U.T @ G1)
+            G3 = T3 @ F3.T
+            G3 -= W @ (W.T @ G3)
+            g = math.sqrt(2.0 * np.linalg.norm(G1) ** 2 + np.linalg.norm(G3) ** 2)
+            nf = float(np.linalg.norm(F1))
+            hist.append({"iter": it, "grad_rel": g / nf if nf > 0 else math.inf,
+                         "normF": nf})
+            if (nf > 0 and g <= tol * nf) or it == max_iter:
+                F = F1.reshape(r1, r1, r3, order="F")
+                return BKSResult(U, W, F, nf > 0 and g <= tol * nf, it, g / nf, nf, hist)
+        U = top_left_singular(T1, r1)
+        T3 = mode3(A, U, U)
+        W = top_left_singular(T3, r3)
+    raise AssertionError("unreachable")

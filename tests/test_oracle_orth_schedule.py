@@ -1,0 +1,106 @@
+"""Pins of the oracle's block orthogonalisation and block schedules."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_orth_block_reconstruction_and_orthonormality():
+    g = synth.rng(11)
+    m = 200
+    Q = np.linalg.qr(g.standard_normal((m, 7)))[0]
+    B = g.standard_normal((m, 6)) + Q @ g.standard_normal((7, 6)) * 10
+    Qn, H, R, kept = O.orth_block(Q, B, 1e-12)
+    assert kept == list(range(6))
+    Z = np.concatenate([Q, Qn], axis=1)
+    assert np.linalg.norm(Z.T @ Z - np.eye(13)) < 1e-13
+    assert np.linalg.norm(B - Q @ H - Qn @ R) < 1e-12 * np.linalg.norm(B)
+    assert np.allclose(np.triu(R), R)
+    assert np.all(np.diag(R) > 0)
+
+
+def test_orth_block_drops_dependent_columns():
+    g = synth.rng(12)
+    m = 100
+    Q = np.linalg.qr(g.standard_normal((m, 4)))[0]
+    a = g.standard_normal(m); b = g.standard_normal(m)
+    # col0 free, col1 inside span(Q), col2 free, col3 = 2*col0 - col2 + Q-part, col4 = 0
+    B = np.stack([a, Q @ np.ones(4), b, 2 * a - b + Q[:, 0], np.zeros(m)], axis=1)
+    Qn, H, R, kept = O.orth_block(Q, B, 1e-12)
+    assert kept == [0, 2]
+    assert Qn.shape == (m, 2)
+    assert np.linalg.norm(B - Q @ H - Qn @ R) < 1e-12 * np.linalg.norm(B)
+    # the cap on the total number of basis vectors (k3 <= n) also drops
+    Qn2, _, _, kept2 = O.orth_block(Q, B, 1e-12, max_total=5)
+    assert kept2 == [0]
+
+
+def _gold():
+    with open(os.path.join(GOLD, "schedule_counts.json")) as f:
+        return json.load(f)
+
+
+def test_schedule_tables():
+    gold = _gold()
+    for t in gold["tables"]:
+        got = O.schedule_counts(t["r"], t["r"], len(t["stages"]), t["p"], t["variant"])
+        for st, (want, have) in enumerate(zip(t["stages"], got)):
+            if want[0] is not None:
+                assert have[0] == want[0], (t["cite"], st + 1)
+            assert have[1] == want[1], (t["cite"], st + 1)
+
+
+def test_schedule_captions():
+    for c in _gold()["captions"]:
+        got = O.schedule_counts(c["r"], c["r"], c["s"], c["p"], c["variant"], n=c["n"])
+        assert got[-1] == (c["k1"], c["k3"]), c["cite"]
+
+
+def test_schedule_disagreements_are_the_rule_values():
+    d = {x["cite"]: x for x in _gold()["disagree"]}
+    assert O.schedule_counts(2, 2, 4, 4, "bk")[3][0] == 140
+    assert O.schedule_counts(10, 10, 4, 4, "bk")[3][0] == 446
+    assert O.schedule_counts(2, 2, 2, 4, "bk")[-1] == (20, 13)
+    assert len(d) == 3
+
+
+def _sym_case(seed, m=30, n=8, draws=400):
+    c = synth.random_coo(seed, m, n, draws)
+    return O.symmetrise(m, n, c.i, c.j, c.k, c.v)
+
+
+@pytest.mark.parametrize("variant,s,p", [("bk", 2, 2), ("bk", 3, 2), ("min", 3, 2), ("max", 2, 0)])
+def test_expand_counts_and_lemma1(variant, s, p):
+    A = _sym_case(5)
+    g = synth.rng(9)
+    r = 2
+    U0 = synth.orthonormal(g, A.m, r); W0 = synth.orthonormal(g, A.n, r)
+    X, Z, info = O.expand(A, U0, W0, s, p, variant)
+    want = O.schedule_counts(r, r, s, p, variant, m=A.m, n=A.n)[-1]
+    assert (X.shape[1], Z.shape[1]) == want
+    assert np.linalg.norm(X.T @ X - np.eye(X.shape[1])) < 1e-12
+    assert np.linalg.norm(Z.T @ Z - np.eye(Z.shape[1])) < 1e-12
+    assert np.allclose(X[:, :r], U0) and np.allclose(Z[:, :r], W0)
+    # Lemma 1: A.(U_j, U0, W0) = 0 for blocks j >= 2 (columns past U0 and U1)
+    k_u1 = r + r * r
+    Hj = X[:, k_u1:].T @ O.mode1(A, U0, W0)
+    assert np.linalg.norm(Hj) < 1e-12 * max(1.0, np.linalg.norm(O.mode1(A, U0, W0)))
+    # and its mode-3 counterpart: A.(U0, U0, W_j) = 0 for j >= 2
+    k_w1 = r + r * (r + 1) // 2
+    Gj = Z[:, k_w1:].T @ O.mode3(A, U0)
+    assert np.linalg.norm(Gj) < 1e-12 * max(1.0, np.linalg.norm(O.mode3(A, U0)))
+
+
+def test_k3_cap():
+    A = _sym_case(6, m=30, n=5, draws=500)
+    g = synth.rng(1)
+    U0 = synth.orthonormal(g, A.m, 3); W0 = synth.orthonormal(g, A.n, 3)
+    X, Z, _ = O.expand(A, U0, W0, 2, 4, "bk")
+    assert Z.shape[1] == 5
+    assert np.linalg.norm(Z.T @ Z - np.eye(5)) < 1e-12
