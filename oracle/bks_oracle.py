@@ -210,13 +210,14 @@ def orth_block(Q: np.ndarray, B: np.ndarray, drop_tol: float, max_total: int | N
     Reading of this library: the block is projected against Q twice
     (classical Gram-Schmidt with one reorthogonalisation); then its columns
     are orthonormalised left to right, each projected twice against Q and
-    the new columns kept so far.  A column whose residual norm is not above
-    ``drop_tol`` times its raw norm (or that would take the basis past
-    ``max_total`` columns) is dropped.
+    the new columns kept so far.  A column is dropped when its residual
+    norm is not above ``drop_tol`` times its raw norm, or when it would take
+    the basis past ``max_total`` columns.
 
-    Returns (Qn, H, R, kept): B = Q H + Qn R up to the dropped residuals,
-    H is K x b, R is b' x b (b' = len(kept)) and R[t, c] = 0 whenever
-    kept[t] > c.
+    Returns (Qn, H, R, kept, P): B = Q H + Qn R up to the dropped
+    residuals, H is K x b, R is b' x b (b' = len(kept)) with R[t, c] = 0
+    whenever kept[t] > c, and P = B - Q H, the projected block (equal to
+    Qn R when no column is dropped).
     """
     m, b = B.shape
     K = Q.shape[1]
@@ -227,6 +228,7 @@ def orth_block(Q: np.ndarray, B: np.ndarray, drop_tol: float, max_total: int | N
         h = Q.T @ Bt
         Bt -= Q @ h
         H += h
+    Pb = Bt.copy()
     cap = b if max_total is None else max(0, min(b, max_total - K))
     cols, kept = [], []
     R = np.zeros((b, b))
@@ -247,7 +249,7 @@ def orth_block(Q: np.ndarray, B: np.ndarray, drop_tol: float, max_total: int | N
             kept.append(c)
     bp = len(cols)
     Qn = np.stack(cols, axis=1) if cols else np.zeros((m, 0))
-    return Qn, H, R[:bp].copy(), kept
+    return Qn, H, R[:bp].copy(), kept, Pb
 
 
 # ----------------------------------------------------------------------------
@@ -376,9 +378,9 @@ def expand(A: SymTensor, U0: np.ndarray, W0: np.ndarray, s: int, p: int,
                 newU.append(np.zeros((m, 0)))
                 continue
             Bm = mode1(A, L, Rr)
-            Qn, H, R, kept = orth_block(X, Bm, drop_tol, max_total=m)
+            Qn, H, R, kept, P = orth_block(X, Bm, drop_tol, max_total=m)
             if st == 1:
-                info["H1"], info["R1"] = H, R
+                info["H1"], info["R1"], info["P1"] = H, R, P
             X = np.concatenate([X, Qn], axis=1)
             newU.append(Qn)
         for (a, b_, tri) in ws:
@@ -389,9 +391,9 @@ def expand(A: SymTensor, U0: np.ndarray, W0: np.ndarray, s: int, p: int,
                 newW.append(np.zeros((n, 0)))
                 continue
             Bm = mode3(A, L) if tri else mode3(A, L, Rr)
-            Qn, H, R, kept = orth_block(Z, Bm, drop_tol, max_total=n)
+            Qn, H, R, kept, P = orth_block(Z, Bm, drop_tol, max_total=n)
             if st == 1:
-                info["H3"], info["R3"] = H, R
+                info["H3"], info["R3"], info["P3"] = H, R, P
             Z = np.concatenate([Z, Qn], axis=1)
             newW.append(Qn)
         Ub.extend(newU)
@@ -416,17 +418,21 @@ def _tri_weights_F3(F: np.ndarray) -> np.ndarray:
     return out
 
 
-def gradient_prop2(H1, R1, H3, R3, r1, r3):
+def gradient_prop2(H1, P1, P3, r1, r3):
     """||grad|| and ||F|| at (U0,U0,W0) from the first block-Krylov step
-    (Proposition 2).  H1 = unfold_1(F) (r1 x r1 r3); R1 is the R factor of
-    the mode-1 residual so <H0, H1^1>_{-1} = H1 R1^T; R3 is the R factor of
-    the triangle mode-3 residual, so <H0,H1^3>_{-3} = F3w R3^T with F3w the
-    weighted triangle of F.  For a (1,2)-symmetric tensor the mode-2 term
-    equals the mode-1 term, hence ||grad||^2 = 2||H1 R1^T||^2 + ||F3w R3^T||^2
-    (this library's reading of Proposition 2 with V = U)."""
+    (Proposition 2).  H1 = unfold_1(F) = U0^T A.(U0,W0)_{2,3} (r1 x r1 r3)
+    and P1 = U1 R1 is the projected mode-1 block, so the mode-1 term
+    ||<H0, H1^1>_{-1}|| = ||H1 R1^T|| = ||P1 H1^T||; the mode-3 term is
+    ||P3 F3w^T|| with P3 = W1 R3 the projected triangle block and F3w the
+    weighted triangle of F.  Evaluating through P rather than R keeps the
+    mass of columns the QR dropped.  For a (1,2)-symmetric tensor the
+    mode-2 term equals the mode-1 term, hence
+    ||grad||^2 = 2 ||P1 H1^T||^2 + ||P3 F3w^T||^2 (this library's reading
+    of Proposition 2 with V = U)."""
     F = H1.reshape(r1, r1, r3, order="F")
-    g1 = np.linalg.norm(H1 @ R1.T) if R1.size else 0.0
-    g3 = np.linalg.norm(_tri_weights_F3(F) @ R3.T) if R3.size else 0.0
+    F3w = _tri_weights_F3(F)
+    g1 = float(np.linalg.norm(P1 @ H1.T))
+    g3 = float(np.linalg.norm(P3 @ F3w.T))
     grad = math.sqrt(2.0 * g1 * g1 + g3 * g3)
     return grad, float(np.linalg.norm(F)), F
 
@@ -588,7 +594,7 @@ def bks(A: SymTensor, U0: np.ndarray, W0: np.ndarray, s: int = 2, p: int = 4,
     F = None
     for it in range(max_outer + 1):
         X, Z, info = expand(A, U, W, 1, p, variant, drop_tol)
-        g, nf, F = gradient_prop2(info["H1"], info["R1"], info["H3"], info["R3"], r1, r3)
+        g, nf, F = gradient_prop2(info["H1"], info["P1"], info["P3"], r1, r3)
         hist.append({"grad_rel": g / nf if nf > 0 else math.inf, "normF": nf})
         if nf > 0 and g <= tol * nf:
             return BKSResult(U, W, F, True, it, g / nf, nf, hist)

@@ -16,7 +16,7 @@ def test_orth_block_reconstruction_and_orthonormality():
     m = 200
     Q = np.linalg.qr(g.standard_normal((m, 7)))[0]
     B = g.standard_normal((m, 6)) + Q @ g.standard_normal((7, 6)) * 10
-    Qn, H, R, kept = O.orth_block(Q, B, 1e-12)
+    Qn, H, R, kept, S = O.orth_block(Q, B, 1e-12)
     assert kept == list(range(6))
     Z = np.concatenate([Q, Qn], axis=1)
     assert np.linalg.norm(Z.T @ Z - np.eye(13)) < 1e-13
@@ -32,12 +32,12 @@ def test_orth_block_drops_dependent_columns():
     a = g.standard_normal(m); b = g.standard_normal(m)
     # col0 free, col1 inside span(Q), col2 free, col3 = 2*col0 - col2 + Q-part, col4 = 0
     B = np.stack([a, Q @ np.ones(4), b, 2 * a - b + Q[:, 0], np.zeros(m)], axis=1)
-    Qn, H, R, kept = O.orth_block(Q, B, 1e-12)
+    Qn, H, R, kept, S = O.orth_block(Q, B, 1e-12)
     assert kept == [0, 2]
     assert Qn.shape == (m, 2)
     assert np.linalg.norm(B - Q @ H - Qn @ R) < 1e-12 * np.linalg.norm(B)
     # the cap on the total number of basis vectors (k3 <= n) also drops
-    Qn2, _, _, kept2 = O.orth_block(Q, B, 1e-12, max_total=5)
+    Qn2, _, _, kept2, _ = O.orth_block(Q, B, 1e-12, max_total=5)
     assert kept2 == [0]
 
 

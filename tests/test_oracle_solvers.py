@@ -27,7 +27,7 @@ def test_prop2_gradient_equals_global_gradient():
     for r1, r3 in [(2, 2), (3, 2), (2, 3)]:
         U = synth.orthonormal(g, A.m, r1); W = synth.orthonormal(g, A.n, r3)
         X, Z, info = O.expand(A, U, W, 1, 2)
-        gp, nfp, Fp = O.gradient_prop2(info["H1"], info["R1"], info["H3"], info["R3"], r1, r3)
+        gp, nfp, Fp = O.gradient_prop2(info["H1"], info["P1"], info["P3"], r1, r3)
         gg, nfg, Fg = O.gradient_global(A, U, W)
         assert abs(gp - gg) <= 1e-12 * gg
         assert abs(nfp - nfg) <= 1e-13 * nfg
@@ -77,8 +77,8 @@ def test_closed_form_single_slice(solver):
     A = _from_dense(T)
     g = synth.rng(5)
     U0 = synth.orthonormal(g, 24, 2); W0 = np.ones((1, 1))
-    res = (O.bks(A, U0, W0, s=2, p=2, tol=1e-12) if solver == "bks"
-           else O.hooi(A, U0, W0, tol=1e-12))
+    res = (O.bks(A, U0, W0, s=2, p=2, tol=1e-10) if solver == "bks"
+           else O.hooi(A, U0, W0, tol=1e-10))
     assert res.converged
     assert abs(res.normF ** 2 - np.sum(lam ** 2)) < 1e-10 * np.sum(lam ** 2)
     assert O.sin_theta_max(Utrue, res.U) < 1e-8
@@ -93,8 +93,8 @@ def test_closed_form_rank_one_slices(solver):
     A = _from_dense(T)
     g = synth.rng(6)
     U0 = synth.orthonormal(g, 20, 2); W0 = synth.orthonormal(g, 4, 1)
-    res = (O.bks(A, U0, W0, s=2, p=2, tol=1e-12) if solver == "bks"
-           else O.hooi(A, U0, W0, tol=1e-12))
+    res = (O.bks(A, U0, W0, s=2, p=2, tol=1e-10) if solver == "bks"
+           else O.hooi(A, U0, W0, tol=1e-10))
     assert res.converged
     want = np.sum(c ** 2) * np.sum(lam ** 2)
     assert abs(res.normF ** 2 - want) < 1e-10 * want
