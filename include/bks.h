@@ -1,0 +1,213 @@
+/*
+ * bks.h -- C ABI of the GB300 Block Krylov-Schur library.
+ *
+ * Computes best rank-(r1,r1,r3) approximations of large sparse 3-tensors
+ * A (m x m x n) that are symmetric in modes 1 and 2, A(i,j,k) = A(j,i,k)
+ * (Definition 2.1 of Eldén & Dehghan, "A Krylov-Schur like method for
+ * computing the best rank-(r1,r2,r3) approximation of large and sparse
+ * tensors").  The problem (Section 2.4, eqs. (main min) and (max)):
+ *
+ *     max || A.(U,U,W) ||   subject to  U^T U = I_r1,  W^T W = I_r3,
+ *
+ * with the optimal core F = A.(U,U,W) (eq. (Rayleigh)).
+ *
+ * Conventions for every call below
+ *   - Return value: BKS_OK (0) or a negative BKS_E* code.  The message of
+ *     the last failure on the calling thread is bks_last_error_string().
+ *     No C++ exception crosses this boundary.
+ *   - Matrices are column-major with an explicit leading dimension
+ *     (ld >= rows).  Indices are 0-based.
+ *   - Pointers are DEVICE pointers (cudaMalloc'ed or equivalent) unless a
+ *     comment says host.  The caller owns every buffer it passes; the
+ *     library owns the tensor handle and its device buffers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered: device results are ready when
+ *     the stream reaches the call's end.  Calls that return host-side
+ *     values (bks_tensor_info, the solvers' info) synchronise the stream.
+ *   - dtype BKS_F64 means double, BKS_F32 means float, for every floating
+ *     buffer of the call that the comment calls "dtype-typed".
+ *
+ * Limits: 2*ceil(log2 m) + ceil(log2 n) <= 64 bits (the ingest sort key),
+ * stored nonzeros < 2^31, contraction widths p, q <= 8 per call for the
+ * mode-1 and mode-3 contractions.
+ */
+#ifndef BKS_GB300_H
+#define BKS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define BKS_OK            0
+#define BKS_EINVAL       -1  /* bad argument: index out of range, size <= 0, null pointer */
+#define BKS_ENOMEM       -2  /* device allocation failed */
+#define BKS_ECUDA        -3  /* a CUDA runtime call failed (message has the CUDA error) */
+#define BKS_EASYM        -4  /* BKS_VALIDATE_SYMMETRIC: input is not (1,2)-symmetric */
+#define BKS_ENOTCONV     -5  /* solver hit max_outer / max_iter; best iterate still written */
+#define BKS_EBREAKDOWN   -6  /* a basis block collapsed to zero width where one is required */
+#define BKS_ENUMERIC     -7  /* NaN or Inf in ||F|| or in the gradient */
+#define BKS_EUNSUPPORTED -8  /* a size beyond the limits above */
+
+/* ---- dtypes, flags, options -------------------------------------------- */
+#define BKS_F32 1
+#define BKS_F64 2
+
+#define BKS_MIRROR             1  /* add (j,i,k,v) for every input entry with i != j */
+#define BKS_VALIDATE_SYMMETRIC 2  /* without MIRROR: check A(i,j,k) == A(j,i,k) bitwise */
+#define BKS_INPUT_ON_DEVICE    4  /* i, j, k, v are device pointers (default: host) */
+
+#define BKS_PREC_FP64  0  /* contractions in FP64 */
+#define BKS_PREC_MIXED 1  /* contractions in FP32 (FP64 orthogonalisation, inner solve, restart) */
+
+#define BKS_VARIANT_BK  0  /* BK schedule, Table 3 */
+#define BKS_VARIANT_MIN 1  /* min-BK, Algorithm 4 / Table 1 */
+#define BKS_VARIANT_MAX 2  /* max-BK, Table 2 */
+
+typedef struct bks_tensor bks_tensor;
+
+/* ---- tensor storage (Definition 2.1; Section 4.3 storage reading) -------
+ * bks_tensor_create_coo: copy a COO list into a new device-resident
+ * (1,2)-symmetric tensor.
+ *   m, n      : tensor is m x m x n (m, n >= 1)
+ *   nnz       : number of input entries (>= 0)
+ *   i, j, k   : int32 indices, host pointers unless BKS_INPUT_ON_DEVICE
+ *   v         : values of type vdtype (BKS_F32 or BKS_F64)
+ *   flags     : BKS_MIRROR adds the mirror (j,i,k,v) of each off-diagonal
+ *               entry.  The stored list is the input in input order, then
+ *               the mirrors in input order, stably sorted by (i,k,j);
+ *               entries with equal (i,j,k) are summed left to right in
+ *               vdtype; exact zeros are kept.  BKS_VALIDATE_SYMMETRIC
+ *               (without MIRROR) rejects a summed tensor that is not
+ *               bitwise (1,2)-symmetric with BKS_EASYM.
+ *   out       : receives the handle (host pointer to a handle)
+ * Errors: BKS_EINVAL (index >= m or >= n, m or n < 1, nnz < 0, null
+ * pointers), BKS_EUNSUPPORTED (sizes beyond the limits), BKS_EASYM,
+ * BKS_ENOMEM, BKS_ECUDA.  On error *out is NULL and nothing leaks. */
+int bks_tensor_create_coo(int64_t m, int64_t n, int64_t nnz,
+                          const int32_t* i, const int32_t* j, const int32_t* k,
+                          const void* v, int vdtype, int flags, void* stream,
+                          bks_tensor** out);
+
+/* Free the handle and its device buffers (NULL is a no-op). */
+void bks_tensor_destroy(bks_tensor* t);
+
+/* Host outputs (any may be NULL): sizes, stored nonzeros after
+ * symmetrisation and ||A||_F^2 (FP64 sum of the stored values squared). */
+int bks_tensor_info(const bks_tensor* t, int64_t* m, int64_t* n,
+                    int64_t* nnz_stored, double* fro2);
+
+/* Copy the stored tensor in its canonical order (sorted by (i,k,j)) into
+ * caller device buffers of nnz_stored entries each; v has the input
+ * vdtype.  Used for bit-exact checks of the ingest. */
+int bks_tensor_export_coo(const bks_tensor* t, int32_t* i, int32_t* j,
+                          int32_t* k, void* v, void* stream);
+
+/* ---- contractions (Section 2.2; Algorithm 3 step (i); Section 4.3.1) ----
+ * bks_contract_mode1: out = unfold_1(A.(X,Y)_{2,3}),
+ *     out[i + ldo*(a + p*b)] = sum over stored (i,j,k) of v X[j,a] Y[k,b]
+ *   X: m x p (ldx), Y: n x q (ldy), out: m x (p*q) (ldo); dtype-typed;
+ *   1 <= p, q <= 8.  `out` is overwritten (rows without entries get 0).
+ *   dtype BKS_F64 computes in FP64; BKS_F32 computes in FP32 with FP32
+ *   accumulation (blocked summation: short sequential runs combined by a
+ *   fixed-order tree). Deterministic: the same call gives the same bits. */
+int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
+                       const void* Y, int64_t ldy, int q, void* out,
+                       int64_t ldo, int dtype, void* stream);
+
+/* bks_contract_mode3: out = unfold_3(A.(X,X2)_{1,2})
+ *   X2 != NULL: out[k + ldo*(a + p*b)] = sum v X[i,a] X2[j,b]; out is
+ *     n x (p*q); X2 is m x q (ldx2).
+ *   X2 == NULL: the (1,2)-symmetric case X2 = X stored as triunfold_3
+ *     (Section 4.3.1): out[k + ldo*(a + b(b+1)/2)] for a <= b; out is
+ *     n x p(p+1)/2.
+ *   1 <= p, q <= 8; dtype-typed; out overwritten; deterministic. */
+int bks_contract_mode3(const bks_tensor* t, const void* X, int64_t ldx, int p,
+                       const void* X2, int64_t ldx2, int q, void* out,
+                       int64_t ldo, int dtype, void* stream);
+
+/* bks_core: F = A.(U,U,W) (eq. (Rayleigh); with the Krylov bases it is
+ *   C = A.(X,X,Z) of eq. (tkd)).  U: m x r1 (ldu), W: n x r3 (ldw),
+ *   F: r1*r1*r3 contiguous, F[a + r1*(b + r1*c)]; dtype-typed; any
+ *   r1 <= 128, r3 <= 128.  F is symmetric in (a, b). */
+int bks_core(const bks_tensor* t, const void* U, int64_t ldu, int r1,
+             const void* W, int64_t ldw, int r3, void* F, int dtype,
+             void* stream);
+
+/* ---- solvers (Algorithm 5; Section 6.1) --------------------------------- */
+typedef struct {
+  int r1, r3;          /* target multilinear rank (r1, r1, r3) */
+  int stages;          /* s: BK stages per expansion (paper recommends 2) */
+  int block_p;         /* p: leading columns of each ON-block used (paper: 4) */
+  double tol;          /* stop when ||grad|| / ||F|| <= tol (Section 6.2) */
+  int max_outer;       /* outer-iteration cap (BKS_ENOTCONV past it) */
+  int max_inner;       /* inner HOOI sweep cap per outer iteration */
+  int variant;         /* BKS_VARIANT_* */
+  int precision;       /* BKS_PREC_FP64 or BKS_PREC_MIXED */
+  int refine_sweeps;   /* MIXED only: FP64 outer iterations after the FP32 phase converged */
+  uint64_t seed;       /* random start when U0/W0 are NULL */
+  double drop_tol;     /* rank-drop threshold of the block QR (relative) */
+  double inner_tol;    /* inner stopping tolerance (<= 0: same as tol) */
+  double mixed_tol;    /* MIXED only: tolerance of the FP32 phase (<= 0: 1e-6) */
+} bks_params;
+
+typedef struct {
+  int iters;           /* outer iterations done */
+  int converged;       /* 1 if the final gradient test passed */
+  double grad_rel;     /* ||grad|| / ||F|| at the returned point */
+  double normF;        /* ||F|| at the returned point */
+  int k1, k3;          /* basis sizes of the last expansion */
+  int inner_sweeps;    /* total inner HOOI sweeps */
+  int fp32_iters;      /* MIXED: outer iterations with FP32 contractions */
+  double seconds;      /* host wall time of the call */
+  double* history;     /* host, optional: 2 doubles (grad_rel, normF) per outer iteration */
+  int history_cap;     /* capacity of history in iterations */
+  int history_len;     /* filled entries */
+} bks_info;
+
+/* Default parameters: r1 = r3 = 2, s = 2, p = 4, tol 1e-10, max_outer 500,
+ * max_inner 1000, BK, FP64, refine 1, seed 1, drop_tol 1e-12. */
+void bks_params_default(bks_params* p);
+
+/* bks_solve: tensor Krylov-Schur (Algorithm 5 with U = V, X = Y).
+ *   U0 (m x r1, ld m), W0 (n x r3, ld n): orthonormal start, device FP64,
+ *     or NULL for a seeded random start.
+ *   U (m x r1, ld m), W (n x r3, ld n), F (r1*r1*r3): device FP64 outputs.
+ *   info: host pointer or NULL.
+ * Returns BKS_OK, BKS_ENOTCONV (best iterate written), BKS_ENUMERIC,
+ * BKS_EBREAKDOWN, BKS_EINVAL, BKS_ENOMEM, BKS_ECUDA.  Synchronises
+ * `stream` once per outer iteration to read the convergence test. */
+int bks_solve(const bks_tensor* t, const bks_params* prm, const double* U0,
+              const double* W0, double* U, double* W, double* F,
+              bks_info* info, void* stream);
+
+typedef struct {
+  int r1, r3;
+  double tol;
+  int max_iter;
+  int grad_every;      /* gradient test cadence (Section 6.1: every 10) */
+  int precision;       /* BKS_PREC_FP64 or BKS_PREC_MIXED */
+  uint64_t seed;
+} hooi_params;
+
+void hooi_params_default(hooi_params* p);
+
+/* hooi_solve: HOOI for (1,2)-symmetric tensors (Section 6.1): U from the
+ * r1 leading left singular vectors of unfold_1(A.(U,W)_{2,3}), then W from
+ * the r3 leading left singular vectors of unfold_3(A.(U,U)_{1,2}).
+ * Same buffers and errors as bks_solve. */
+int hooi_solve(const bks_tensor* t, const hooi_params* prm, const double* U0,
+               const double* W0, double* U, double* W, double* F,
+               bks_info* info, void* stream);
+
+/* Last error message of the calling thread ("" if none). */
+const char* bks_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BKS_GB300_H */

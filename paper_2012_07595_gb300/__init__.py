@@ -1,0 +1,376 @@
+"""Python binding of the GB300 Block Krylov-Schur library (libbks_gb300.so).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+The names follow the C ABI in include/bks.h.  PyTorch supplies device
+memory and streams; dense matrices are torch CUDA tensors in column-major
+layout (shape (rows, cols), stride (1, ld)).  The library must be built
+(``paper_2012_07595_gb300._build.build()``); importing this package never
+falls back to another implementation: a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "lib", "BKS_OK", "BKS_F32", "BKS_F64", "BKS_MIRROR", "BKS_VALIDATE_SYMMETRIC",
+    "BKS_INPUT_ON_DEVICE", "BKS_PREC_FP64", "BKS_PREC_MIXED", "BKS_VARIANT_BK",
+    "BKS_VARIANT_MIN", "BKS_VARIANT_MAX", "BksError", "Tensor", "bks_tensor_create_coo",
+    "bks_tensor_destroy", "bks_tensor_info", "bks_tensor_export_coo", "bks_contract_mode1",
+    "bks_contract_mode3", "bks_core", "bks_solve", "hooi_solve", "BksParams", "HooiParams",
+    "col_major", "library_path",
+]
+
+BKS_OK = 0
+BKS_EINVAL, BKS_ENOMEM, BKS_ECUDA, BKS_EASYM = -1, -2, -3, -4
+BKS_ENOTCONV, BKS_EBREAKDOWN, BKS_ENUMERIC, BKS_EUNSUPPORTED = -5, -6, -7, -8
+BKS_F32, BKS_F64 = 1, 2
+BKS_MIRROR, BKS_VALIDATE_SYMMETRIC, BKS_INPUT_ON_DEVICE = 1, 2, 4
+BKS_PREC_FP64, BKS_PREC_MIXED = 0, 1
+BKS_VARIANT_BK, BKS_VARIANT_MIN, BKS_VARIANT_MAX = 0, 1, 2
+
+_ERRNAMES = {BKS_EINVAL: "BKS_EINVAL", BKS_ENOMEM: "BKS_ENOMEM", BKS_ECUDA: "BKS_ECUDA",
+             BKS_EASYM: "BKS_EASYM", BKS_ENOTCONV: "BKS_ENOTCONV",
+             BKS_EBREAKDOWN: "BKS_EBREAKDOWN", BKS_ENUMERIC: "BKS_ENUMERIC",
+             BKS_EUNSUPPORTED: "BKS_EUNSUPPORTED"}
+
+
+class BksError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("r1", ctypes.c_int), ("r3", ctypes.c_int), ("stages", ctypes.c_int),
+                ("block_p", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
+                ("variant", ctypes.c_int), ("precision", ctypes.c_int),
+                ("refine_sweeps", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("drop_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("mixed_tol", ctypes.c_double)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("grad_rel", ctypes.c_double), ("normF", ctypes.c_double),
+                ("k1", ctypes.c_int), ("k3", ctypes.c_int), ("inner_sweeps", ctypes.c_int),
+                ("fp32_iters", ctypes.c_int), ("seconds", ctypes.c_double),
+                ("history", ctypes.POINTER(ctypes.c_double)), ("history_cap", ctypes.c_int),
+                ("history_len", ctypes.c_int)]
+
+
+class _HooiParams(ctypes.Structure):
+    _fields_ = [("r1", ctypes.c_int), ("r3", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("grad_every", ctypes.c_int),
+                ("precision", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libbks_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run paper_2012_07595_gb300._build.build()")
+    L = ctypes.CDLL(path)
+    vp, i64, c_int, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.bks_tensor_create_coo.argtypes = [i64, i64, i64, vp, vp, vp, vp, c_int, c_int, vp,
+                                        ctypes.POINTER(vp)]
+    L.bks_tensor_create_coo.restype = c_int
+    L.bks_tensor_destroy.argtypes = [vp]
+    L.bks_tensor_destroy.restype = None
+    L.bks_tensor_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                  ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+    L.bks_tensor_info.restype = c_int
+    L.bks_tensor_export_coo.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.bks_tensor_export_coo.restype = c_int
+    L.bks_contract_mode1.argtypes = [vp, vp, i64, c_int, vp, i64, c_int, vp, i64, c_int, vp]
+    L.bks_contract_mode1.restype = c_int
+    L.bks_contract_mode3.argtypes = [vp, vp, i64, c_int, vp, i64, c_int, vp, i64, c_int, vp]
+    L.bks_contract_mode3.restype = c_int
+    L.bks_core.argtypes = [vp, vp, i64, c_int, vp, i64, c_int, vp, c_int, vp]
+    L.bks_core.restype = c_int
+    L.bks_params_default.argtypes = [ctypes.POINTER(_Params)]
+    L.bks_params_default.restype = None
+    L.hooi_params_default.argtypes = [ctypes.POINTER(_HooiParams)]
+    L.hooi_params_default.restype = None
+    L.bks_solve.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, vp, vp, vp,
+                            ctypes.POINTER(_Info), vp]
+    L.bks_solve.restype = c_int
+    L.hooi_solve.argtypes = [vp, ctypes.POINTER(_HooiParams), vp, vp, vp, vp, vp,
+                             ctypes.POINTER(_Info), vp]
+    L.hooi_solve.restype = c_int
+    L.bks_last_error_string.argtypes = []
+    L.bks_last_error_string.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int, allow=()):
+    if rc != BKS_OK and rc not in allow:
+        raise BksError(rc, lib().bks_last_error_string().decode())
+    return rc
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def col_major(x):
+    """The same torch matrix with column-major strides (a copy if needed)."""
+    if x.dim() == 1:
+        x = x.reshape(-1, 1)
+    if x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+        return x
+    return x.t().contiguous().t()
+
+
+def _ld(x) -> int:
+    return max(int(x.stride(1)), int(x.shape[0]), 1)
+
+
+def _dtype_code(x) -> int:
+    import torch
+    if x.dtype == torch.float64:
+        return BKS_F64
+    if x.dtype == torch.float32:
+        return BKS_F32
+    raise TypeError(f"unsupported dtype {x.dtype}")
+
+
+def _empty_cm(rows, cols, dtype, device):
+    import torch
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+class Tensor:
+    """Owning handle of a stored (1,2)-symmetric tensor."""
+
+    def __init__(self, handle: ctypes.c_void_p, vdtype: int):
+        self._h = handle
+        self.vdtype = vdtype
+        m, n, nnz, f2 = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().bks_tensor_info(self._h, ctypes.byref(m), ctypes.byref(n), ctypes.byref(nnz),
+                                     ctypes.byref(f2)))
+        self.m, self.n, self.nnz, self.fro2 = m.value, n.value, nnz.value, f2.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().bks_tensor_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bks_tensor_create_coo(m: int, n: int, i, j, k, v, mirror: bool = True,
+                          validate: bool = False, stream=None) -> Tensor:
+    """Create a stored tensor from COO entries.  i, j, k, v are numpy arrays
+    (host) or torch CUDA tensors (device); v is float32 or float64."""
+    import torch
+    flags = (BKS_MIRROR if mirror else 0) | (BKS_VALIDATE_SYMMETRIC if validate else 0)
+    keep = []
+    if isinstance(i, torch.Tensor):
+        flags |= BKS_INPUT_ON_DEVICE
+        ii, jj, kk = (x.to(torch.int32).contiguous() for x in (i, j, k))
+        vv = v.contiguous()
+        vdt = _dtype_code(vv)
+        ptrs = [x.data_ptr() for x in (ii, jj, kk, vv)]
+        keep = [ii, jj, kk, vv]
+        nnz = ii.numel()
+    else:
+        ii, jj, kk = (np.ascontiguousarray(x, dtype=np.int32) for x in (i, j, k))
+        vv = np.ascontiguousarray(v)
+        if vv.dtype == np.float64:
+            vdt = BKS_F64
+        elif vv.dtype == np.float32:
+            vdt = BKS_F32
+        else:
+            raise TypeError(f"unsupported value dtype {vv.dtype}")
+        ptrs = [x.ctypes.data if x.size else 0 for x in (ii, jj, kk, vv)]
+        keep = [ii, jj, kk, vv]
+        nnz = ii.size
+    h = ctypes.c_void_p()
+    _check(lib().bks_tensor_create_coo(m, n, nnz, *[ctypes.c_void_p(p) for p in ptrs], vdt, flags,
+                                       _stream(stream), ctypes.byref(h)))
+    del keep
+    return Tensor(h, vdt)
+
+
+def bks_tensor_destroy(t: Tensor):
+    t.close()
+
+
+def bks_tensor_info(t: Tensor):
+    return {"m": t.m, "n": t.n, "nnz_stored": t.nnz, "fro2": t.fro2}
+
+
+def bks_tensor_export_coo(t: Tensor, stream=None):
+    """Canonical stored entries (sorted by (i,k,j)) as torch CUDA tensors."""
+    import torch
+    dt = torch.float64 if t.vdtype == BKS_F64 else torch.float32
+    i = torch.empty(t.nnz, dtype=torch.int32, device="cuda")
+    j = torch.empty_like(i)
+    k = torch.empty_like(i)
+    v = torch.empty(t.nnz, dtype=dt, device="cuda")
+    _check(lib().bks_tensor_export_coo(t.handle, ctypes.c_void_p(i.data_ptr()),
+                                       ctypes.c_void_p(j.data_ptr()),
+                                       ctypes.c_void_p(k.data_ptr()),
+                                       ctypes.c_void_p(v.data_ptr()), _stream(stream)))
+    return i, j, k, v
+
+
+def bks_contract_mode1(t: Tensor, X, Y, out=None, stream=None):
+    """unfold_1(A.(X,Y)_{2,3}): m x (p q), column a + p b."""
+    X, Y = col_major(X), col_major(Y)
+    p, q = X.shape[1], Y.shape[1]
+    if out is None:
+        out = _empty_cm(t.m, p * q, X.dtype, X.device)
+    _check(lib().bks_contract_mode1(t.handle, ctypes.c_void_p(X.data_ptr()), _ld(X), p,
+                                    ctypes.c_void_p(Y.data_ptr()), _ld(Y), q,
+                                    ctypes.c_void_p(out.data_ptr()), _ld(out), _dtype_code(X),
+                                    _stream(stream)))
+    return out
+
+
+def bks_contract_mode3(t: Tensor, X, X2=None, out=None, stream=None):
+    """unfold_3(A.(X,X2)_{1,2}): n x (p q); X2 None -> triangle n x p(p+1)/2."""
+    X = col_major(X)
+    p = X.shape[1]
+    if X2 is not None:
+        X2 = col_major(X2)
+        q = X2.shape[1]
+        w = p * q
+        x2p, ld2 = ctypes.c_void_p(X2.data_ptr()), _ld(X2)
+    else:
+        q, w = p, p * (p + 1) // 2
+        x2p, ld2 = ctypes.c_void_p(0), t.m
+    if out is None:
+        out = _empty_cm(t.n, w, X.dtype, X.device)
+    _check(lib().bks_contract_mode3(t.handle, ctypes.c_void_p(X.data_ptr()), _ld(X), p, x2p, ld2,
+                                    q, ctypes.c_void_p(out.data_ptr()), _ld(out),
+                                    _dtype_code(X), _stream(stream)))
+    return out
+
+
+def bks_core(t: Tensor, U, W, stream=None):
+    """A.(U,U,W) as an r1 x r1 x r3 tensor (torch, column-major flattening)."""
+    import torch
+    U, W = col_major(U), col_major(W)
+    r1, r3 = U.shape[1], W.shape[1]
+    F = torch.empty(r1 * r1 * r3, dtype=U.dtype, device=U.device)
+    _check(lib().bks_core(t.handle, ctypes.c_void_p(U.data_ptr()), _ld(U), r1,
+                          ctypes.c_void_p(W.data_ptr()), _ld(W), r3,
+                          ctypes.c_void_p(F.data_ptr()), _dtype_code(U), _stream(stream)))
+    return F.reshape(r3, r1, r1).permute(2, 1, 0)
+
+
+@dataclasses.dataclass
+class BksParams:
+    r1: int = 2
+    r3: int = 2
+    stages: int = 2
+    block_p: int = 4
+    tol: float = 1e-10
+    max_outer: int = 500
+    max_inner: int = 1000
+    variant: int = BKS_VARIANT_BK
+    precision: int = BKS_PREC_FP64
+    refine_sweeps: int = 1
+    seed: int = 1
+    drop_tol: float = 1e-12
+    inner_tol: float = 0.0
+    mixed_tol: float = 1e-6
+
+    def to_c(self) -> _Params:
+        p = _Params()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+@dataclasses.dataclass
+class HooiParams:
+    r1: int = 2
+    r3: int = 2
+    tol: float = 1e-10
+    max_iter: int = 5000
+    grad_every: int = 10
+    precision: int = BKS_PREC_FP64
+    seed: int = 1
+
+    def to_c(self) -> _HooiParams:
+        p = _HooiParams()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+def _solve(fn, t: Tensor, cparams, r1, r3, U0, W0, stream, history_cap, raise_notconv):
+    import torch
+    U = _empty_cm(t.m, r1, torch.float64, "cuda")
+    W = _empty_cm(t.n, r3, torch.float64, "cuda")
+    F = torch.empty(r1 * r1 * r3, dtype=torch.float64, device="cuda")
+    hist = (ctypes.c_double * (2 * max(history_cap, 1)))()
+    info = _Info()
+    info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    info.history_cap = history_cap
+    # starts must be column-major with ld = rows
+    u0 = U0.to(device="cuda", dtype=torch.float64).t().contiguous().t() if U0 is not None else None
+    w0 = W0.to(device="cuda", dtype=torch.float64).t().contiguous().t() if W0 is not None else None
+    rc = fn(t.handle, ctypes.byref(cparams),
+            ctypes.c_void_p(u0.data_ptr() if u0 is not None else 0),
+            ctypes.c_void_p(w0.data_ptr() if w0 is not None else 0),
+            ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(W.data_ptr()),
+            ctypes.c_void_p(F.data_ptr()), ctypes.byref(info), _stream(stream))
+    _check(rc, allow=() if raise_notconv else (BKS_ENOTCONV,))
+    out = {"iters": info.iters, "converged": bool(info.converged), "grad_rel": info.grad_rel,
+           "normF": info.normF, "k1": info.k1, "k3": info.k3,
+           "inner_sweeps": info.inner_sweeps, "fp32_iters": info.fp32_iters,
+           "seconds": info.seconds, "status": rc,
+           "history": [(hist[2 * q], hist[2 * q + 1]) for q in range(info.history_len)]}
+    return U, W, F.reshape(r3, r1, r1).permute(2, 1, 0), out
+
+
+def bks_solve(t: Tensor, params: Optional[BksParams] = None, U0=None, W0=None, stream=None,
+              history_cap: int = 1000, raise_notconv: bool = False):
+    """Tensor Krylov-Schur (Algorithm 5).  Returns (U, W, F, info) with U
+    (m x r1), W (n x r3) FP64 CUDA tensors and F (r1 x r1 x r3)."""
+    params = params or BksParams()
+    return _solve(lib().bks_solve, t, params.to_c(), params.r1, params.r3, U0, W0, stream,
+                  history_cap, raise_notconv)
+
+
+def hooi_solve(t: Tensor, params: Optional[HooiParams] = None, U0=None, W0=None, stream=None,
+               history_cap: int = 1000, raise_notconv: bool = False):
+    """HOOI for (1,2)-symmetric tensors (Section 6.1)."""
+    params = params or HooiParams()
+    return _solve(lib().hooi_solve, t, params.to_c(), params.r1, params.r3, U0, W0, stream,
+                  history_cap, raise_notconv)

@@ -1,0 +1,186 @@
+// Shared internals of the GB300 BKS library: error state, device buffers,
+// the stored-tensor layout and the launch helpers used by every .cu file.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/bks.h"
+
+namespace bks {
+
+// ---- error handling (thread-local message, status codes of bks.h) -------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+struct Status {
+  int code = BKS_OK;
+  std::string msg;
+};
+
+#define BKS_CUDA_TRY(expr)                                                   \
+  do {                                                                       \
+    cudaError_t e_ = (expr);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      return ::bks::fail(e_ == cudaErrorMemoryAllocation ? BKS_ENOMEM        \
+                                                         : BKS_ECUDA,        \
+                         std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    }                                                                        \
+  } while (0)
+
+#define BKS_TRY(expr)            \
+  do {                           \
+    int r_ = (expr);             \
+    if (r_ != BKS_OK) return r_; \
+  } while (0)
+
+// ---- device memory owned by the library ----------------------------------
+// Allocations go through cudaMallocAsync on the call's stream so that
+// temporaries are stream-ordered.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; bytes = o.bytes; s = o.s;
+      o.p = nullptr; o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  int alloc(size_t nbytes, cudaStream_t stream) {
+    release();
+    s = stream;
+    bytes = nbytes;
+    if (nbytes == 0) return BKS_OK;
+    BKS_CUDA_TRY(cudaMallocAsync(&p, nbytes, stream));
+    return BKS_OK;
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+  }
+  // long-lived buffers are freed on the legacy stream (the allocating
+  // stream may be gone by then)
+  void persist() { s = nullptr; }
+  template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// ---- stored tensor layout -------------------------------------------------
+// Work tiles of the sparse contractions.  A row longer than kSplit entries
+// is cut into "virtual rows" of at most kSplit entries; tile t of a part
+// holds the virtual rows whose first entry lies in [t*kTile, (t+1)*kTile),
+// so a tile spans at most kTile + kSplit entries and never cuts a virtual
+// row.  One warp processes one tile.
+constexpr int kTile = 512;
+constexpr int kSplit = 512;
+
+struct Part {
+  // one sorted copy of the stored entries, CSR over `rows`
+  int64_t rows = 0;
+  DevBuf ptr;      // int32 [rows+1]
+  DevBuf c0;       // int32 [nnz]: mode-1 copy -> k, mode-3 copy -> i
+  DevBuf c1;       // int32 [nnz]: j
+  DevBuf v;        // [nnz] in the input value dtype
+  DevBuf v32;      // float [nnz] when the input dtype is double
+  DevBuf v64;      // double [nnz] when the input dtype is float
+  // tile plan
+  int32_t nv = 0, ntiles = 0, nslots = 0, nsplit = 0;
+  DevBuf vptr;        // int32 [nv+1]   first entry of each virtual row
+  DevBuf vrow;        // int32 [nv]     row of each virtual row
+  DevBuf vslot;       // int32 [nv]     partial-sum slot, -1 if the row is not cut
+  DevBuf tile_first;  // int32 [ntiles+1] first virtual row of each tile
+  DevBuf split_row;   // int32 [nsplit]   rows that were cut
+  DevBuf split_first; // int32 [nsplit+1] their first slot (slots are consecutive)
+  int32_t nempty = 0;
+  DevBuf empty_rows;  // int32 [nempty] rows without entries (their output is zero)
+  std::vector<int32_t> host_ptr;  // host copy of ptr (kept for the mode-3 copy only)
+  void persist() {
+    for (DevBuf* b : {&ptr, &c0, &c1, &v, &v32, &v64, &vptr, &vrow, &vslot, &tile_first,
+                      &split_row, &split_first, &empty_rows})
+      b->persist();
+  }
+};
+
+}  // namespace bks
+
+struct bks_tensor {
+  int64_t m = 0, n = 0, nnz = 0;
+  int vdtype = BKS_F64;
+  double fro2 = 0.0;
+  bks::Part m1;   // sorted by (i, k, j): rows i, columns (k, j)
+  bks::Part m3;   // sorted by (k, i, j): rows k, columns (i, j)
+};
+
+namespace bks {
+
+// exact IEEE adds (no contraction into FMA) and bitwise equality
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ bool same_bits(float a, float b) {
+  return __float_as_uint(a) == __float_as_uint(b);
+}
+__device__ __forceinline__ bool same_bits(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int num_sms() {
+  static int s = -1;
+  if (s < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    if (s <= 0) s = 1;
+  }
+  return s;
+}
+
+// ---- scans (scan.cu) ------------------------------------------------------
+// out[i] = sum_{t<i} in[i]; out may alias in; total (device) optional.
+int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t count,
+                       int32_t* total_dev, cudaStream_t s);
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t count,
+                       int64_t* total_dev, cudaStream_t s);
+// stable LSD radix sort of (key, payload) by the low `bits` bits of key
+int radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t count, int bits,
+                     cudaStream_t s);
+
+// ---- tile plans (ingest.cu) -----------------------------------------------
+int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s);
+
+// ---- contractions (contract.cu) ------------------------------------------
+// Row-major padded "gather" copies of the dense operands are built inside.
+int contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
+                   const void* Y, int64_t ldy, int q, void* out, int64_t ldo,
+                   int dtype, cudaStream_t s);
+int contract_mode3(const bks_tensor* t, const void* X, int64_t ldx, int p,
+                   const void* X2, int64_t ldx2, int q, void* out, int64_t ldo,
+                   int dtype, cudaStream_t s);
+int contract_core(const bks_tensor* t, const void* U, int64_t ldu, int r1,
+                  const void* W, int64_t ldw, int r3, void* F, int dtype,
+                  cudaStream_t s);
+// FP64 operands/results; fp32 selects FP32 arithmetic (the mixed form)
+int contract_mode1_x(const bks_tensor* t, const double* X, int64_t ldx, int p, const double* Y,
+                     int64_t ldy, int q, double* out, int64_t ldo, bool fp32, cudaStream_t s);
+int contract_mode3_x(const bks_tensor* t, const double* X, int64_t ldx, int p, const double* X2,
+                     int64_t ldx2, int q, double* out, int64_t ldo, bool fp32, cudaStream_t s);
+int contract_core_x(const bks_tensor* t, const double* U, int64_t ldu, int r1, const double* W,
+                    int64_t ldw, int r3, double* F, bool fp32, cudaStream_t s);
+// inner solve (inner.cu)
+int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int max_inner,
+                double* Uh, double* Wh, double* negU, double* negW, double* info,
+                cudaStream_t s);
+
+}  // namespace bks

@@ -1,0 +1,672 @@
+// Sparse tensor x dense block contractions (Section 2.2; Algorithm 3 step
+// (i); Section 4.3.1) and the cores F = A.(U,U,W), C = A.(X,X,Z)
+// (eq. (Rayleigh), eq. (tkd)).
+//
+// Layout.  The stored tensor has two sorted copies: rows i (entries sorted
+// by (k, j) inside a row) for the mode-1 contraction, and rows k (sorted by
+// (i, j)) for the mode-3 contraction and the cores.  A contraction writes
+// one output row per tensor row, so the work is a segmented reduction over
+// the entries of each row:
+//
+//   out_row[a + p*b] = sum over the row's entries e of v_e * A[ia_e, a] * B[ib_e, b]
+//
+// with (A, ia, B, ib) = (X, j, Y, k) for mode 1 and (X, i, X2, j) for mode 3.
+//
+// Kernel design (one warp per tile of <= kTile + kSplit consecutive
+// entries, see common.cuh): each lane takes a contiguous run of the tile's
+// entries and accumulates PB x QB products in registers.  Rows (virtual
+// rows) that cross lanes are combined by a segmented suffix sum over the
+// lanes (shuffles, fixed order); rows longer than kSplit write per-piece
+// partial sums that a second kernel adds in a fixed order.  No atomics:
+// the result is bitwise reproducible.  The dense operands are gathered from
+// row-major copies padded to PB (QB) columns, built by a pack kernel, so
+// one entry costs one 8-32 byte gather per operand.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace bks {
+
+namespace {
+
+template <typename T, int W> struct VecLoad;
+
+// ---- pack a column-major m x p block into row-major m x PB (zero padded)
+template <typename IT, typename T>
+__global__ void k_pack(const IT* __restrict__ X, int64_t ldx, int64_t rows, int p, int PB,
+                       T* __restrict__ out) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    for (int a = 0; a < PB; ++a) out[r * PB + a] = a < p ? (T)X[r + ldx * a] : T(0);
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void load_row(const T* __restrict__ base, T (&x)[N]) {
+  // 8/16-byte vector loads of a padded row
+  if constexpr (sizeof(T) * N % 16 == 0) {
+#pragma unroll
+    for (int t = 0; t < (int)(sizeof(T) * N / 16); ++t) {
+      float4 q = __ldg(reinterpret_cast<const float4*>(base) + t);
+      const T* qq = reinterpret_cast<const T*>(&q);
+#pragma unroll
+      for (int u = 0; u < (int)(16 / sizeof(T)); ++u) x[t * (16 / sizeof(T)) + u] = qq[u];
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < N; ++t) x[t] = __ldg(base + t);
+  }
+}
+
+// accumulator shape: TRI -> upper triangle of PB x PB, else PB x QB
+template <int PB, int QB, bool TRI>
+struct Shape {
+  static constexpr int W = TRI ? PB * (PB + 1) / 2 : PB * QB;
+};
+
+template <typename T, int PB, int QB, bool TRI>
+__device__ __forceinline__ void accumulate(T (&acc)[Shape<PB, QB, TRI>::W], T v,
+                                           const T (&xa)[PB], const T (&xb)[TRI ? PB : QB]) {
+  T va[PB];
+#pragma unroll
+  for (int a = 0; a < PB; ++a) va[a] = v * xa[a];
+  if constexpr (TRI) {
+#pragma unroll
+    for (int b = 0; b < PB; ++b)
+#pragma unroll
+      for (int a = 0; a <= b; ++a) acc[a + b * (b + 1) / 2] = fma(va[a], xb[b], acc[a + b * (b + 1) / 2]);
+  } else {
+#pragma unroll
+    for (int b = 0; b < QB; ++b)
+#pragma unroll
+      for (int a = 0; a < PB; ++a) acc[a + PB * b] = fma(va[a], xb[b], acc[a + PB * b]);
+  }
+}
+
+struct TileArgs {
+  const int32_t* tile_first;
+  const int32_t* vptr;
+  const int32_t* vrow;
+  const int32_t* vslot;
+  int32_t ntiles;
+  const int32_t* ia;   // index into operand A per entry
+  const int32_t* ib;   // index into operand B per entry
+};
+
+// Sum of the entries [lo, hi) of the tile's data into acc.
+template <typename T, int PB, int QB, bool TRI>
+__device__ __forceinline__ void run_entries(int lo, int hi, const TileArgs& ta,
+                                            const T* __restrict__ vals,
+                                            const T* __restrict__ Ap,
+                                            const T* __restrict__ Bp,
+                                            T (&acc)[Shape<PB, QB, TRI>::W]) {
+  constexpr int NB = TRI ? PB : QB;
+  int last_a = -1;
+  T xa[PB];
+#pragma unroll
+  for (int a = 0; a < PB; ++a) xa[a] = T(0);
+  for (int e = lo; e < hi; ++e) {
+    const int ia = __ldg(ta.ia + e);
+    const int ib = __ldg(ta.ib + e);
+    const T v = __ldg(vals + e);
+    if (ia != last_a) {
+      load_row<T, PB>(Ap + (int64_t)ia * PB, xa);
+      last_a = ia;
+    }
+    T xb[NB];
+    load_row<T, NB>(Bp + (int64_t)ib * NB, xb);
+    accumulate<T, PB, QB, TRI>(acc, v, xa, xb);
+  }
+}
+
+template <typename T, typename OT, int PB, int QB, bool TRI>
+__device__ __forceinline__ void flush_row(int vr, const TileArgs& ta,
+                                          const T (&acc)[Shape<PB, QB, TRI>::W], int p, int q,
+                                          OT* __restrict__ out, int64_t ldo,
+                                          T* __restrict__ partial) {
+  constexpr int W = Shape<PB, QB, TRI>::W;
+  const int slot = __ldg(ta.vslot + vr);
+  if (slot >= 0) {
+    T* dst = partial + (int64_t)slot * W;
+#pragma unroll
+    for (int c = 0; c < W; ++c) dst[c] = acc[c];
+    return;
+  }
+  const int64_t row = __ldg(ta.vrow + vr);
+  if constexpr (TRI) {
+#pragma unroll
+    for (int b = 0; b < PB; ++b)
+#pragma unroll
+      for (int a = 0; a <= b; ++a)
+        if (b < p) out[row + ldo * (a + b * (b + 1) / 2)] = (OT)acc[a + b * (b + 1) / 2];
+  } else {
+#pragma unroll
+    for (int b = 0; b < QB; ++b)
+#pragma unroll
+      for (int a = 0; a < PB; ++a)
+        if (a < p && b < q) out[row + ldo * (a + p * b)] = (OT)acc[a + PB * b];
+  }
+}
+
+__device__ __forceinline__ int upper_vrow(const int32_t* __restrict__ vptr, int lo, int hi,
+                                          int e) {
+  // largest v in [lo, hi) with vptr[v] <= e
+  int a = lo, b = hi;
+  while (b - a > 1) {
+    int mid = (a + b) >> 1;
+    if (__ldg(vptr + mid) <= e) a = mid; else b = mid;
+  }
+  return a;
+}
+
+template <typename T, typename OT, int PB, int QB, bool TRI>
+__global__ void __launch_bounds__(256)
+k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
+           const T* __restrict__ Bp, int p, int q, OT* __restrict__ out, int64_t ldo,
+           T* __restrict__ partial) {
+  constexpr int W = Shape<PB, QB, TRI>::W;
+  const int lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (tile >= ta.ntiles) return;
+  const int v0 = __ldg(ta.tile_first + tile), v1 = __ldg(ta.tile_first + tile + 1);
+  if (v0 >= v1) return;
+  const int e0 = __ldg(ta.vptr + v0), e1 = __ldg(ta.vptr + v1);
+  const int per = (e1 - e0 + 31) >> 5;
+  const int lo = min(e1, e0 + lane * per), hi = min(e1, lo + per);
+  const bool has = lo < hi;
+
+  int vf = -1, vl = -1;
+  bool head = false, open_tail = false;
+  if (has) {
+    vf = upper_vrow(ta.vptr, v0, v1, lo);
+    vl = upper_vrow(ta.vptr, vf, v1, hi - 1);
+    head = __ldg(ta.vptr + vf) < lo;
+    open_tail = __ldg(ta.vptr + vl + 1) > hi && !(head && vl == vf);
+  }
+  T acc[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) acc[c] = T(0);
+  // phase A: the head piece (a row that began in an earlier lane)
+  if (head) {
+    int hend = min(hi, __ldg(ta.vptr + vf + 1));
+    run_entries<T, PB, QB, TRI>(lo, hend, ta, vals, Ap, Bp, acc);
+  }
+  // phase B: segmented suffix sum of head pieces over lanes (key = row)
+  int key = head ? vf : -1 - lane;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int ok = __shfl_down_sync(0xffffffffu, key, o);
+    bool take = (lane + o < 32) && ok == key;
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      T other = __shfl_down_sync(0xffffffffu, acc[c], o);
+      if (take) acc[c] += other;
+    }
+  }
+  // the owner of an open tail starts from the sum of the later lanes' heads
+  int nkey = __shfl_down_sync(0xffffffffu, key, 1);
+  bool carry = open_tail && lane < 31 && nkey == vl;
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    T other = __shfl_down_sync(0xffffffffu, acc[c], 1);
+    acc[c] = carry ? other : T(0);
+  }
+  if (!has) return;
+  // phase C1: the open tail (owned, continues into later lanes)
+  if (open_tail) {
+    run_entries<T, PB, QB, TRI>(__ldg(ta.vptr + vl), hi, ta, vals, Ap, Bp, acc);
+    flush_row<T, OT, PB, QB, TRI>(vl, ta, acc, p, q, out, ldo, partial);
+  }
+  // phase C2: owned rows that end inside this lane
+  const int first_owned = head ? vf + 1 : vf;
+  const int last_owned = open_tail ? vl - 1 : vl;
+  for (int v = first_owned; v <= last_owned; ++v) {
+#pragma unroll
+    for (int c = 0; c < W; ++c) acc[c] = T(0);
+    run_entries<T, PB, QB, TRI>(__ldg(ta.vptr + v), __ldg(ta.vptr + v + 1), ta, vals, Ap, Bp,
+                                acc);
+    flush_row<T, OT, PB, QB, TRI>(v, ta, acc, p, q, out, ldo, partial);
+  }
+}
+
+// Rows cut into pieces: add the pieces' partial sums in a fixed order.
+template <typename T, typename OT, int PB, int QB, bool TRI>
+__global__ void k_split_reduce(const int32_t* __restrict__ split_row,
+                               const int32_t* __restrict__ split_first, int nsplit,
+                               const T* __restrict__ partial, int p, int q, OT* __restrict__ out,
+                               int64_t ldo) {
+  constexpr int W = Shape<PB, QB, TRI>::W;
+  __shared__ T sh[256];
+  const int s = blockIdx.x;
+  if (s >= nsplit) return;
+  const int f0 = split_first[s], f1 = split_first[s + 1];
+  const int groups = 256 / W;
+  const int c = threadIdx.x % W, g = threadIdx.x / W;
+  T acc = T(0);
+  if (g < groups)
+    for (int f = f0 + g; f < f1; f += groups) acc += partial[(int64_t)f * W + c];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < W) {
+    T tot = T(0);
+    for (int t = 0; t < groups; ++t) tot += sh[t * W + threadIdx.x];
+    const int64_t row = split_row[s];
+    int col = -1;
+    if constexpr (TRI) {
+      int b = 0;
+      while ((b + 1) * (b + 2) / 2 <= c) ++b;
+      if (b < p) col = c;
+    } else {
+      int a = c % PB, b = c / PB;
+      if (a < p && b < q) col = a + p * b;
+    }
+    if (col >= 0) out[row + ldo * col] = (OT)tot;
+  }
+}
+
+template <typename T>
+__global__ void k_zero_rows(const int32_t* __restrict__ rows, int nrows, int w,
+                            T* __restrict__ out, int64_t ldo) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nrows * w;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(t % nrows), c = (int)(t / nrows);
+    out[rows[r] + ldo * c] = T(0);
+  }
+}
+
+inline int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 32));
+}
+
+inline int bucket(int x) { return x <= 2 ? 2 : (x <= 4 ? 4 : 8); }
+
+template <typename T> const T* values_of(const Part& P, int vdtype);
+template <> const float* values_of<float>(const Part& P, int vdtype) {
+  return vdtype == BKS_F32 ? P.v.as<float>() : P.v32.as<float>();
+}
+template <> const double* values_of<double>(const Part& P, int vdtype) {
+  return vdtype == BKS_F64 ? P.v.as<double>() : P.v64.as<double>();
+}
+
+// One launch pair (tile kernel + piece reduction) for fixed buckets.
+template <typename T, typename OT, int PB, int QB, bool TRI>
+int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib,
+                    const T* Ap, const T* Bp, int p, int q, OT* out, int64_t ldo,
+                    cudaStream_t s) {
+  constexpr int W = Shape<PB, QB, TRI>::W;
+  TileArgs ta{P.tile_first.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
+              P.vslot.as<int32_t>(), P.ntiles, ia, ib};
+  DevBuf partial;
+  if (P.nslots > 0) BKS_TRY(partial.alloc(sizeof(T) * (size_t)P.nslots * W, s));
+  const int warps = 8;
+  const int blocks = (P.ntiles + warps - 1) / warps;
+  if (P.nv > 0) {
+    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,
+                                                                 Bp, p, q, out, ldo, partial.as<T>());
+    BKS_CUDA_TRY(cudaGetLastError());
+  }
+  if (P.nsplit > 0) {
+    k_split_reduce<T, OT, PB, QB, TRI><<<P.nsplit, 256, 0, s>>>(
+        P.split_row.as<int32_t>(), P.split_first.as<int32_t>(), P.nsplit, partial.as<T>(), p, q,
+        out, ldo);
+    BKS_CUDA_TRY(cudaGetLastError());
+  }
+  if (P.nempty > 0) {
+    const int w = TRI ? p * (p + 1) / 2 : p * q;
+    k_zero_rows<OT><<<grid_for((int64_t)P.nempty * w), 256, 0, s>>>(P.empty_rows.as<int32_t>(),
+                                                                    P.nempty, w, out, ldo);
+    BKS_CUDA_TRY(cudaGetLastError());
+  }
+  return BKS_OK;
+}
+
+template <typename T, typename OT>
+int dispatch(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib, const T* Ap,
+             int PB, const T* Bp, int QB, bool tri, int p, int q, OT* out, int64_t ldo,
+             cudaStream_t s) {
+#define BKS_CASE(pb, qb)                                                                      \
+  if (!tri && PB == pb && QB == qb)                                                           \
+    return launch_contract<T, OT, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, out, ldo, s);
+  BKS_CASE(2, 2) BKS_CASE(2, 4) BKS_CASE(2, 8) BKS_CASE(4, 2) BKS_CASE(4, 4) BKS_CASE(4, 8)
+  BKS_CASE(8, 2) BKS_CASE(8, 4)
+#undef BKS_CASE
+  if (tri && PB == 2) return launch_contract<T, OT, 2, 2, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
+  if (tri && PB == 4) return launch_contract<T, OT, 4, 4, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
+  if (tri && PB == 8) return launch_contract<T, OT, 8, 8, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
+  return fail(BKS_EUNSUPPORTED, "contraction bucket not instantiated");
+}
+
+template <typename T, typename IT>
+int pack(const IT* X, int64_t ldx, int64_t rows, int p, int PB, DevBuf& buf, cudaStream_t s) {
+  BKS_TRY(buf.alloc(sizeof(T) * (size_t)rows * PB, s));
+  k_pack<IT, T><<<grid_for(rows), 256, 0, s>>>(X, ldx, rows, p, PB, buf.as<T>());
+  BKS_CUDA_TRY(cudaGetLastError());
+  return BKS_OK;
+}
+
+template <typename T, typename IT, typename OT>
+int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* Y, int64_t ldy,
+                int q, OT* out, int64_t ldo, cudaStream_t s) {
+  const int PB = bucket(p);
+  // keep PB*QB <= 32: split the Y columns into chunks of at most 4 when PB = 8
+  const int qchunk = PB == 8 ? 4 : 8;
+  DevBuf Xp;
+  BKS_TRY((pack<T, IT>(X, ldx, t->m, p, PB, Xp, s)));
+  for (int q0 = 0; q0 < q; q0 += qchunk) {
+    const int qq = std::min(qchunk, q - q0);
+    const int QB = bucket(qq);
+    DevBuf Yp;
+    BKS_TRY((pack<T, IT>(Y + ldy * q0, ldy, t->n, qq, QB, Yp, s)));
+    // columns a + p*(q0 + b) of the full output start at column p*q0
+    BKS_TRY((dispatch<T, OT>(t->m1, t->vdtype, t->m1.c1.as<int32_t>(), t->m1.c0.as<int32_t>(),
+                        Xp.as<T>(), PB, Yp.as<T>(), QB, false, p, qq, out + ldo * (p * q0), ldo,
+                        s)));
+  }
+  return BKS_OK;
+}
+
+template <typename T, typename IT, typename OT>
+int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* X2, int64_t ldx2,
+                int q, OT* out, int64_t ldo, cudaStream_t s) {
+  const int PB = bucket(p);
+  DevBuf Xp;
+  BKS_TRY((pack<T, IT>(X, ldx, t->m, p, PB, Xp, s)));
+  if (!X2)
+    return dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
+                       Xp.as<T>(), PB, Xp.as<T>(), PB, true, p, p, out, ldo, s);
+  const int qchunk = PB == 8 ? 4 : 8;
+  for (int q0 = 0; q0 < q; q0 += qchunk) {
+    const int qq = std::min(qchunk, q - q0);
+    const int QB = bucket(qq);
+    DevBuf X2p;
+    BKS_TRY((pack<T, IT>(X2 + ldx2 * q0, ldx2, t->m, qq, QB, X2p, s)));
+    BKS_TRY((dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
+                        Xp.as<T>(), PB, X2p.as<T>(), QB, false, p, qq, out + ldo * (p * q0), ldo,
+                        s)));
+  }
+  return BKS_OK;
+}
+
+// ---- cores ----------------------------------------------------------------
+// Small rank (r1 <= 8): F[a,b,c] = sum_k W[k,c] T[k, tri(a,b)] with T the
+// triangle mode-3 contraction A.(U,U)_{1,2}.
+template <typename T, typename IT, typename OT>
+__global__ void k_core_from_tri(const T* __restrict__ Tm, int64_t n, int r1, const IT* __restrict__ W,
+                                int64_t ldw, int r3, OT* __restrict__ F) {
+  const int ntri = r1 * (r1 + 1) / 2;
+  for (int o = blockIdx.x; o < ntri * r3; o += gridDim.x) {
+    const int tcol = o % ntri, c = o / ntri;
+    __shared__ T sh[256];
+    T acc = T(0);
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) acc += (T)W[k + ldw * c] * Tm[k + n * tcol];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      int b = 0;
+      while ((b + 1) * (b + 2) / 2 <= tcol) ++b;
+      const int a = tcol - b * (b + 1) / 2;
+      F[a + r1 * (b + r1 * c)] = (OT)sh[0];
+      F[b + r1 * (a + r1 * c)] = (OT)sh[0];
+    }
+    __syncthreads();
+  }
+}
+
+// Large rank (the Krylov core C = A.(X,X,Z), k1 up to 128): per chunk of
+// one slice k, M = sum_e v_e X[i_e,:]^T X[j_e,:] accumulated in registers
+// as 4x4 tiles of the upper block triangle; chunk partials are combined
+// with Z in a second kernel, C[a,b,c] = sum_chunk Z[k_chunk, c] M_chunk[a,b].
+constexpr int kCoreThreads = 256;
+constexpr int kCoreBatch = 32;
+constexpr int kCoreTiles = 3;     // tiles per thread: (k1/4)(k1/4+1)/2 <= 768 -> k1 <= 128
+
+template <typename T>
+__global__ void __launch_bounds__(kCoreThreads)
+k_core_chunks(const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ chunk_hi,
+              const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
+              const T* __restrict__ vals, const T* __restrict__ Xp, int K, int KP,
+              T* __restrict__ Mpart) {
+  extern __shared__ unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);          // [kCoreBatch][KP]
+  T* Bs = As + kCoreBatch * KP;                     // [kCoreBatch][KP]
+  const int ch = blockIdx.x;
+  const int lo = chunk_lo[ch], hi = chunk_hi[ch];
+  const int nt = KP / 4;                            // tiles per side
+  const int ntiles = nt * (nt + 1) / 2;
+  int ta[kCoreTiles], tb[kCoreTiles];
+#pragma unroll
+  for (int u = 0; u < kCoreTiles; ++u) {
+    int id = threadIdx.x + u * kCoreThreads;
+    ta[u] = -1; tb[u] = -1;
+    if (id < ntiles) {
+      int b = 0;
+      while ((b + 1) * (b + 2) / 2 <= id) ++b;
+      ta[u] = id - b * (b + 1) / 2;
+      tb[u] = b;
+    }
+  }
+  T acc[kCoreTiles][4][4];
+#pragma unroll
+  for (int u = 0; u < kCoreTiles; ++u)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[u][x][y] = T(0);
+  for (int base = lo; base < hi; base += kCoreBatch) {
+    const int cnt = min(kCoreBatch, hi - base);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kCoreBatch * KP; t += kCoreThreads) {
+      const int e = t / KP, a = t % KP;
+      T va = T(0), vb = T(0);
+      if (e < cnt) {
+        const int idx = base + e;
+        va = vals[idx] * Xp[(int64_t)ii[idx] * KP + a];
+        vb = Xp[(int64_t)jj[idx] * KP + a];
+      }
+      As[e * KP + a] = va;
+      Bs[e * KP + a] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kCoreTiles; ++u) {
+      if (ta[u] < 0) continue;
+      for (int e = 0; e < cnt; ++e) {
+        T xa[4], xb[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) xa[x] = As[e * KP + ta[u] * 4 + x];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) xb[y] = Bs[e * KP + tb[u] * 4 + y];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[u][x][y] = fma(xa[x], xb[y], acc[u][x][y]);
+      }
+    }
+  }
+  T* dst = Mpart + (int64_t)ch * K * K;
+#pragma unroll
+  for (int u = 0; u < kCoreTiles; ++u) {
+    if (ta[u] < 0) continue;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int a = ta[u] * 4 + x, b = tb[u] * 4 + y;
+        if (a < K && b < K && a <= b) dst[a + (int64_t)K * b] = acc[u][x][y];
+      }
+  }
+}
+
+// C[a,b,c] = sum_chunk Z[k_chunk, c] M_chunk[min(a,b), max(a,b)]
+template <typename T, typename IT, typename OT>
+__global__ void k_core_combine(const T* __restrict__ Mpart, const int32_t* __restrict__ chunk_k,
+                               int nchunks, int K, const IT* __restrict__ Z, int64_t ldz, int r3,
+                               OT* __restrict__ C) {
+  const int64_t total = (int64_t)K * (K + 1) / 2 * r3;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int ntri = K * (K + 1) / 2;
+    const int tcol = (int)(o % ntri), c = (int)(o / ntri);
+    int b = 0;
+    while ((b + 1) * (b + 2) / 2 <= tcol) ++b;
+    const int a = tcol - b * (b + 1) / 2;
+    T acc = T(0);
+    for (int ch = 0; ch < nchunks; ++ch)
+      acc += (T)Z[chunk_k[ch] + ldz * c] * Mpart[(int64_t)ch * K * K + a + (int64_t)K * b];
+    C[a + (int64_t)K * (b + (int64_t)K * c)] = (OT)acc;
+    C[b + (int64_t)K * (a + (int64_t)K * c)] = (OT)acc;
+  }
+}
+
+template <typename T, typename IT, typename OT>
+int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* W, int64_t ldw,
+               int r3, OT* F, cudaStream_t s) {
+  if (r1 <= 8) {
+    const int ntri = r1 * (r1 + 1) / 2;
+    DevBuf Tm;
+    BKS_TRY(Tm.alloc(sizeof(T) * (size_t)t->n * ntri, s));
+    BKS_TRY((mode3_typed<T, IT, T>(t, U, ldu, r1, nullptr, 0, r1, Tm.as<T>(), t->n, s)));
+    k_core_from_tri<T, IT, OT><<<std::min(ntri * r3, 1024), 256, 0, s>>>(Tm.as<T>(), t->n, r1, W,
+                                                                         ldw, r3, F);
+    BKS_CUDA_TRY(cudaGetLastError());
+    return BKS_OK;
+  }
+  if (r1 > 128) return fail(BKS_EUNSUPPORTED, "core rank above 128");
+  const int KP = (r1 + 3) / 4 * 4;
+  const Part& P = t->m3;
+  // chunks: each slice k cut into pieces of about nnz / (4 * SMs) entries
+  const int64_t target = std::max<int64_t>(256, t->nnz / (4LL * num_sms()) + 1);
+  std::vector<int32_t> lo, hi, kk;
+  for (int64_t k = 0; k < t->n; ++k) {
+    const int32_t a = P.host_ptr[k], b = P.host_ptr[k + 1];
+    for (int64_t x = a; x < b; x += target) {
+      lo.push_back((int32_t)x);
+      hi.push_back((int32_t)std::min<int64_t>(b, x + target));
+      kk.push_back((int32_t)k);
+    }
+  }
+  const int nch = (int)lo.size();
+  if (nch == 0) {
+    BKS_CUDA_TRY(cudaMemsetAsync(F, 0, sizeof(OT) * (size_t)r1 * r1 * r3, s));
+    return BKS_OK;
+  }
+  DevBuf dlo, dhi, dk, Xp, Mp;
+  BKS_TRY(dlo.alloc(4 * nch, s));
+  BKS_TRY(dhi.alloc(4 * nch, s));
+  BKS_TRY(dk.alloc(4 * nch, s));
+  BKS_CUDA_TRY(cudaMemcpyAsync(dlo.p, lo.data(), 4 * nch, cudaMemcpyHostToDevice, s));
+  BKS_CUDA_TRY(cudaMemcpyAsync(dhi.p, hi.data(), 4 * nch, cudaMemcpyHostToDevice, s));
+  BKS_CUDA_TRY(cudaMemcpyAsync(dk.p, kk.data(), 4 * nch, cudaMemcpyHostToDevice, s));
+  BKS_TRY((pack<T, IT>(U, ldu, t->m, r1, KP, Xp, s)));
+  BKS_TRY(Mp.alloc(sizeof(T) * (size_t)nch * r1 * r1, s));
+  const size_t smem = sizeof(T) * 2 * kCoreBatch * KP;
+  if (smem > 48 * 1024)
+    BKS_CUDA_TRY(cudaFuncSetAttribute(k_core_chunks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  k_core_chunks<T><<<nch, kCoreThreads, smem, s>>>(dlo.as<int32_t>(), dhi.as<int32_t>(),
+                                                   P.c0.as<int32_t>(), P.c1.as<int32_t>(),
+                                                   values_of<T>(P, t->vdtype), Xp.as<T>(), r1,
+                                                   KP, Mp.as<T>());
+  BKS_CUDA_TRY(cudaGetLastError());
+  const int64_t outs = (int64_t)r1 * (r1 + 1) / 2 * r3;
+  k_core_combine<T, IT, OT><<<grid_for(outs), 256, 0, s>>>(Mp.as<T>(), dk.as<int32_t>(), nch, r1,
+                                                           W, ldw, r3, F);
+  BKS_CUDA_TRY(cudaGetLastError());
+  // the host vectors above were read by async copies: keep them alive
+  BKS_CUDA_TRY(cudaStreamSynchronize(s));
+  return BKS_OK;
+}
+
+}  // namespace
+
+int contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p, const void* Y,
+                   int64_t ldy, int q, void* out, int64_t ldo, int dtype, cudaStream_t s) {
+  if (dtype == BKS_F64)
+    return mode1_typed<double, double, double>(t, (const double*)X, ldx, p, (const double*)Y, ldy,
+                                               q, (double*)out, ldo, s);
+  return mode1_typed<float, float, float>(t, (const float*)X, ldx, p, (const float*)Y, ldy, q,
+                                          (float*)out, ldo, s);
+}
+
+int contract_mode3(const bks_tensor* t, const void* X, int64_t ldx, int p, const void* X2,
+                   int64_t ldx2, int q, void* out, int64_t ldo, int dtype, cudaStream_t s) {
+  if (dtype == BKS_F64)
+    return mode3_typed<double, double, double>(t, (const double*)X, ldx, p, (const double*)X2,
+                                               ldx2, q, (double*)out, ldo, s);
+  return mode3_typed<float, float, float>(t, (const float*)X, ldx, p, (const float*)X2, ldx2, q,
+                                          (float*)out, ldo, s);
+}
+
+int contract_core(const bks_tensor* t, const void* U, int64_t ldu, int r1, const void* W,
+                  int64_t ldw, int r3, void* F, int dtype, cudaStream_t s) {
+  if (dtype == BKS_F64)
+    return core_typed<double, double, double>(t, (const double*)U, ldu, r1, (const double*)W, ldw,
+                                              r3, (double*)F, s);
+  return core_typed<float, float, float>(t, (const float*)U, ldu, r1, (const float*)W, ldw, r3,
+                                         (float*)F, s);
+}
+
+// FP64 operands and results; fp32 = true computes in FP32 (the mixed form)
+int contract_mode1_x(const bks_tensor* t, const double* X, int64_t ldx, int p, const double* Y,
+                     int64_t ldy, int q, double* out, int64_t ldo, bool fp32, cudaStream_t s) {
+  if (fp32) return mode1_typed<float, double, double>(t, X, ldx, p, Y, ldy, q, out, ldo, s);
+  return mode1_typed<double, double, double>(t, X, ldx, p, Y, ldy, q, out, ldo, s);
+}
+int contract_mode3_x(const bks_tensor* t, const double* X, int64_t ldx, int p, const double* X2,
+                     int64_t ldx2, int q, double* out, int64_t ldo, bool fp32, cudaStream_t s) {
+  if (fp32) return mode3_typed<float, double, double>(t, X, ldx, p, X2, ldx2, q, out, ldo, s);
+  return mode3_typed<double, double, double>(t, X, ldx, p, X2, ldx2, q, out, ldo, s);
+}
+int contract_core_x(const bks_tensor* t, const double* U, int64_t ldu, int r1, const double* W,
+                    int64_t ldw, int r3, double* F, bool fp32, cudaStream_t s) {
+  if (fp32) return core_typed<float, double, double>(t, U, ldu, r1, W, ldw, r3, F, s);
+  return core_typed<double, double, double>(t, U, ldu, r1, W, ldw, r3, F, s);
+}
+
+}  // namespace bks
+
+using namespace bks;
+
+static int check_common(const bks_tensor* t, const void* X, int64_t ldx, int p, int dtype,
+                        int64_t rows) {
+  if (!t) return fail(BKS_EINVAL, "null tensor");
+  if (!X) return fail(BKS_EINVAL, "null operand");
+  if (dtype != BKS_F32 && dtype != BKS_F64) return fail(BKS_EINVAL, "dtype must be BKS_F32 or BKS_F64");
+  if (ldx < rows) return fail(BKS_EINVAL, "leading dimension smaller than the row count");
+  if (p < 1) return fail(BKS_EINVAL, "width must be >= 1");
+  return BKS_OK;
+}
+
+extern "C" int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
+                                  const void* Y, int64_t ldy, int q, void* out, int64_t ldo,
+                                  int dtype, void* stream) {
+  BKS_TRY(check_common(t, X, ldx, p, dtype, t ? t->m : 0));
+  BKS_TRY(check_common(t, Y, ldy, q, dtype, t->n));
+  if (!out || ldo < t->m) return fail(BKS_EINVAL, "bad output");
+  if (p > 8 || q > 8) return fail(BKS_EUNSUPPORTED, "mode-1 widths p, q must be <= 8");
+  return contract_mode1(t, X, ldx, p, Y, ldy, q, out, ldo, dtype, (cudaStream_t)stream);
+}
+
+extern "C" int bks_contract_mode3(const bks_tensor* t, const void* X, int64_t ldx, int p,
+                                  const void* X2, int64_t ldx2, int q, void* out, int64_t ldo,
+                                  int dtype, void* stream) {
+  BKS_TRY(check_common(t, X, ldx, p, dtype, t ? t->m : 0));
+  if (X2) BKS_TRY(check_common(t, X2, ldx2, q, dtype, t->m));
+  if (!out || ldo < t->n) return fail(BKS_EINVAL, "bad output");
+  if (p > 8 || (X2 && q > 8)) return fail(BKS_EUNSUPPORTED, "mode-3 widths p, q must be <= 8");
+  return contract_mode3(t, X, ldx, p, X2, ldx2, q, out, ldo, dtype, (cudaStream_t)stream);
+}
+
+extern "C" int bks_core(const bks_tensor* t, const void* U, int64_t ldu, int r1, const void* W,
+                        int64_t ldw, int r3, void* F, int dtype, void* stream) {
+  BKS_TRY(check_common(t, U, ldu, r1, dtype, t ? t->m : 0));
+  BKS_TRY(check_common(t, W, ldw, r3, dtype, t->n));
+  if (!F) return fail(BKS_EINVAL, "null F");
+  if (r1 > 128 || r3 > 128) return fail(BKS_EUNSUPPORTED, "core ranks must be <= 128");
+  return contract_core(t, U, ldu, r1, W, ldw, r3, F, dtype, (cudaStream_t)stream);
+}

@@ -1,0 +1,409 @@
+// Inner problem of the tensor Krylov-Schur method (Algorithm 5 step (i)):
+// the best rank-(r1,r1,r3) approximation of the dense (1,2)-symmetric core
+// C = A.(X,X,Z) (k1 x k1 x k3), solved on one thread block.
+//
+// Section 6.2 starts from the truncated HOSVD of C, runs 5 HOOI sweeps and
+// then Newton-Grassmann.  This library's reading: the truncated HOSVD start
+// and the current point (Uh = [I;0], Wh = [I;0]) each get 5 symmetric HOOI
+// sweeps; the one with the larger ||F|| continues with HOOI sweeps until
+// its G-gradient is below tol * ||F|| or max_inner sweeps are done.
+//
+// The HOSVD start only seeds the iteration, so its two Gram matrices and
+// their eigenvectors are computed in FP32 (k_hosvd); the sweeps, the
+// gradient and every result are FP64.
+#include <algorithm>
+
+#include "common.cuh"
+#include "jacobi.cuh"
+
+namespace bks {
+
+namespace {
+
+constexpr int kInnerThreads = 512;
+constexpr int kMaxR = 8;                 // r1, r3 <= 8
+constexpr int kMaxW = kMaxR * kMaxR;     // r1*r3 and r1^2 <= 64
+
+inline int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 32));
+}
+
+// G1 = unfold1(C) unfold1(C)^T (k1 x k1), G3 = unfold3(C) unfold3(C)^T
+// (k3 x k3), in FP32, split over blocks along the summed index; partials
+// are summed in a fixed order by k_hosvd.
+__global__ void k_hosvd_grams(const double* __restrict__ C, int k1, int k3,
+                              float* __restrict__ part1, float* __restrict__ part3) {
+  // block b sums slices c in [c0, c1) for G1, and rows a-pairs for G3
+  const int nb = gridDim.x;
+  const int tid = threadIdx.x;
+  // G1 part: sum over (b, c) with c in this block's range
+  const int c0 = (int)((int64_t)k3 * blockIdx.x / nb), c1 = (int)((int64_t)k3 * (blockIdx.x + 1) / nb);
+  for (int x = tid; x < k1 * k1; x += blockDim.x) {
+    const int a = x % k1, a2 = x / k1;
+    float s = 0.f;
+    for (int c = c0; c < c1; ++c)
+      for (int b = 0; b < k1; ++b)
+        s += (float)C[a + (int64_t)k1 * (b + (int64_t)k1 * c)] *
+             (float)C[a2 + (int64_t)k1 * (b + (int64_t)k1 * c)];
+    part1[(int64_t)blockIdx.x * k1 * k1 + x] = s;
+  }
+  // G3 part: sum over pairs (a, b) with b in this block's range
+  const int b0 = (int)((int64_t)k1 * blockIdx.x / nb), b1 = (int)((int64_t)k1 * (blockIdx.x + 1) / nb);
+  for (int x = tid; x < k3 * k3; x += blockDim.x) {
+    const int c = x % k3, c2 = x / k3;
+    float s = 0.f;
+    for (int b = b0; b < b1; ++b)
+      for (int a = 0; a < k1; ++a)
+        s += (float)C[a + (int64_t)k1 * (b + (int64_t)k1 * c)] *
+             (float)C[a + (int64_t)k1 * (b + (int64_t)k1 * c2)];
+    part3[(int64_t)blockIdx.x * k3 * k3 + x] = s;
+  }
+}
+
+// Eigenvectors of the two Grams (FP32 Jacobi), r leading ones -> FP64.
+__global__ void __launch_bounds__(kInnerThreads)
+k_hosvd(const float* __restrict__ part1, const float* __restrict__ part3, int nparts, int k1,
+        int k3, int r1, int r3, double* __restrict__ Uh, double* __restrict__ Wh) {
+  extern __shared__ float shf[];
+  const int nmax = max(k1, k3);
+  float* A = shf;
+  float* V = A + nmax * nmax;
+  float* red = V + nmax * nmax;
+  float* cs = red + 64;
+  __shared__ int idx[kMaxR];
+  for (int pass = 0; pass < 2; ++pass) {
+    const int n = pass == 0 ? k1 : k3;
+    const int r = pass == 0 ? r1 : r3;
+    const float* part = pass == 0 ? part1 : part3;
+    for (int x = threadIdx.x; x < n * n; x += blockDim.x) {
+      float s = 0.f;
+      for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * n * n + x];
+      A[x] = s;
+    }
+    __syncthreads();
+    block_jacobi_eig<float>(A, V, n, 1e-6f, 30, red, cs);
+    top_diag<float>(A, n, r, idx);
+    double* out = pass == 0 ? Uh : Wh;
+    for (int x = threadIdx.x; x < n * r; x += blockDim.x) {
+      const int i = x % n, t = x / n;
+      out[x] = (double)V[i * n + idx[t]];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- FP64 symmetric HOOI on the core --------------------------------------
+struct InnerShared {
+  double Uh[128 * kMaxR];
+  double Wh[128 * kMaxR];
+  double T1[128 * kMaxW];    // k1 x (r1 r3), column b + r1 c
+  double T3[128 * kMaxW];    // k3 x r1^2,    column a + r1 b
+  double G[kMaxW * kMaxW];   // small Gram
+  double V[kMaxW * kMaxW];
+  double F1[kMaxR * kMaxW];
+  double F3[kMaxR * kMaxW];
+  double FF1[kMaxR * kMaxR];
+  double FF3[kMaxR * kMaxR];
+  double red[64];
+  double cs[4 * kMaxW];
+  int idx[kMaxW];
+};
+
+// T1 = unfold_1(C x_2 Uh^T x_3 Wh^T) (k1 x r1 r3), via D = C x_3 Wh^T in
+// global scratch (k1 x k1 x r3).
+__device__ void inner_t1(const double* __restrict__ C, int k1, int k3, int r1, int r3,
+                         InnerShared& S, double* __restrict__ D) {
+  for (int x = threadIdx.x; x < k1 * k1; x += blockDim.x) {
+    double acc[kMaxR];
+#pragma unroll
+    for (int t = 0; t < kMaxR; ++t) acc[t] = 0.0;
+    for (int c = 0; c < k3; ++c) {
+      const double v = C[x + (int64_t)k1 * k1 * c];
+#pragma unroll
+      for (int t = 0; t < kMaxR; ++t)
+        if (t < r3) acc[t] = fma(v, S.Wh[c + k3 * t], acc[t]);
+    }
+    for (int t = 0; t < r3; ++t) D[x + (int64_t)k1 * k1 * t] = acc[t];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < k1 * r1 * r3; x += blockDim.x) {
+    const int a = x % k1, j = x / k1;  // j = b' + r1 c'
+    const int bp = j % r1, cp = j / r1;
+    double s = 0.0;
+    for (int b = 0; b < k1; ++b) s = fma(D[a + (int64_t)k1 * (b + (int64_t)k1 * cp)], S.Uh[b + k1 * bp], s);
+    S.T1[a + k1 * j] = s;
+  }
+  __syncthreads();
+}
+
+// T3 = unfold_3(C x_1 Uh^T x_2 Uh^T) (k3 x r1^2), via E = C x_1 Uh^T
+// (r1 x k1 x k3) in global scratch; uses C(a,b,c) = C(b,a,c) so that
+// consecutive threads read consecutive addresses.
+__device__ void inner_t3(const double* __restrict__ C, int k1, int k3, int r1,
+                         InnerShared& S, double* __restrict__ E) {
+  for (int x = threadIdx.x; x < k1 * k3; x += blockDim.x) {
+    const int b = x % k1, c = x / k1;
+    double acc[kMaxR];
+#pragma unroll
+    for (int t = 0; t < kMaxR; ++t) acc[t] = 0.0;
+    for (int a = 0; a < k1; ++a) {
+      const double v = C[b + (int64_t)k1 * (a + (int64_t)k1 * c)];
+#pragma unroll
+      for (int t = 0; t < kMaxR; ++t)
+        if (t < r1) acc[t] = fma(v, S.Uh[a + k1 * t], acc[t]);
+    }
+    for (int t = 0; t < r1; ++t) E[t + (int64_t)r1 * (b + (int64_t)k1 * c)] = acc[t];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < k3 * r1 * r1; x += blockDim.x) {
+    const int c = x % k3, j = x / k3;  // j = a' + r1 b'
+    const int ap = j % r1, bp = j / r1;
+    double s = 0.0;
+    for (int b = 0; b < k1; ++b) s = fma(E[ap + (int64_t)r1 * (b + (int64_t)k1 * c)], S.Uh[b + k1 * bp], s);
+    S.T3[c + k3 * j] = s;
+  }
+  __syncthreads();
+}
+
+// r leading left singular vectors of T (n x w, ld n) into Out (n x r):
+// eigenvectors of T^T T, Out = T v / sigma, then two MGS passes.
+__device__ void inner_topsvd(const double* T, int n, int w, int r, InnerShared& S, double* Out) {
+  for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
+    const int i = x % w, j = x / w;
+    double s = 0.0;
+    for (int t = 0; t < n; ++t) s = fma(T[t + n * i], T[t + n * j], s);
+    S.G[i * w + j] = s;
+  }
+  __syncthreads();
+  block_jacobi_eig<double>(S.G, S.V, w, 1e-15, 60, S.red, S.cs);
+  top_diag<double>(S.G, w, r, S.idx);
+  for (int x = threadIdx.x; x < n * r; x += blockDim.x) {
+    const int i = x % n, t = x / n;
+    double s = 0.0;
+    for (int j = 0; j < w; ++j) s = fma(T[i + n * j], S.V[j * w + S.idx[t]], s);
+    Out[i + n * t] = s;
+  }
+  __syncthreads();
+  // MGS twice (one column at a time; n <= 128, r <= 8)
+  for (int rep = 0; rep < 2; ++rep) {
+    for (int t = 0; t < r; ++t) {
+      for (int u = 0; u < t; ++u) {
+        double d = 0.0;
+        if (threadIdx.x < 32) {
+          for (int i = threadIdx.x; i < n; i += 32) d = fma(Out[i + n * u], Out[i + n * t], d);
+          for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+          if (threadIdx.x == 0) S.red[0] = d;
+        }
+        __syncthreads();
+        d = S.red[0];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) Out[i + n * t] -= d * Out[i + n * u];
+        __syncthreads();
+      }
+      double d = 0.0;
+      if (threadIdx.x < 32) {
+        for (int i = threadIdx.x; i < n; i += 32) d = fma(Out[i + n * t], Out[i + n * t], d);
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+        if (threadIdx.x == 0) S.red[0] = d;
+      }
+      __syncthreads();
+      const double inv = 1.0 / sqrt(S.red[0]);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) Out[i + n * t] *= inv;
+      __syncthreads();
+    }
+  }
+}
+
+// G-gradient of the inner problem at (Uh, Wh) from T1 (at Uh, Wh) and T3
+// (at Uh): ||grad||^2 = 2 ||(I - Uh Uh^T) T1 F1^T||^2 + ||(I - Wh Wh^T) T3 F3^T||^2.
+__device__ void inner_grad(int k1, int k3, int r1, int r3, InnerShared& S, double* gout,
+                           double* fout) {
+  const int w1 = r1 * r3, w3 = r1 * r1;
+  // F1 = Uh^T T1 (r1 x w1), F3 = Wh^T T3 (r3 x w3)
+  for (int x = threadIdx.x; x < r1 * w1 + r3 * w3; x += blockDim.x) {
+    if (x < r1 * w1) {
+      const int a = x % r1, j = x / r1;
+      double s = 0.0;
+      for (int i = 0; i < k1; ++i) s = fma(S.Uh[i + k1 * a], S.T1[i + k1 * j], s);
+      S.F1[x] = s;
+    } else {
+      const int y = x - r1 * w1;
+      const int c = y % r3, j = y / r3;
+      double s = 0.0;
+      for (int i = 0; i < k3; ++i) s = fma(S.Wh[i + k3 * c], S.T3[i + k3 * j], s);
+      S.F3[y] = s;
+    }
+  }
+  __syncthreads();
+  // FF1 = F1 F1^T, FF3 = F3 F3^T
+  for (int x = threadIdx.x; x < r1 * r1 + r3 * r3; x += blockDim.x) {
+    if (x < r1 * r1) {
+      const int a = x % r1, b = x / r1;
+      double s = 0.0;
+      for (int j = 0; j < w1; ++j) s = fma(S.F1[a + r1 * j], S.F1[b + r1 * j], s);
+      S.FF1[x] = s;
+    } else {
+      const int y = x - r1 * r1;
+      const int c = y % r3, e = y / r3;
+      double s = 0.0;
+      for (int j = 0; j < w3; ++j) s = fma(S.F3[c + r3 * j], S.F3[e + r3 * j], s);
+      S.FF3[y] = s;
+    }
+  }
+  __syncthreads();
+  double g1 = 0.0, g3 = 0.0, nf = 0.0;
+  // mode 1: (T1 F1^T - Uh FF1) (k1 x r1)
+  for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) {
+    const int i = x % k1, a = x / k1;
+    double d = 0.0;
+    for (int j = 0; j < w1; ++j) d = fma(S.T1[i + k1 * j], S.F1[a + r1 * j], d);
+    for (int b = 0; b < r1; ++b) d = fma(-S.Uh[i + k1 * b], S.FF1[b + r1 * a], d);
+    g1 = fma(d, d, g1);
+  }
+  // mode 3: (T3 F3^T - Wh FF3) (k3 x r3)
+  for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) {
+    const int i = x % k3, c = x / k3;
+    double d = 0.0;
+    for (int j = 0; j < w3; ++j) d = fma(S.T3[i + k3 * j], S.F3[c + r3 * j], d);
+    for (int e = 0; e < r3; ++e) d = fma(-S.Wh[i + k3 * e], S.FF3[e + r3 * c], d);
+    g3 = fma(d, d, g3);
+  }
+  for (int x = threadIdx.x; x < r1 * w1; x += blockDim.x) nf = fma(S.F1[x], S.F1[x], nf);
+  for (int o = 16; o > 0; o >>= 1) {
+    g1 += __shfl_down_sync(0xffffffffu, g1, o);
+    g3 += __shfl_down_sync(0xffffffffu, g3, o);
+    nf += __shfl_down_sync(0xffffffffu, nf, o);
+  }
+  __shared__ double part[3][32];
+  if ((threadIdx.x & 31) == 0) {
+    part[0][threadIdx.x >> 5] = g1;
+    part[1][threadIdx.x >> 5] = g3;
+    part[2][threadIdx.x >> 5] = nf;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += part[0][w]; b += part[1][w]; c += part[2][w]; }
+    *gout = sqrt(2.0 * a + b);
+    *fout = sqrt(c);
+  }
+  __syncthreads();
+}
+
+// Runs HOOI sweeps from (S.Uh, S.Wh); returns sweeps done, grad, ||F||.
+__device__ int inner_sweeps(const double* C, int k1, int k3, int r1, int r3, int max_sweeps,
+                            double tol, InnerShared& S, double* D, double* E, double* res) {
+  inner_t3(C, k1, k3, r1, S, E);
+  int done = 0;
+  while (true) {
+    inner_t1(C, k1, k3, r1, r3, S, D);
+    inner_grad(k1, k3, r1, r3, S, &res[0], &res[1]);
+    const double g = res[0], nf = res[1];
+    if (done >= max_sweeps || g <= tol * nf) break;
+    inner_topsvd(S.T1, k1, r1 * r3, r1, S, S.Uh);
+    inner_t3(C, k1, k3, r1, S, E);
+    inner_topsvd(S.T3, k3, r1 * r1, r3, S, S.Wh);
+    ++done;
+  }
+  return done;
+}
+
+__global__ void __launch_bounds__(kInnerThreads)
+k_inner(const double* __restrict__ C, int k1, int k3, int r1, int r3, double tol, int max_inner,
+        int init_sweeps, const double* __restrict__ Uh_hosvd, const double* __restrict__ Wh_hosvd,
+        double* __restrict__ D, double* __restrict__ E, double* __restrict__ Uh_out,
+        double* __restrict__ Wh_out, double* __restrict__ negU, double* __restrict__ negW,
+        double* __restrict__ info) {
+  extern __shared__ double shd[];
+  InnerShared& S = *reinterpret_cast<InnerShared*>(shd);
+  __shared__ double res[2];
+  __shared__ double best[2];
+  // candidate 1: truncated HOSVD + init sweeps
+  for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) S.Uh[x] = Uh_hosvd[x];
+  for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) S.Wh[x] = Wh_hosvd[x];
+  __syncthreads();
+  inner_sweeps(C, k1, k3, r1, r3, init_sweeps, 0.0, S, D, E, res);
+  const double nf_a = res[1];
+  for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) Uh_out[x] = S.Uh[x];
+  for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) Wh_out[x] = S.Wh[x];
+  __syncthreads();
+  // candidate 2: the current point [I; 0]
+  for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) S.Uh[x] = (x % k1 == x / k1) ? 1.0 : 0.0;
+  for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) S.Wh[x] = (x % k3 == x / k3) ? 1.0 : 0.0;
+  __syncthreads();
+  inner_sweeps(C, k1, k3, r1, r3, init_sweeps, 0.0, S, D, E, res);
+  const double nf_b = res[1];
+  const bool hosvd_won = nf_a >= nf_b;
+  if (hosvd_won) {
+    for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) S.Uh[x] = Uh_out[x];
+    for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) S.Wh[x] = Wh_out[x];
+  }
+  __syncthreads();
+  const int done = inner_sweeps(C, k1, k3, r1, r3, max_inner, tol, S, D, E, res);
+  for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) {
+    Uh_out[x] = S.Uh[x];
+    negU[x] = -S.Uh[x];
+  }
+  for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) {
+    Wh_out[x] = S.Wh[x];
+    negW[x] = -S.Wh[x];
+  }
+  if (threadIdx.x == 0) {
+    info[0] = res[0];
+    info[1] = res[1];
+    info[2] = done + 2 * init_sweeps;
+    info[3] = hosvd_won ? 1.0 : 0.0;
+    best[0] = res[1];
+  }
+}
+
+}  // namespace
+
+struct InnerWork {
+  DevBuf part1, part3, Uh0, Wh0, D, E;
+};
+
+// Inner solve: C (k1 x k1 x k3, FP64, device) -> Uh (k1 x r1), Wh (k3 x r3),
+// their negatives (for the restart combine) and info[4] = {grad, ||F||,
+// sweeps, hosvd_won} on the device.
+int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int max_inner,
+                double* Uh, double* Wh, double* negU, double* negW, double* info,
+                cudaStream_t s) {
+  if (k1 > 128 || k3 > 128) return fail(BKS_EUNSUPPORTED, "inner solve: k1, k3 must be <= 128");
+  if (r1 > kMaxR || r3 > kMaxR) return fail(BKS_EUNSUPPORTED, "inner solve: r1, r3 must be <= 8");
+  static thread_local InnerWork w;
+  const int nparts = std::min(64, std::max(k1, k3));
+  const size_t p1 = sizeof(float) * (size_t)nparts * k1 * k1, p3 = sizeof(float) * (size_t)nparts * k3 * k3;
+  if (w.part1.bytes < p1) BKS_TRY(w.part1.alloc(p1, s));
+  if (w.part3.bytes < p3) BKS_TRY(w.part3.alloc(p3, s));
+  if (w.Uh0.bytes < sizeof(double) * 128 * kMaxR) BKS_TRY(w.Uh0.alloc(sizeof(double) * 128 * kMaxR, s));
+  if (w.Wh0.bytes < sizeof(double) * 128 * kMaxR) BKS_TRY(w.Wh0.alloc(sizeof(double) * 128 * kMaxR, s));
+  const size_t dsz = sizeof(double) * (size_t)k1 * k1 * kMaxR;
+  if (w.D.bytes < dsz) BKS_TRY(w.D.alloc(dsz, s));
+  const size_t esz = sizeof(double) * (size_t)kMaxR * k1 * k3;
+  if (w.E.bytes < esz) BKS_TRY(w.E.alloc(esz, s));
+  w.part1.persist(); w.part3.persist(); w.Uh0.persist(); w.Wh0.persist(); w.D.persist(); w.E.persist();
+  k_hosvd_grams<<<nparts, 256, 0, s>>>(C, k1, k3, w.part1.as<float>(), w.part3.as<float>());
+  BKS_CUDA_TRY(cudaGetLastError());
+  const int nmax = std::max(k1, k3);
+  const size_t hs = sizeof(float) * (2 * (size_t)nmax * nmax + 64 + 4 * (size_t)nmax);
+  static bool attr = false;
+  if (!attr) {
+    BKS_CUDA_TRY(cudaFuncSetAttribute(k_hosvd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(float) * (2 * 128 * 128 + 64 + 4 * 128))));
+    BKS_CUDA_TRY(cudaFuncSetAttribute(k_inner, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(InnerShared)));
+    attr = true;
+  }
+  k_hosvd<<<1, kInnerThreads, hs, s>>>(w.part1.as<float>(), w.part3.as<float>(), nparts, k1, k3,
+                                       r1, r3, w.Uh0.as<double>(), w.Wh0.as<double>());
+  BKS_CUDA_TRY(cudaGetLastError());
+  k_inner<<<1, kInnerThreads, sizeof(InnerShared), s>>>(C, k1, k3, r1, r3, tol, max_inner, 5,
+                                                        w.Uh0.as<double>(), w.Wh0.as<double>(),
+                                                        w.D.as<double>(), w.E.as<double>(), Uh,
+                                                        Wh, negU, negW, info);
+  BKS_CUDA_TRY(cudaGetLastError());
+  return BKS_OK;
+}
+
+}  // namespace bks

@@ -1,0 +1,117 @@
+"""Contractions and cores on the GPU vs the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from gpu_util import fp32_bound, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _bk():
+    import paper_2012_07595_gb300 as bk
+    from paper_2012_07595_gb300 import _build
+    _build.build()
+    return bk
+
+
+CASES = {
+    # name: (coo factory)   rows longer than 512 entries are cut into pieces
+    "uniform_small": lambda: synth.random_coo(1, 300, 100, 10_000),
+    "long_rows": lambda: synth.random_coo(2, 50, 4, 30_000),
+    "zipf": lambda: synth.zipf_tensor(3, 20_000, 23, 200_000, 1.1),
+    "tiny": lambda: synth.random_coo(4, 7, 3, 20),
+}
+
+
+def _setup(name, vdtype=np.float64):
+    bk = _bk()
+    c = CASES[name]()
+    c.v = c.v.astype(vdtype)
+    A = O.symmetrise(c.m, c.n, c.i, c.j, c.k, c.v)
+    T = bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v)
+    return bk, A, T
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("p,q", [(1, 1), (2, 3), (3, 4), (4, 4), (5, 2), (8, 4), (5, 5), (8, 8)])
+def test_mode1_fp64(name, p, q):
+    import torch
+    bk, A, T = _setup(name)
+    g = synth.rng(11)
+    X = g.standard_normal((A.m, p)); Y = g.standard_normal((A.n, q))
+    got = bk.bks_contract_mode1(T, torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"))
+    ref = O.mode1(A, X, Y)
+    absref = O.mode1(O.SymTensor(A.m, A.n, A.i, A.j, A.k, np.abs(A.v)), np.abs(X), np.abs(Y))
+    assert np.all(np.abs(got.cpu().numpy() - ref) <= 1e-13 * absref + 1e-300)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("p,q", [(2, 2), (3, 4), (5, 5), (8, 3)])
+def test_mode3_fp64(name, p, q):
+    import torch
+    bk, A, T = _setup(name)
+    g = synth.rng(12)
+    X = g.standard_normal((A.m, p)); X2 = g.standard_normal((A.m, q))
+    tX, tX2 = torch.tensor(X, device="cuda"), torch.tensor(X2, device="cuda")
+    Aabs = O.SymTensor(A.m, A.n, A.i, A.j, A.k, np.abs(A.v))
+    got = bk.bks_contract_mode3(T, tX, tX2).cpu().numpy()
+    assert np.all(np.abs(got - O.mode3(A, X, X2)) <= 1e-13 * O.mode3(Aabs, np.abs(X), np.abs(X2)) + 1e-300)
+    tri = bk.bks_contract_mode3(T, tX).cpu().numpy()
+    assert np.all(np.abs(tri - O.mode3(A, X)) <= 1e-13 * O.mode3(Aabs, np.abs(X)) + 1e-300)
+
+
+@pytest.mark.parametrize("name", ["uniform_small", "zipf", "long_rows"])
+def test_contractions_fp32_within_blocked_sum_bound(name):
+    import torch
+    bk, A, T = _setup(name, np.float32)
+    g = synth.rng(13)
+    X = g.standard_normal((A.m, 5)).astype(np.float32); Y = g.standard_normal((A.n, 5)).astype(np.float32)
+    Aabs = O.SymTensor(A.m, A.n, A.i, A.j, A.k, np.abs(A.v))
+    got = bk.bks_contract_mode1(T, torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"))
+    ref = O.mode1(A, X.astype(np.float64), Y.astype(np.float64))
+    bound = fp32_bound(O.mode1(Aabs, np.abs(X).astype(np.float64), np.abs(Y).astype(np.float64)))
+    assert np.all(np.abs(got.cpu().numpy() - ref) <= bound)
+    tri = bk.bks_contract_mode3(T, torch.tensor(X, device="cuda")).cpu().numpy()
+    bound3 = fp32_bound(O.mode3(Aabs, np.abs(X).astype(np.float64)), 512.0)
+    assert np.all(np.abs(tri - O.mode3(A, X.astype(np.float64))) <= bound3)
+
+
+def test_deterministic_bits():
+    import torch
+    bk, A, T = _setup("zipf", np.float32)
+    g = synth.rng(14)
+    X = torch.tensor(g.standard_normal((A.m, 4)), device="cuda", dtype=torch.float32)
+    Y = torch.tensor(g.standard_normal((A.n, 4)), device="cuda", dtype=torch.float32)
+    a = bk.bks_contract_mode1(T, X, Y).cpu().numpy()
+    b = bk.bks_contract_mode1(T, X, Y).cpu().numpy()
+    assert a.tobytes() == b.tobytes()
+    c = bk.bks_contract_mode3(T, X).cpu().numpy()
+    d = bk.bks_contract_mode3(T, X).cpu().numpy()
+    assert c.tobytes() == d.tobytes()
+
+
+@pytest.mark.parametrize("name", ["uniform_small", "zipf"])
+@pytest.mark.parametrize("r1,r3", [(2, 2), (3, 2), (5, 5), (14, 9), (36, 21)])
+def test_core_fp64(name, r1, r3):
+    import torch
+    bk, A, T = _setup(name)
+    g = synth.rng(15)
+    U = g.standard_normal((A.m, r1)); W = g.standard_normal((A.n, r3))
+    got = bk.bks_core(T, torch.tensor(U, device="cuda"), torch.tensor(W, device="cuda")).cpu().numpy()
+    ref = O.core(A, U, W)
+    assert rel_err(got, ref) < 1e-12
+    assert np.allclose(got, got.transpose(1, 0, 2), rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_ragged_widths_and_leading_dimensions():
+    import torch
+    bk, A, T = _setup("uniform_small")
+    g = synth.rng(16)
+    Xbig = torch.tensor(g.standard_normal((A.m + 5, 7)), device="cuda")
+    X = Xbig[: A.m, 1:4]              # ld = m + 5... column-major requires a copy
+    Y = torch.tensor(g.standard_normal((A.n, 3)), device="cuda")
+    got = bk.bks_contract_mode1(T, X, Y)
+    ref = O.mode1(A, X.cpu().numpy(), Y.cpu().numpy())
+    assert rel_err(got.cpu().numpy(), ref) < 1e-13

@@ -1,0 +1,132 @@
+"""BKS (Algorithm 5) and HOOI on the GPU vs the oracle and closed forms."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _bk():
+    import paper_2012_07595_gb300 as bk
+    from paper_2012_07595_gb300 import _build
+    _build.build()
+    return bk
+
+
+def _dense(bk, T):
+    c = synth.dense_to_coo(T)
+    A = O.symmetrise(T.shape[0], T.shape[2], c.i, c.j, c.k, c.v, mirror=False)
+    return A, bk.bks_tensor_create_coo(A.m, A.n, A.i, A.j, A.k, A.v, mirror=False)
+
+
+def _t(x):
+    import torch
+    return torch.tensor(np.asarray(x), device="cuda")
+
+
+@pytest.mark.parametrize("solver", ["bks", "hooi"])
+def test_closed_form_rank_one_slices(solver):
+    bk = _bk()
+    g = synth.rng(32)
+    m = 20
+    lam = np.concatenate([[9.0, -7.0], g.uniform(-1, 1, m - 2)])
+    Q = np.linalg.qr(g.standard_normal((m, m)))[0]
+    M = (Q * lam) @ Q.T
+    M = 0.5 * (M + M.T)
+    c = np.array([1.0, -2.0, 0.5, 3.0])
+    T = M[:, :, None] * c[None, None, :]
+    A, TT = _dense(bk, T)
+    U0 = synth.orthonormal(g, m, 2); W0 = synth.orthonormal(g, 4, 1)
+    if solver == "bks":
+        U, W, F, info = bk.bks_solve(TT, bk.BksParams(r1=2, r3=1, stages=2, block_p=2), _t(U0), _t(W0))
+    else:
+        U, W, F, info = bk.hooi_solve(TT, bk.HooiParams(r1=2, r3=1), _t(U0), _t(W0))
+    assert info["converged"]
+    want = np.sum(c ** 2) * (81.0 + 49.0)
+    assert abs(info["normF"] ** 2 - want) < 1e-10 * want
+    assert O.sin_theta_max(Q[:, :2], U.cpu().numpy()) < 1e-8
+    assert O.sin_theta_max((c / np.linalg.norm(c))[:, None], W.cpu().numpy()) < 1e-8
+
+
+def test_planted_exact_rank_recovered():
+    bk = _bk()
+    T, U0t, W0t, F0 = synth.dense_planted(41, m=40, n=12, r1=2, r3=2)
+    A, TT = _dense(bk, T)
+    g = synth.rng(7)
+    U0 = synth.orthonormal(g, 40, 2); W0 = synth.orthonormal(g, 12, 2)
+    U, W, F, info = bk.bks_solve(TT, bk.BksParams(r1=2, r3=2, stages=2, block_p=2, tol=1e-11), _t(U0), _t(W0))
+    assert info["converged"]
+    nA = np.sqrt(A.fro2())
+    assert abs(info["normF"] - nA) < 1e-12 * nA
+    assert O.sin_theta_max(U0t, U.cpu().numpy()) < 1e-10
+    assert O.sin_theta_max(W0t, W.cpu().numpy()) < 1e-10
+
+
+@pytest.mark.parametrize("seed", [101, 102])
+def test_small_planted_workload_parity(seed):
+    """300x300x100, 10,000 draws + planted term, rank (2,2,2), BK(2,2),
+    tol 1e-10, FP64: same start on both sides; ||F|| within 1e-10 relative
+    and largest principal angles within 1e-8."""
+    bk = _bk()
+    coo, _ = synth.small_planted(1)
+    A = O.symmetrise(coo.m, coo.n, coo.i, coo.j, coo.k, coo.v)
+    T = bk.bks_tensor_create_coo(coo.m, coo.n, coo.i, coo.j, coo.k, coo.v)
+    g = synth.rng(seed)
+    U0 = synth.orthonormal(g, A.m, 2); W0 = synth.orthonormal(g, A.n, 2)
+    ro = O.bks(A, U0, W0, s=2, p=2, tol=1e-10)
+    U, W, F, info = bk.bks_solve(T, bk.BksParams(r1=2, r3=2, stages=2, block_p=2, tol=1e-10), _t(U0), _t(W0))
+    assert ro.converged and info["converged"]
+    assert abs(info["normF"] - ro.normF) <= 1e-10 * ro.normF
+    assert O.sin_theta_max(ro.U, U.cpu().numpy()) < 1e-8
+    assert O.sin_theta_max(ro.W, W.cpu().numpy()) < 1e-8
+    Fn = F.cpu().numpy()
+    assert np.allclose(Fn, Fn.transpose(1, 0, 2), atol=1e-12 * np.linalg.norm(Fn))
+    assert np.sum(Fn ** 2) <= A.fro2() * (1 + 1e-12)
+    # the returned F is A.(U,U,W) at the returned point
+    assert np.allclose(Fn, O.core(A, U.cpu().numpy(), W.cpu().numpy()), atol=1e-10 * np.linalg.norm(Fn))
+    norms = [h[1] for h in info["history"]]
+    assert all(b >= a * (1 - 1e-12) for a, b in zip(norms, norms[1:]))
+
+
+@pytest.mark.parametrize("rho", [1e-2, 1e-3])
+def test_example1_bks_hooi_agree_with_oracle(rho):
+    bk = _bk()
+    T = synth.example1(61, 30, 10, 2, 2, rho)
+    A, TT = _dense(bk, T)
+    g = synth.rng(62)
+    U0 = synth.orthonormal(g, 30, 2); W0 = synth.orthonormal(g, 10, 2)
+    rb = O.bks(A, U0, W0, s=2, p=2, tol=1e-11)
+    Ub, Wb, Fb, ib = bk.bks_solve(TT, bk.BksParams(r1=2, r3=2, stages=2, block_p=2, tol=1e-11), _t(U0), _t(W0))
+    Uh, Wh, Fh, ih = bk.hooi_solve(TT, bk.HooiParams(r1=2, r3=2, tol=1e-11), _t(U0), _t(W0))
+    rh = O.hooi(A, U0, W0, tol=1e-11)
+    assert ib["converged"] and ih["converged"]
+    for nf in (ib["normF"], ih["normF"], rh.normF):
+        assert abs(nf - rb.normF) < 1e-10 * rb.normF
+    for U in (Ub, Uh):
+        assert O.sin_theta_max(rb.U, U.cpu().numpy()) < 1e-8
+    for W in (Wb, Wh):
+        assert O.sin_theta_max(rb.W, W.cpu().numpy()) < 1e-8
+
+
+def test_mixed_precision_matches_fp64_at_1e6():
+    """The FP32-contraction form reaches the FP64 optimum within 1e-6 in
+    the subspace angle on a power-law tensor."""
+    bk = _bk()
+    c = synth.zipf_tensor(21, 5000, 20, 60_000, 1.1)
+    A = O.symmetrise(c.m, c.n, c.i, c.j, c.k, c.v)
+    T = bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v)
+    g = synth.rng(22)
+    U0 = synth.orthonormal(g, c.m, 3); W0 = synth.orthonormal(g, c.n, 3)
+    p64 = bk.BksParams(r1=3, r3=3, stages=2, block_p=4, tol=1e-9)
+    U, W, F, i64 = bk.bks_solve(T, p64, _t(U0), _t(W0))
+    pm = bk.BksParams(r1=3, r3=3, stages=2, block_p=4, tol=1e-9, precision=bk.BKS_PREC_MIXED,
+                      refine_sweeps=20, mixed_tol=1e-6)
+    Um, Wm, Fm, im = bk.bks_solve(T, pm, _t(U0), _t(W0))
+    assert i64["converged"] and im["converged"]
+    assert im["fp32_iters"] > 0
+    assert O.sin_theta_max(U.cpu().numpy(), Um.cpu().numpy()) < 1e-6
+    assert O.sin_theta_max(W.cpu().numpy(), Wm.cpu().numpy()) < 1e-6
+    gg, nf, _ = O.gradient_global(A, Um.cpu().numpy(), Wm.cpu().numpy())
+    assert gg / nf < 1e-8
