@@ -150,7 +150,7 @@ typedef struct {
   int refine_sweeps;   /* MIXED only: FP64 outer iterations after the FP32 phase converged */
   uint64_t seed;       /* random start when U0/W0 are NULL */
   double drop_tol;     /* rank-drop threshold of the block QR (relative) */
-  double inner_tol;    /* inner stopping tolerance (<= 0: same as tol) */
+  double inner_tol;    /* inner stopping tolerance (<= 0: a tenth of the outer tolerance) */
   double mixed_tol;    /* MIXED only: tolerance of the FP32 phase (<= 0: 1e-6) */
 } bks_params;
 
@@ -205,6 +205,10 @@ int hooi_solve(const bks_tensor* t, const hooi_params* prm, const double* U0,
 
 /* Last error message of the calling thread ("" if none). */
 const char* bks_last_error_string(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all threads, all devices); a diagnostic counter for benchmarks. */
+uint64_t bks_launch_count(void);
 
 #ifdef __cplusplus
 }

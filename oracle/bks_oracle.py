@@ -590,7 +590,9 @@ def bks(A: SymTensor, U0: np.ndarray, W0: np.ndarray, s: int = 2, p: int = 4,
     r1, r3 = U0.shape[1], W0.shape[1]
     U, W = U0.copy(), W0.copy()
     hist = []
-    itol = tol if inner_tol is None else inner_tol
+    # the inner problem is solved to a tenth of the outer tolerance so that
+    # its residual gradient does not hold the outer test just above tol
+    itol = 0.1 * tol if inner_tol is None else inner_tol
     F = None
     for it in range(max_outer + 1):
         X, Z, info = expand(A, U, W, 1, p, variant, drop_tol)

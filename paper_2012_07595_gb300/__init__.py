@@ -24,7 +24,7 @@ __all__ = [
     "BKS_VARIANT_MIN", "BKS_VARIANT_MAX", "BksError", "Tensor", "bks_tensor_create_coo",
     "bks_tensor_destroy", "bks_tensor_info", "bks_tensor_export_coo", "bks_contract_mode1",
     "bks_contract_mode3", "bks_core", "bks_solve", "hooi_solve", "BksParams", "HooiParams",
-    "col_major", "library_path",
+    "col_major", "library_path", "bks_launch_count",
 ]
 
 BKS_OK = 0
@@ -75,6 +75,11 @@ class _HooiParams(ctypes.Structure):
 _lib = None
 
 
+def bks_launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(lib().bks_launch_count())
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -115,6 +120,8 @@ def lib():
     L.hooi_solve.argtypes = [vp, ctypes.POINTER(_HooiParams), vp, vp, vp, vp, vp,
                              ctypes.POINTER(_Info), vp]
     L.hooi_solve.restype = c_int
+    L.bks_launch_count.argtypes = []
+    L.bks_launch_count.restype = ctypes.c_uint64
     L.bks_last_error_string.argtypes = []
     L.bks_last_error_string.restype = ctypes.c_char_p
     _lib = L

@@ -13,6 +13,9 @@
 
 namespace bks {
 
+// ---- launch accounting (bks_launch_count) --------------------------------
+void note_launch();
+
 // ---- error handling (thread-local message, status codes of bks.h) -------
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);

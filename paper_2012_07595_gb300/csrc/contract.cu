@@ -303,19 +303,19 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
   const int blocks = (P.ntiles + warps - 1) / warps;
   if (P.nv > 0) {
     k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,
-                                                                 Bp, p, q, out, ldo, partial.as<T>());
+                                                                 Bp, p, q, out, ldo, partial.as<T>()); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (P.nsplit > 0) {
     k_split_reduce<T, OT, PB, QB, TRI><<<P.nsplit, 256, 0, s>>>(
         P.split_row.as<int32_t>(), P.split_first.as<int32_t>(), P.nsplit, partial.as<T>(), p, q,
-        out, ldo);
+        out, ldo); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (P.nempty > 0) {
     const int w = TRI ? p * (p + 1) / 2 : p * q;
     k_zero_rows<OT><<<grid_for((int64_t)P.nempty * w), 256, 0, s>>>(P.empty_rows.as<int32_t>(),
-                                                                    P.nempty, w, out, ldo);
+                                                                    P.nempty, w, out, ldo); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   return BKS_OK;
@@ -340,7 +340,7 @@ int dispatch(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib, co
 template <typename T, typename IT>
 int pack(const IT* X, int64_t ldx, int64_t rows, int p, int PB, DevBuf& buf, cudaStream_t s) {
   BKS_TRY(buf.alloc(sizeof(T) * (size_t)rows * PB, s));
-  k_pack<IT, T><<<grid_for(rows), 256, 0, s>>>(X, ldx, rows, p, PB, buf.as<T>());
+  k_pack<IT, T><<<grid_for(rows), 256, 0, s>>>(X, ldx, rows, p, PB, buf.as<T>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }
@@ -532,7 +532,7 @@ int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* 
     BKS_TRY(Tm.alloc(sizeof(T) * (size_t)t->n * ntri, s));
     BKS_TRY((mode3_typed<T, IT, T>(t, U, ldu, r1, nullptr, 0, r1, Tm.as<T>(), t->n, s)));
     k_core_from_tri<T, IT, OT><<<std::min(ntri * r3, 1024), 256, 0, s>>>(Tm.as<T>(), t->n, r1, W,
-                                                                         ldw, r3, F);
+                                                                         ldw, r3, F); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
     return BKS_OK;
   }
@@ -571,11 +571,11 @@ int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* 
   k_core_chunks<T><<<nch, kCoreThreads, smem, s>>>(dlo.as<int32_t>(), dhi.as<int32_t>(),
                                                    P.c0.as<int32_t>(), P.c1.as<int32_t>(),
                                                    values_of<T>(P, t->vdtype), Xp.as<T>(), r1,
-                                                   KP, Mp.as<T>());
+                                                   KP, Mp.as<T>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   const int64_t outs = (int64_t)r1 * (r1 + 1) / 2 * r3;
   k_core_combine<T, IT, OT><<<grid_for(outs), 256, 0, s>>>(Mp.as<T>(), dk.as<int32_t>(), nch, r1,
-                                                           W, ldw, r3, F);
+                                                           W, ldw, r3, F); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   // the host vectors above were read by async copies: keep them alive
   BKS_CUDA_TRY(cudaStreamSynchronize(s));

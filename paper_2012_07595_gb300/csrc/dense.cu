@@ -368,7 +368,7 @@ int launch_ts(const double* Q, int64_t ldq, int K, const double* B, int64_t ldb,
     attr_set = true;
   }
   k_ts_pass<CU, CG><<<grid, kTSThreads, smem, s>>>(Q, ldq, K, B, ldb, b, Mq, Mb, bo, update, Out,
-                                                   ldo, gram, gpart, m);
+                                                   ldo, gram, gpart, m); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }
@@ -416,7 +416,7 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
   const int gw = K + b;
   auto reduce = [&](int count) {
     k_gram_reduce<<<std::max(1, (count + 255) / 256), 256, 0, s>>>(ws.gpart.as<double>(), grid,
-                                                                   count, ws.gram.as<double>());
+                                                                   count, ws.gram.as<double>()); ::bks::note_launch();
   };
   // P1: Gram of [Q B]^T B (first projection coefficients)
   if (o.fast_first)
@@ -426,7 +426,7 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
     BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, nullptr, nullptr, b, 0, nullptr, 0, 1,
                                       ws.gpart.as<double>(), m, grid, s)));
   reduce(gw * b);
-  k_orth_r1<<<1, 256, 0, s>>>(ws.gram.as<double>(), K, b, sm);
+  k_orth_r1<<<1, 256, 0, s>>>(ws.gram.as<double>(), K, b, sm); ::bks::note_launch();
   // P2: B1 = B - Q H1 (in place) and the FP64 Gram of [Q B1]^T B1
   if (o.fast_first)
     BKS_TRY((launch_ts<float, double>(Q, ldq, K, B, ldb, b, sm + L.Mq, sm + L.Mb, b, 1, B, ldb, 1,
@@ -436,10 +436,10 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
                                       ws.gpart.as<double>(), m, grid, s)));
   reduce(gw * b);
   k_orth_r2<<<1, 256, 0, s>>>(ws.gram.as<double>(), K, b, o.drop_tol, o.cap, o.two_level ? 1 : 0,
-                              o.raw, sm, st);
+                              o.raw, sm, st); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   if (o.raw_out) {
-    k_copy_small<<<1, 32, 0, s>>>(sm + L.raw, o.raw_out, b);
+    k_copy_small<<<1, 32, 0, s>>>(sm + L.raw, o.raw_out, b); ::bks::note_launch();
   }
   // optional gradient pass: || (B1 - Q H2) gradM ||_F^2
   if (o.grad_out) {
@@ -449,16 +449,16 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
       BKS_TRY(ws.gmat.alloc(sizeof(double) * (kMaxB + kMaxK) * kMaxB, s));
     double* gM = ws.gmat.as<double>();
     double* gQ = gM + (size_t)b * g;
-    k_grad_prep<<<1, 256, 0, s>>>(ws.gram.as<double>(), K, b, sm + L.H, o.grad_mat, g, gM, gQ);
+    k_grad_prep<<<1, 256, 0, s>>>(ws.gram.as<double>(), K, b, sm + L.H, o.grad_mat, g, gM, gQ); ::bks::note_launch();
     BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, gQ, gM, g, 1, ws.gtmp.as<double>(), m, 1,
                                       ws.gpart.as<double>(), m, grid, s)));
     k_gram_reduce<<<std::max(1, ((K + g) * g + 255) / 256), 256, 0, s>>>(
-        ws.gpart.as<double>(), grid, (K + g) * g, ws.gram2.as<double>());
-    k_gram_trace<<<1, 32, 0, s>>>(ws.gram2.as<double>(), K, g, o.grad_out);
+        ws.gpart.as<double>(), grid, (K + g) * g, ws.gram2.as<double>()); ::bks::note_launch();
+    k_gram_trace<<<1, 32, 0, s>>>(ws.gram2.as<double>(), K, g, o.grad_out); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (o.h_out_early) {
-    k_copy_small<<<1, 256, 0, s>>>(sm + L.H, o.h_out_early, K * b);
+    k_copy_small<<<1, 256, 0, s>>>(sm + L.H, o.h_out_early, K * b); ::bks::note_launch();
   }
   int hst[40];
   BKS_CUDA_TRY(cudaMemcpyAsync(hst, st, 40 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -467,7 +467,7 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
   if (no == 0) {
     *bo_host = 0;
     if (H) {
-      k_copy_small<<<1, 256, 0, s>>>(sm + L.H, H, K * b);
+      k_copy_small<<<1, 256, 0, s>>>(sm + L.H, H, K * b); ::bks::note_launch();
       BKS_CUDA_TRY(cudaGetLastError());
     }
     return BKS_OK;
@@ -477,7 +477,7 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
   BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, sm + L.Mq, sm + L.Mb, no, 1, B, ldb, 1,
                                     ws.gpart.as<double>(), m, grid, s)));
   reduce(gw3 * no);
-  k_orth_r3<<<1, 256, 0, s>>>(ws.gram.as<double>(), K, b, sm, st, H, R, st + 1);
+  k_orth_r3<<<1, 256, 0, s>>>(ws.gram.as<double>(), K, b, sm, st, H, R, st + 1); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   // P4: kept columns <- Bn R3^-1 - Q H3 R3^-1; deferred columns unchanged
   BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, no, sm + L.Mq, sm + L.Mb, no, 1, B, ldb, 0,
@@ -525,7 +525,7 @@ int ts_gram(const double* Q, int64_t ldq, int K, const double* B, int64_t ldb, i
   BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, nullptr, nullptr, b, 0, nullptr, 0, 1,
                                      ws.gpart.as<double>(), m, grid, s)));
   k_gram_reduce<<<std::max(1, ((K + b) * b + 255) / 256), 256, 0, s>>>(ws.gpart.as<double>(), grid,
-                                                                      (K + b) * b, G);
+                                                                      (K + b) * b, G); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }
@@ -540,7 +540,7 @@ int ts_combine_gram(const double* Q, int64_t ldq, int K, const double* B, int64_
   BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, Mq, Mb, bo, 1, Out, ldo, 1,
                                      ws.gpart.as<double>(), m, grid, s)));
   k_gram_reduce<<<std::max(1, ((K + bo) * bo + 255) / 256), 256, 0, s>>>(ws.gpart.as<double>(),
-                                                                        grid, (K + bo) * bo, G);
+                                                                        grid, (K + bo) * bo, G); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }
@@ -606,14 +606,14 @@ __global__ void k_randn(uint64_t seed, uint64_t sid, int64_t count, double* __re
 int to_float(const double* X, int64_t ldx, int64_t rows, int cols, float* out, int64_t ldo,
              cudaStream_t s) {
   if (rows * cols == 0) return BKS_OK;
-  k_cast2d<double, float><<<grid_for(rows * cols), 256, 0, s>>>(X, ldx, rows, cols, out, ldo);
+  k_cast2d<double, float><<<grid_for(rows * cols), 256, 0, s>>>(X, ldx, rows, cols, out, ldo); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }
 int to_double(const float* X, int64_t ldx, int64_t rows, int cols, double* out, int64_t ldo,
               cudaStream_t s) {
   if (rows * cols == 0) return BKS_OK;
-  k_cast2d<float, double><<<grid_for(rows * cols), 256, 0, s>>>(X, ldx, rows, cols, out, ldo);
+  k_cast2d<float, double><<<grid_for(rows * cols), 256, 0, s>>>(X, ldx, rows, cols, out, ldo); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }
@@ -629,7 +629,7 @@ int top_left_singular(double* T, int64_t ldt, int64_t m, int w, int r, double* O
   BKS_TRY(orth_block(nullptr, m, 0, T, ldt, w, m, o, nullptr, Rb.as<double>(), &bo, ws, s));
   if (bo < r) return fail(BKS_EBREAKDOWN, "contraction has rank below the target rank");
   BKS_TRY(Ur.alloc(sizeof(double) * bo * r, s));
-  k_small_left<<<1, 256, 0, s>>>(Rb.as<double>(), w, bo, w, r, Ur.as<double>());
+  k_small_left<<<1, 256, 0, s>>>(Rb.as<double>(), w, bo, w, r, Ur.as<double>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   // Out = Qn * Ur  (Qn = T[:, 0:bo])
   return ts_combine(nullptr, m, 0, T, ldt, bo, nullptr, Ur.as<double>(), r, Out, ldo, m, ws, s);
@@ -637,7 +637,7 @@ int top_left_singular(double* T, int64_t ldt, int64_t m, int w, int r, double* O
 
 int random_orthonormal(uint64_t seed, uint64_t sid, int64_t m, int r, double* Out, DenseWork& ws,
                        cudaStream_t s) {
-  k_randn<<<grid_for(m * r), 256, 0, s>>>(seed, sid, m * r, Out);
+  k_randn<<<grid_for(m * r), 256, 0, s>>>(seed, sid, m * r, Out); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   DevBuf Rb;
   BKS_TRY(Rb.alloc(sizeof(double) * r * r, s));

@@ -4,6 +4,7 @@
 // cores) with their work-tile plans.  Runs once per tensor.
 #include <algorithm>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -11,6 +12,8 @@
 namespace bks {
 
 static thread_local std::string g_err;
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void set_error(const std::string& msg) { g_err = msg; }
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -270,7 +273,7 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
     BKS_TRY(offf.alloc(sizeof(int32_t) * nnz, s));
     DevBuf tot;
     BKS_TRY(tot.alloc(sizeof(int32_t), s));
-    k_offdiag_flags<<<grid_for(nnz), 256, 0, s>>>(di, dj, nnz, offf.as<int32_t>());
+    k_offdiag_flags<<<grid_for(nnz), 256, 0, s>>>(di, dj, nnz, offf.as<int32_t>()); ::bks::note_launch();
     BKS_TRY(exclusive_scan_i32(offf.as<int32_t>(), offpos.as<int32_t>(), nnz, tot.as<int32_t>(), s));
     BKS_TRY(read_i32(tot.as<int32_t>(), &noff, s));
   }
@@ -283,7 +286,7 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   if (nnz > 0)
     k_build_keys<<<grid_for(nnz), 256, 0, s>>>(di, dj, dk, nnz, offpos.as<int32_t>(), mirror ? 1 : 0,
                                                bj, bk, keys.as<uint64_t>(), pay.as<uint32_t>(),
-                                               mirror_src.as<uint32_t>());
+                                               mirror_src.as<uint32_t>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   BKS_TRY(radix_sort_pairs(keys.as<uint64_t>(), pay.as<uint32_t>(), N, bi + bk + bj, s));
   // runs of equal keys
@@ -294,12 +297,12 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
     BKS_TRY(hpos.alloc(sizeof(int32_t) * N, s));
     DevBuf tot;
     BKS_TRY(tot.alloc(sizeof(int32_t), s));
-    k_head_flags<<<grid_for(N), 256, 0, s>>>(keys.as<uint64_t>(), N, head.as<int32_t>());
+    k_head_flags<<<grid_for(N), 256, 0, s>>>(keys.as<uint64_t>(), N, head.as<int32_t>()); ::bks::note_launch();
     BKS_TRY(exclusive_scan_i32(head.as<int32_t>(), hpos.as<int32_t>(), N, tot.as<int32_t>(), s));
     BKS_TRY(read_i32(tot.as<int32_t>(), &nseg, s));
     BKS_TRY(starts.alloc(sizeof(int32_t) * nseg, s));
     k_seg_starts<<<grid_for(N), 256, 0, s>>>(head.as<int32_t>(), hpos.as<int32_t>(), N,
-                                              starts.as<int32_t>());
+                                              starts.as<int32_t>()); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   T->nnz = nseg;
@@ -315,11 +318,11 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
                                                  starts.as<int32_t>(), nseg, N, dv,
                                                  mirror_src.as<uint32_t>(), nnz, bj, bk,
                                                  row.as<int32_t>(), P.c0.as<int32_t>(),
-                                                 P.c1.as<int32_t>(), P.v.as<V>());
+                                                 P.c1.as<int32_t>(), P.v.as<V>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   head.release(); hpos.release(); starts.release(); offf.release(); offpos.release();
   BKS_TRY(P.ptr.alloc(sizeof(int32_t) * (m + 1), s));
-  k_row_ptr<<<grid_for(nseg + 1), 256, 0, s>>>(row.as<int32_t>(), nseg, m, P.ptr.as<int32_t>());
+  k_row_ptr<<<grid_for(nseg + 1), 256, 0, s>>>(row.as<int32_t>(), nseg, m, P.ptr.as<int32_t>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   if (!mirror && (flags & BKS_VALIDATE_SYMMETRIC)) {
     DevBuf bad;
@@ -327,7 +330,7 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
     BKS_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
     k_check_symmetric<V><<<grid_for(m), 256, 0, s>>>(P.ptr.as<int32_t>(), P.c0.as<int32_t>(),
                                                      P.c1.as<int32_t>(), P.v.as<V>(), m,
-                                                     bad.as<int>());
+                                                     bad.as<int>()); ::bks::note_launch();
     int hb = 0;
     BKS_CUDA_TRY(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     BKS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -336,10 +339,10 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   // value copies in the other precision
   if (sizeof(V) == 8) {
     BKS_TRY(P.v32.alloc(sizeof(float) * S, s));
-    k_convert<double, float><<<grid_for(nseg), 256, 0, s>>>((const double*)P.v.p, P.v32.as<float>(), nseg);
+    k_convert<double, float><<<grid_for(nseg), 256, 0, s>>>((const double*)P.v.p, P.v32.as<float>(), nseg); ::bks::note_launch();
   } else {
     BKS_TRY(P.v64.alloc(sizeof(double) * S, s));
-    k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)P.v.p, P.v64.as<double>(), nseg);
+    k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)P.v.p, P.v64.as<double>(), nseg); ::bks::note_launch();
   }
   BKS_CUDA_TRY(cudaGetLastError());
   // ||A||^2
@@ -347,8 +350,8 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
     DevBuf part, out;
     BKS_TRY(part.alloc(sizeof(double) * 1024, s));
     BKS_TRY(out.alloc(sizeof(double), s));
-    k_sumsq_partial<V><<<1024, 256, 0, s>>>(P.v.as<V>(), nseg, part.as<double>());
-    k_sum_partials<<<1, 32, 0, s>>>(part.as<double>(), 1024, out.as<double>());
+    k_sumsq_partial<V><<<1024, 256, 0, s>>>(P.v.as<V>(), nseg, part.as<double>()); ::bks::note_launch();
+    k_sum_partials<<<1, 32, 0, s>>>(part.as<double>(), 1024, out.as<double>()); ::bks::note_launch();
     BKS_CUDA_TRY(cudaMemcpyAsync(&T->fro2, out.p, sizeof(double), cudaMemcpyDeviceToHost, s));
     BKS_CUDA_TRY(cudaStreamSynchronize(s));
   }
@@ -364,25 +367,25 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
     if (nseg > 0) {
       k_keys_mode3<<<grid_for(nseg), 256, 0, s>>>(row.as<int32_t>(), P.c0.as<int32_t>(),
                                                   P.c1.as<int32_t>(), nseg, bi, bj,
-                                                  keys.as<uint64_t>(), pay.as<uint32_t>());
+                                                  keys.as<uint64_t>(), pay.as<uint32_t>()); ::bks::note_launch();
       BKS_CUDA_TRY(cudaGetLastError());
       BKS_TRY(radix_sort_pairs(keys.as<uint64_t>(), pay.as<uint32_t>(), nseg, bk + bi + bj, s));
       k_gather_mode3<V><<<grid_for(nseg), 256, 0, s>>>(keys.as<uint64_t>(), pay.as<uint32_t>(),
                                                        nseg, bi, bj, P.v.as<V>(),
                                                        krow.as<int32_t>(), Q.c0.as<int32_t>(),
-                                                       Q.c1.as<int32_t>(), Q.v.as<V>());
+                                                       Q.c1.as<int32_t>(), Q.v.as<V>()); ::bks::note_launch();
       BKS_CUDA_TRY(cudaGetLastError());
     }
     BKS_TRY(Q.ptr.alloc(sizeof(int32_t) * (n + 1), s));
-    k_row_ptr<<<grid_for(nseg + 1), 256, 0, s>>>(krow.as<int32_t>(), nseg, n, Q.ptr.as<int32_t>());
+    k_row_ptr<<<grid_for(nseg + 1), 256, 0, s>>>(krow.as<int32_t>(), nseg, n, Q.ptr.as<int32_t>()); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (sizeof(V) == 8) {
     BKS_TRY(Q.v32.alloc(sizeof(float) * S, s));
-    k_convert<double, float><<<grid_for(nseg), 256, 0, s>>>((const double*)Q.v.p, Q.v32.as<float>(), nseg);
+    k_convert<double, float><<<grid_for(nseg), 256, 0, s>>>((const double*)Q.v.p, Q.v32.as<float>(), nseg); ::bks::note_launch();
   } else {
     BKS_TRY(Q.v64.alloc(sizeof(double) * S, s));
-    k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)Q.v.p, Q.v64.as<double>(), nseg);
+    k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)Q.v.p, Q.v64.as<double>(), nseg); ::bks::note_launch();
   }
   BKS_CUDA_TRY(cudaGetLastError());
   BKS_TRY(build_tile_plan(T->m1, nseg, s));
@@ -412,7 +415,7 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
   BKS_TRY(tot.alloc(sizeof(int32_t) * 4, s));
   k_vcount<<<grid_for(R), 256, 0, s>>>(P.ptr.as<int32_t>(), R, nvr.as<int32_t>(),
                                        nslot.as<int32_t>(), issplit.as<int32_t>(),
-                                       isempty.as<int32_t>());
+                                       isempty.as<int32_t>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   BKS_TRY(exclusive_scan_i32(nvr.as<int32_t>(), vbase.as<int32_t>(), R, tot.as<int32_t>(), s));
   BKS_TRY(exclusive_scan_i32(nslot.as<int32_t>(), slotbase.as<int32_t>(), R, tot.as<int32_t>() + 1, s));
@@ -427,7 +430,7 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
   P.nempty = h[3];
   BKS_TRY(P.empty_rows.alloc(sizeof(int32_t) * std::max(P.nempty, 1), s));
   k_empty_list<<<grid_for(R), 256, 0, s>>>(isempty.as<int32_t>(), emptypos.as<int32_t>(), R,
-                                           P.empty_rows.as<int32_t>());
+                                           P.empty_rows.as<int32_t>()); ::bks::note_launch();
   P.ntiles = (int32_t)(nnz / kTile + 1);
   BKS_TRY(P.vptr.alloc(sizeof(int32_t) * (P.nv + 1), s));
   BKS_TRY(P.vrow.alloc(sizeof(int32_t) * std::max(P.nv, 1), s));
@@ -439,7 +442,7 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
                                       nvr.as<int32_t>(), slotbase.as<int32_t>(),
                                       splitpos.as<int32_t>(), P.vptr.as<int32_t>(),
                                       P.vrow.as<int32_t>(), P.vslot.as<int32_t>(),
-                                      P.split_row.as<int32_t>(), P.split_first.as<int32_t>());
+                                      P.split_row.as<int32_t>(), P.split_first.as<int32_t>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   int32_t nn = (int32_t)nnz;
   BKS_CUDA_TRY(cudaMemcpyAsync(P.vptr.as<int32_t>() + P.nv, &nn, sizeof(int32_t),
@@ -448,7 +451,7 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
   BKS_CUDA_TRY(cudaMemcpyAsync(P.split_first.as<int32_t>() + P.nsplit, &ns, sizeof(int32_t),
                                cudaMemcpyHostToDevice, s));
   k_tile_first<<<grid_for(P.ntiles + 1), 256, 0, s>>>(P.vptr.as<int32_t>(), P.nv, P.ntiles,
-                                                      P.tile_first.as<int32_t>());
+                                                      P.tile_first.as<int32_t>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   BKS_CUDA_TRY(cudaStreamSynchronize(s));  // host copies above read stack values
   return BKS_OK;
@@ -501,7 +504,7 @@ extern "C" int bks_tensor_create_coo(int64_t m, int64_t n, int64_t nnz, const in
       if (rc == BKS_OK) {
         int hb = 0;
         cudaMemsetAsync(bad.p, 0, sizeof(int), s);
-        k_validate<<<grid_for(nnz), 256, 0, s>>>(di, dj, dk, nnz, m, n, bad.as<int>());
+        k_validate<<<grid_for(nnz), 256, 0, s>>>(di, dj, dk, nnz, m, n, bad.as<int>()); ::bks::note_launch();
         cudaError_t e = cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = fail(BKS_ECUDA, std::string("validate: ") + cudaGetErrorString(e));
@@ -547,7 +550,7 @@ extern "C" int bks_tensor_export_coo(const bks_tensor* t, int32_t* i, int32_t* j
   if (!i || !j || !k || !v) return fail(BKS_EINVAL, "null output pointer");
   cudaStream_t s = (cudaStream_t)stream;
   const Part& P = t->m1;
-  k_expand_rows<<<grid_for(t->m), 256, 0, s>>>(P.ptr.as<int32_t>(), t->m, i);
+  k_expand_rows<<<grid_for(t->m), 256, 0, s>>>(P.ptr.as<int32_t>(), t->m, i); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   BKS_CUDA_TRY(cudaMemcpyAsync(j, P.c1.p, 4 * t->nnz, cudaMemcpyDeviceToDevice, s));
   BKS_CUDA_TRY(cudaMemcpyAsync(k, P.c0.p, 4 * t->nnz, cudaMemcpyDeviceToDevice, s));
@@ -557,3 +560,5 @@ extern "C" int bks_tensor_export_coo(const bks_tensor* t, int32_t* i, int32_t* j
 }
 
 extern "C" const char* bks_last_error_string(void) { return g_err.c_str(); }
+
+extern "C" uint64_t bks_launch_count(void) { return g_launches.load(); }

@@ -383,7 +383,7 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   const size_t esz = sizeof(double) * (size_t)kMaxR * k1 * k3;
   if (w.E.bytes < esz) BKS_TRY(w.E.alloc(esz, s));
   w.part1.persist(); w.part3.persist(); w.Uh0.persist(); w.Wh0.persist(); w.D.persist(); w.E.persist();
-  k_hosvd_grams<<<nparts, 256, 0, s>>>(C, k1, k3, w.part1.as<float>(), w.part3.as<float>());
+  k_hosvd_grams<<<nparts, 256, 0, s>>>(C, k1, k3, w.part1.as<float>(), w.part3.as<float>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   const int nmax = std::max(k1, k3);
   const size_t hs = sizeof(float) * (2 * (size_t)nmax * nmax + 64 + 4 * (size_t)nmax);
@@ -396,12 +396,12 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
     attr = true;
   }
   k_hosvd<<<1, kInnerThreads, hs, s>>>(w.part1.as<float>(), w.part3.as<float>(), nparts, k1, k3,
-                                       r1, r3, w.Uh0.as<double>(), w.Wh0.as<double>());
+                                       r1, r3, w.Uh0.as<double>(), w.Wh0.as<double>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   k_inner<<<1, kInnerThreads, sizeof(InnerShared), s>>>(C, k1, k3, r1, r3, tol, max_inner, 5,
                                                         w.Uh0.as<double>(), w.Wh0.as<double>(),
                                                         w.D.as<double>(), w.E.as<double>(), Uh,
-                                                        Wh, negU, negW, info);
+                                                        Wh, negU, negW, info); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }

@@ -86,16 +86,16 @@ int exclusive_scan(const T* in, T* out, int64_t n, T* total, cudaStream_t s) {
   }
   int64_t blocks = (n + kScanTile - 1) / kScanTile;
   if (blocks == 1) {
-    scan_block_apply<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total);
+    scan_block_apply<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
     return BKS_OK;
   }
   DevBuf sums;
   BKS_TRY(sums.alloc(sizeof(T) * blocks, s));
-  scan_block_sums<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, n, sums.as<T>());
+  scan_block_sums<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, n, sums.as<T>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   BKS_TRY(exclusive_scan<T>(sums.as<T>(), sums.as<T>(), blocks, nullptr, s));
-  scan_block_apply<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, out, n, sums.as<T>(), total);
+  scan_block_apply<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, out, n, sums.as<T>(), total); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }
@@ -198,12 +198,12 @@ int radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaSt
   uint32_t *va = vals, *vb = v2.as<uint32_t>();
   int passes = 0;
   for (int shift = 0; shift < bits; shift += 8, ++passes) {
-    radix_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, counts.as<int32_t>(), ntiles);
+    radix_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, counts.as<int32_t>(), ntiles); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
     BKS_TRY(exclusive_scan_i32(counts.as<int32_t>(), counts.as<int32_t>(), 256LL * ntiles,
                                nullptr, s));
     radix_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift,
-                                                  counts.as<int32_t>(), ntiles);
+                                                  counts.as<int32_t>(), ntiles); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
     std::swap(ka, kb);
     std::swap(va, vb);

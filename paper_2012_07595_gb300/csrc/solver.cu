@@ -72,7 +72,7 @@ inline int grid_for(int64_t n) {
 int copy2d(const double* src, int64_t lds, int64_t rows, int cols, double* dst, int64_t ldd,
            cudaStream_t s) {
   if (rows * cols == 0) return BKS_OK;
-  k_copy2d<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, rows, cols, dst, ldd);
+  k_copy2d<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, rows, cols, dst, ldd); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }
@@ -223,7 +223,7 @@ struct BksState {
     o.two_level = true;
     o.fast_first = fp32;
     if (stage1) {
-      k_f3w<<<1, 256, 0, s>>>(H1.as<double>(), r1, r3, F3wT.as<double>());
+      k_f3w<<<1, 256, 0, s>>>(H1.as<double>(), r1, r3, F3wT.as<double>()); ::bks::note_launch();
       BKS_CUDA_TRY(cudaGetLastError());
       o.grad_out = scal.as<double>() + 1;
       o.grad_mat = F3wT.as<double>();
@@ -246,7 +246,7 @@ struct BksState {
     BKS_CUDA_TRY(cudaMemsetAsync(scal.p, 0, sizeof(double) * 4, s));
     BKS_TRY(add_u_block(0, 0, fp32, true));
     BKS_TRY(add_w_block(0, 0, true, fp32, true));
-    k_sumsq<<<1, 256, 0, s>>>(H1.as<double>(), r1 * r1 * r3, scal.as<double>() + 2);
+    k_sumsq<<<1, 256, 0, s>>>(H1.as<double>(), r1 * r1 * r3, scal.as<double>() + 2); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
     double h[3];
     BKS_CUDA_TRY(cudaMemcpyAsync(h, scal.p, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -273,9 +273,13 @@ struct BksState {
     return BKS_OK;
   }
 
+  double cur_tol = 0.0;  // outer tolerance of the current phase
+
   int inner_and_restart(bool fp32) {
     BKS_TRY(contract_core_x(t, Xp(), m, k1, Zp(), n, k3, C.as<double>(), fp32, s));
-    const double itol = P.inner_tol > 0 ? P.inner_tol : P.tol;
+    // inner tolerance: a tenth of the outer one unless given, so that the
+    // inner residual gradient does not hold the outer test just above tol
+    const double itol = P.inner_tol > 0 ? P.inner_tol : 0.1 * cur_tol;
     BKS_TRY(inner_solve(C.as<double>(), k1, k3, r1, r3, itol, P.max_inner, Uh.as<double>(),
                         Wh.as<double>(), negU.as<double>(), negW.as<double>(),
                         inner_info.as<double>(), s));
@@ -396,6 +400,7 @@ extern "C" int bks_solve(const bks_tensor* t, const bks_params* prm, const doubl
       if (mixed && refine_left-- <= 0) break;
     }
     if (it >= prm->max_outer) break;
+    S.cur_tol = fp32 ? mtol : prm->tol;
     BKS_TRY(S.expand_rest(fp32));
     BKS_TRY(S.inner_and_restart(fp32));
   }
@@ -513,7 +518,7 @@ extern "C" int hooi_solve(const bks_tensor* t, const hooi_params* prm, const dou
   else BKS_TRY(random_orthonormal(prm->seed, 3, n, r3, Wp, ws, s));
   auto make_t3 = [&]() -> int {
     BKS_TRY(contract_mode3_x(t, Up, m, r1, nullptr, m, r1, T3.as<double>(), n, fp32, s));
-    k_tri_weight<<<grid_for(n * w3), 256, 0, s>>>(T3.as<double>(), n, r1);
+    k_tri_weight<<<grid_for(n * w3), 256, 0, s>>>(T3.as<double>(), n, r1); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
     return BKS_OK;
   };
@@ -529,18 +534,18 @@ extern "C" int hooi_solve(const bks_tensor* t, const hooi_params* prm, const dou
       // mode 1: F1 = U^T T1, gradient T1 F1^T - U (F1 F1^T)
       BKS_TRY(ts_gram(Up, m, r1, T1.as<double>(), m, w1, m, G.as<double>(), ws, s));
       k_hooi_small<<<1, 128, 0, s>>>(G.as<double>(), r1, w1, FT.as<double>(), FF.as<double>(),
-                                     sc.as<double>() + 2);
+                                     sc.as<double>() + 2); ::bks::note_launch();
       BKS_TRY(ts_combine_gram(Up, m, r1, T1.as<double>(), m, w1, FF.as<double>(), FT.as<double>(),
                               r1, gout.as<double>(), m, m, G.as<double>(), ws, s));
-      k_trace_out<<<1, 32, 0, s>>>(G.as<double>(), r1, r1, sc.as<double>() + 0);
+      k_trace_out<<<1, 32, 0, s>>>(G.as<double>(), r1, r1, sc.as<double>() + 0); ::bks::note_launch();
       // mode 3 with the weighted triangle T3w: F3w = W^T T3w
       BKS_TRY(ts_gram(Wp, n, r3, T3.as<double>(), n, w3, n, G.as<double>(), ws, s));
       k_hooi_small<<<1, 128, 0, s>>>(G.as<double>(), r3, w3, FT3.as<double>(), FF3.as<double>(),
-                                     sc.as<double>() + 3);
+                                     sc.as<double>() + 3); ::bks::note_launch();
       BKS_TRY(ts_combine_gram(Wp, n, r3, T3.as<double>(), n, w3, FF3.as<double>(),
                               FT3.as<double>(), r3, gout3.as<double>(), n, n, G.as<double>(), ws,
                               s));
-      k_trace_out<<<1, 32, 0, s>>>(G.as<double>(), r3, r3, sc.as<double>() + 1);
+      k_trace_out<<<1, 32, 0, s>>>(G.as<double>(), r3, r3, sc.as<double>() + 1); ::bks::note_launch();
       BKS_CUDA_TRY(cudaGetLastError());
       double h[4];
       BKS_CUDA_TRY(cudaMemcpyAsync(h, sc.p, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -565,7 +570,7 @@ extern "C" int hooi_solve(const bks_tensor* t, const hooi_params* prm, const dou
   }
   // outputs: F = U^T T1 from the last gradient evaluation (FT holds F^T,
   // w1 x r1), written as unfold_1(F) = r1 x w1
-  k_transpose<<<grid_for((int64_t)w1 * r1), 256, 0, s>>>(FT.as<double>(), w1, r1, F);
+  k_transpose<<<grid_for((int64_t)w1 * r1), 256, 0, s>>>(FT.as<double>(), w1, r1, F); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   BKS_TRY(copy2d(Up, m, m, r1, U, m, s));
   BKS_TRY(copy2d(Wp, n, n, r3, W, n, s));
