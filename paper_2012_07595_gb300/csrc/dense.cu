@@ -144,15 +144,20 @@ __global__ void k_orth_r1(const double* __restrict__ G, int K, int b, double* __
   for (int c = threadIdx.x; c < b; c += blockDim.x) sm[L.raw + c] = sqrt(fmax(G[K + c + gw * c], 0.0));
 }
 
-// Round 2: H2 = Q^T B1, S = B1^T B1 - H2^T H2 and a Cholesky pass that
-// classifies every column c by its residual d_c after projection on Q and
-// the earlier kept columns:
-//   resolved  sqrt(d_c) > 1e-6 * max_c' ||(I-QQ^T) b_c'||  (the Gram holds
-//             d_c to a few digits): kept if sqrt(d_c) > drop_tol * ||b_c||,
-//             else dropped (the rank-drop rule; the paper gives none);
-//   otherwise deferred (two-level mode: orthogonalised again in a second
-//             level against the kept columns, where its residual is
-//             computed from the vectors, not from this Gram) or dropped.
+// Round 2: H2 = Q^T B1, S = B1^T B1 - H2^T H2 and a left-to-right Cholesky
+// pass.  Column c has the residual d_c after projection on Q and the kept
+// columns to its left.  A Gram matrix holds d_c to a few digits only while
+// the column is not nearly dependent on those columns, so:
+//   sqrt(d_c) > 1e-3 ||(I-QQ^T) b_c||  (resolved): kept if
+//       sqrt(d_c) > drop_tol ||b_c|| (the rank-drop rule; the paper gives
+//       none), else dropped;
+//   otherwise: this column and every column to its right are deferred
+//       (two-level mode) to a further pass against [Q, kept columns],
+//       where their Gram is formed from re-projected vectors; without
+//       two-level mode they are dropped.
+// The first column of any pass is always resolved, so every pass decides
+// at least one column.  The order of the kept columns is the left-to-right
+// order of a column-by-column Gram-Schmidt.
 // The output of P3 is [kept columns (Rk^-1 QR) | deferred columns (second
 // projection only)]: Mb = [Rk^-1 on kept rows | selection of deferred],
 // Mq = [H2[:,kept] Rk^-1 | H2[:,deferred]].
@@ -176,10 +181,14 @@ __global__ void k_orth_r2(const double* __restrict__ G, int K, int b, double dro
     for (int c = threadIdx.x; c < b; c += blockDim.x) sm[L.raw + c] = raw_in[c];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double pmax = 0.0;
-    for (int c = 0; c < b; ++c) pmax = fmax(pmax, sqrt(fmax(S[c + b * c], 0.0)));
     int nk = 0, nd = 0;
+    bool deferring = false;
     for (int c = 0; c < b; ++c) {
+      if (deferring) {
+        dpos[nd++] = c;
+        sm[L.kept + c] = 2;
+        continue;
+      }
       for (int t = 0; t < nk; ++t) {
         const int kt = pos[t];
         double v = S[kt + b * c];
@@ -190,11 +199,15 @@ __global__ void k_orth_r2(const double* __restrict__ G, int K, int b, double dro
       for (int t = 0; t < nk; ++t) d -= R[t + b * c] * R[t + b * c];
       const double raw = sm[L.raw + c];
       const double res = sqrt(fmax(d, 0.0));
-      const bool resolved = res > 1e-6 * pmax;
+      const double proj = sqrt(fmax(S[c + b * c], 0.0));
+      // with no kept column before it at this level, d_c is the Gram
+      // diagonal itself and is always resolved (every level decides at
+      // least its first column)
+      const bool resolved = nk == 0 || res > 1e-3 * proj;
       int cls = 0;  // 0 drop, 1 keep, 2 defer
-      if (nk + nd < cap && raw > 0.0) {
+      if (nk < cap && raw > 0.0) {
         if (resolved) cls = res > drop_tol * raw ? 1 : 0;
-        else cls = two_level ? 2 : 0;
+        else if (two_level) { cls = 2; deferring = true; }
       }
       if (cls == 1) {
         R[nk + b * c] = res;
@@ -496,7 +509,9 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
     OrthOpts o2;
     o2.drop_tol = o.drop_tol;
     o2.cap = o.cap - nk;
-    o2.two_level = false;
+    o2.two_level = nd > 1;  // the suffix's first column is always decided
+    o2.depth = o.depth + 1;
+    if (o2.depth > kMaxB + 1) return fail(BKS_EBREAKDOWN, "block QR: deferral did not terminate");
     o2.fast_first = false;
     o2.raw = ws.raw2.as<double>();
     int bo2 = 0;

@@ -30,6 +30,7 @@ struct OrthOpts {
   const double* grad_mat = nullptr;  // M (b x grad_cols, ld b); null: M = H^T
   int grad_cols = 0;
   double* h_out_early = nullptr;  // device K x b: the projection coefficients H
+  int depth = 0;                  // deferral level (internal)
 };
 
 // Block Gram-Schmidt + thin QR of B (m x b) against the orthonormal Q
