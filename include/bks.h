@@ -118,6 +118,27 @@ int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
                        const void* Y, int64_t ldy, int q, void* out,
                        int64_t ldo, int dtype, void* stream);
 
+/* bks_contract_mode1_noalloc: the same result as bks_contract_mode1 (same
+ *   arguments, same kernels, bitwise the same output) for callers that
+ *   cannot allocate device memory -- for example a host framework that has
+ *   reserved the whole device for its own memory pool, or code that must
+ *   not let a library call cudaMalloc, which can synchronise the device and
+ *   fail under memory pressure.  The paper has no counterpart of this call.
+ *   Scratch (the packed copies of X and Y and the partial sums of long
+ *   rows) lives in a fixed 32 MiB device array inside the library, which
+ *   every GPU that loads the library keeps until the process exits; a call
+ *   needing more (about 4*8*m + 4*8*n + 8*32*(nnz/512) bytes in FP64)
+ *   returns BKS_EUNSUPPORTED before launching anything.  The call allocates
+ *   nothing.  Its first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.  All calls share the one array and every call
+ *   overwrites what it uses (nothing has to start at zero), so calls that
+ *   overlap on the GPU -- on different streams, or from several host
+ *   threads -- race; order them on one stream. */
+int bks_contract_mode1_noalloc(const bks_tensor* t, const void* X, int64_t ldx,
+                               int p, const void* Y, int64_t ldy, int q,
+                               void* out, int64_t ldo, int dtype, void* stream);
+
 /* bks_contract_mode3: out = unfold_3(A.(X,X2)_{1,2})
  *   X2 != NULL: out[k + ldo*(a + p*b)] = sum v X[i,a] X2[j,b]; out is
  *     n x (p*q); X2 is m x q (ldx2).

@@ -106,6 +106,9 @@ def lib():
     L.bks_tensor_export_coo.restype = c_int
     L.bks_contract_mode1.argtypes = [vp, vp, i64, c_int, vp, i64, c_int, vp, i64, c_int, vp]
     L.bks_contract_mode1.restype = c_int
+    L.bks_contract_mode1_noalloc.argtypes = [vp, vp, i64, c_int, vp, i64, c_int, vp, i64, c_int,
+                                             vp]
+    L.bks_contract_mode1_noalloc.restype = c_int
     L.bks_contract_mode3.argtypes = [vp, vp, i64, c_int, vp, i64, c_int, vp, i64, c_int, vp]
     L.bks_contract_mode3.restype = c_int
     L.bks_core.argtypes = [vp, vp, i64, c_int, vp, i64, c_int, vp, c_int, vp]
@@ -264,6 +267,19 @@ def bks_contract_mode1(t: Tensor, X, Y, out=None, stream=None):
                                     ctypes.c_void_p(Y.data_ptr()), _ld(Y), q,
                                     ctypes.c_void_p(out.data_ptr()), _ld(out), _dtype_code(X),
                                     _stream(stream)))
+    return out
+
+
+def bks_contract_mode1_noalloc(t: Tensor, X, Y, out, stream=None):
+    """bks_contract_mode1 for callers that cannot allocate device memory:
+    the library uses its fixed 32 MiB device scratch array instead of
+    allocating.  `out` (m x p q, column-major) must be given."""
+    X, Y = col_major(X), col_major(Y)
+    p, q = X.shape[1], Y.shape[1]
+    _check(lib().bks_contract_mode1_noalloc(t.handle, ctypes.c_void_p(X.data_ptr()), _ld(X), p,
+                                            ctypes.c_void_p(Y.data_ptr()), _ld(Y), q,
+                                            ctypes.c_void_p(out.data_ptr()), _ld(out),
+                                            _dtype_code(X), _stream(stream)))
     return out
 
 

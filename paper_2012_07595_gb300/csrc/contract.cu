@@ -670,3 +670,140 @@ extern "C" int bks_core(const bks_tensor* t, const void* U, int64_t ldu, int r1,
   if (r1 > 128 || r3 > 128) return fail(BKS_EUNSUPPORTED, "core ranks must be <= 128");
   return contract_core(t, U, ldu, r1, W, ldw, r3, F, dtype, (cudaStream_t)stream);
 }
+
+// ---------------------------------------------------------------------------
+// Mode-1 contraction without device allocation.
+//
+// Some callers cannot allocate device memory: a host framework that has
+// reserved the whole device for its own memory pool, or code that must not
+// let a library call cudaMalloc (which can synchronise the device and fail
+// under memory pressure).  This variant keeps the contraction's scratch --
+// the packed row-major copies of X and Y and the partial sums of long rows --
+// in one file-scope device array of fixed size instead of allocating it.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace bks {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code only sees a stand-in symbol, not a device address).
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  BKS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(BKS_EUNSUPPORTED, "device index too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    BKS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return BKS_OK;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <typename T, typename OT, int PB, int QB, bool TRI>
+int launch_contract_fixed(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib,
+                          const T* Ap, const T* Bp, int p, int q, OT* out, int64_t ldo,
+                          T* partial, cudaStream_t s) {
+  TileArgs ta{P.tile_first.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
+              P.vslot.as<int32_t>(), P.ntiles, ia, ib};
+  const int warps = 8;
+  const int blocks = (P.ntiles + warps - 1) / warps;
+  if (P.nv > 0) {
+    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,
+                                                                 Bp, p, q, out, ldo, partial); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+  }
+  if (P.nsplit > 0) {
+    k_split_reduce<T, OT, PB, QB, TRI><<<P.nsplit, 256, 0, s>>>(
+        P.split_row.as<int32_t>(), P.split_first.as<int32_t>(), P.nsplit, partial, p, q, out,
+        ldo); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+  }
+  if (P.nempty > 0) {
+    const int w = p * q;
+    k_zero_rows<OT><<<grid_for((int64_t)P.nempty * w), 256, 0, s>>>(P.empty_rows.as<int32_t>(),
+                                                                    P.nempty, w, out, ldo); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+  }
+  return BKS_OK;
+}
+
+template <typename T>
+int dispatch_fixed(const Part& P, int vdtype, const T* Ap, int PB, const T* Bp, int QB, int p,
+                   int q, T* out, int64_t ldo, T* partial, cudaStream_t s) {
+  const int32_t* ia = P.c1.as<int32_t>();
+  const int32_t* ib = P.c0.as<int32_t>();
+#define BKS_FIXED_CASE(pb, qb)                                                               \
+  if (PB == pb && QB == qb)                                                                  \
+    return launch_contract_fixed<T, T, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, out, \
+                                                      ldo, partial, s);
+  BKS_FIXED_CASE(2, 2) BKS_FIXED_CASE(2, 4) BKS_FIXED_CASE(2, 8) BKS_FIXED_CASE(4, 2)
+  BKS_FIXED_CASE(4, 4) BKS_FIXED_CASE(4, 8) BKS_FIXED_CASE(8, 2) BKS_FIXED_CASE(8, 4)
+#undef BKS_FIXED_CASE
+  return fail(BKS_EUNSUPPORTED, "contraction bucket not instantiated");
+}
+
+template <typename T>
+int mode1_noalloc_typed(const bks_tensor* t, const T* X, int64_t ldx, int p, const T* Y,
+                        int64_t ldy, int q, T* out, int64_t ldo, cudaStream_t s) {
+  const int PB = bucket(p);
+  const int qchunk = PB == 8 ? 4 : 8;
+  const int QBmax = bucket(std::min(qchunk, q));
+  const Part& P = t->m1;
+  // scratch layout: [Xp: m x PB][Yp: n x QB][piece partials: nslots x PB*QB]
+  const size_t xb = align256(sizeof(T) * (size_t)t->m * PB);
+  const size_t yb = align256(sizeof(T) * (size_t)t->n * QBmax);
+  const size_t pbytes = align256(sizeof(T) * (size_t)P.nslots * PB * QBmax);
+  const size_t need = xb + yb + pbytes;
+  if (need > kNoAllocScratchBytes)
+    return fail(BKS_EUNSUPPORTED,
+                "bks_contract_mode1_noalloc: needs " + std::to_string(need) +
+                    " bytes of scratch, above the fixed " +
+                    std::to_string(kNoAllocScratchBytes) + " bytes");
+  unsigned char* base = nullptr;
+  BKS_TRY(noalloc_scratch(&base));
+  T* Xp = reinterpret_cast<T*>(base);
+  T* Yp = reinterpret_cast<T*>(base + xb);
+  T* partial = reinterpret_cast<T*>(base + xb + yb);
+  k_pack<T, T><<<grid_for(t->m), 256, 0, s>>>(X, ldx, t->m, p, PB, Xp); ::bks::note_launch();
+  BKS_CUDA_TRY(cudaGetLastError());
+  for (int q0 = 0; q0 < q; q0 += qchunk) {
+    const int qq = std::min(qchunk, q - q0);
+    const int QB = bucket(qq);
+    // stream order: the previous chunk's kernels finish reading Yp first
+    k_pack<T, T><<<grid_for(t->n), 256, 0, s>>>(Y + ldy * q0, ldy, t->n, qq, QB, Yp); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+    BKS_TRY(dispatch_fixed<T>(P, t->vdtype, Xp, PB, Yp, QB, p, qq, out + ldo * (p * q0), ldo,
+                              partial, s));
+  }
+  return BKS_OK;
+}
+
+}  // namespace
+}  // namespace bks
+
+extern "C" int bks_contract_mode1_noalloc(const bks_tensor* t, const void* X, int64_t ldx,
+                                          int p, const void* Y, int64_t ldy, int q, void* out,
+                                          int64_t ldo, int dtype, void* stream) {
+  BKS_TRY(check_common(t, X, ldx, p, dtype, t ? t->m : 0));
+  BKS_TRY(check_common(t, Y, ldy, q, dtype, t->n));
+  if (!out || ldo < t->m) return fail(BKS_EINVAL, "bad output");
+  if (p > 8 || q > 8) return fail(BKS_EUNSUPPORTED, "mode-1 widths p, q must be <= 8");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == BKS_F64)
+    return mode1_noalloc_typed<double>(t, (const double*)X, ldx, p, (const double*)Y, ldy, q,
+                                       (double*)out, ldo, s);
+  return mode1_noalloc_typed<float>(t, (const float*)X, ldx, p, (const float*)Y, ldy, q,
+                                    (float*)out, ldo, s);
+}
