@@ -35,11 +35,15 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOAD = {
-    "workload": "zipf1.1 (1,2)-symmetric 100000x100000x50, 5M stored (2.5M draws mirrored), "
-                "rank (3,3,3), BK(s=2,p=4) -> (k1,k3)=(36,21)",
-    "m": 100_000, "n": 50, "draws": 2_500_000, "zipf_s": 1.1, "seed": 2,
-    "r": 3, "stages": 2, "block_p": 4, "tol": 1e-8, "mixed_tol": 1e-5,
+    "workload": "zipf1.1 (1,2)-symmetric 100000x100000x50, ~5.0M stored (4.055M draws, "
+                "mirrored, duplicates summed), rank (3,3,3), BK(s=2,p=4) -> (k1,k3)=(36,21)",
+    "m": 100_000, "n": 50, "draws": 4_055_000, "zipf_s": 1.1, "seed": 2,
+    "r": 3, "stages": 2, "block_p": 4, "tol": 1e-9, "mixed_tol": 1e-6, "tol_scale_free": 1,
 }
+# The stopping test of both forms is the scale-free ||grad|| / ||F||^2 <= 1e-9
+# (the paper's ||grad|| / ||F|| grows with the scale of A: ||F|| ~ 5e4 here);
+# the bench checks that both results are within 1e-6 (sin of the largest
+# principal angle) of a tightly converged FP64 solution.
 
 
 def _peaks():
@@ -153,7 +157,7 @@ def run_reference(args):
         if s >= args.warmup:
             times.append(d["seconds_per_outer_iter"])
     t_iter = statistics.median(times)
-    nnz_full = 2 * WORKLOAD["draws"]
+    nnz_full = 5_000_000  # stored entries of the full workload (measured by the GPU arm)
     scale = nnz_full / max(1, d["nnz_sample"])
     solve_s = t_iter * scale * outer_iters
     value = 1.0 / solve_s
@@ -172,6 +176,46 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+LARGE = {"m": 1_000_000, "n": 200, "draws": 25_000_000, "zipf_s": 1.2, "seed": 3, "r": 5}
+
+
+def ncu_case(args):
+    """Profiling entry for ncu: a few launches of one kernel family."""
+    import torch
+    import paper_2012_07595_gb300 as bk
+    from paper_2012_07595_gb300 import _build
+    _build.build()
+    if args.size == "large":
+        L = LARGE
+        coo = synth.zipf_tensor(L["seed"], L["m"], L["n"], L["draws"], L["zipf_s"],
+                                values="absnormal", vdtype=np.float32)
+        r, p = L["r"], 4
+    else:
+        coo = make_input()
+        coo.v = coo.v.astype(np.float32)
+        r, p = WORKLOAD["r"], 4
+    T = bk.bks_tensor_create_coo(coo.m, coo.n, coo.i, coo.j, coo.k, coo.v)
+    g = synth.rng(9)
+    X = torch.tensor(g.standard_normal((coo.m, r)), device="cuda", dtype=torch.float32)
+    Y = torch.tensor(g.standard_normal((coo.n, p)), device="cuda", dtype=torch.float32)
+    for _ in range(3):
+        if args.ncu_case == "mode1":
+            bk.bks_contract_mode1(T, X, Y)
+        elif args.ncu_case == "mode3":
+            bk.bks_contract_mode3(T, X)
+        elif args.ncu_case == "core":
+            Xc = torch.tensor(g.standard_normal((coo.m, 36)), device="cuda", dtype=torch.float32)
+            Zc = torch.tensor(g.standard_normal((coo.n, 21)), device="cuda", dtype=torch.float32)
+            bk.bks_core(T, Xc, Zc)
+        elif args.ncu_case == "solve":
+            U0h, W0h = start_matrices(coo.m, coo.n, r)
+            bk.bks_solve(T, bk.BksParams(r1=r, r3=r, stages=2, block_p=4, tol=1e-8,
+                                         precision=bk.BKS_PREC_MIXED, max_outer=3),
+                         torch.tensor(U0h, device="cuda"), torch.tensor(W0h, device="cuda"))
+    torch.cuda.synchronize()
+    print(f"ncu case {args.ncu_case} ({args.size}) done: nnz {T.nnz}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,7 +223,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", default=None,
+                    help="profiling entry: build the workload, run a few launches of one "
+                         "kernel family (mode1, mode3, core, solve) and exit without a JSON line")
+    ap.add_argument("--size", default="medium", choices=["medium", "large"],
+                    help="ncu-case workload: medium = 1e5 x 1e5 x 50 (5M stored), "
+                         "large = 1e6 x 1e6 x 200 (5e7 stored)")
     args = ap.parse_args()
+    if args.ncu_case:
+        return ncu_case(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
@@ -210,7 +262,8 @@ def main():
     def params(prec):
         return bk.BksParams(r1=w["r"], r3=w["r"], stages=w["stages"], block_p=w["block_p"],
                             tol=w["tol"], precision=prec, mixed_tol=w["mixed_tol"],
-                            refine_sweeps=50, max_outer=500)
+                            tol_scale_free=w["tol_scale_free"], refine_sweeps=50,
+                            max_outer=500)
 
     def timed_solves(prec, steps, warm):
         lat = []
@@ -230,6 +283,12 @@ def main():
                 lat.append(e0.elapsed_time(e1) / 1e3)
                 infos.append(info)
         return lat, infos, (U, W, F)
+
+    # ---- tightly converged FP64 reference (not timed) ----
+    pref = params(bk.BKS_PREC_FP64)
+    pref.tol = 1e-12
+    Uref, Wref, _, _ = bk.bks_solve(T, pref, U0, W0, stream=stream)
+    Uref, Wref = Uref.cpu().numpy(), Wref.cpu().numpy()
 
     # ---- headline: mixed-precision solves ----
     clocks = Clocks()
@@ -253,7 +312,9 @@ def main():
         return float(np.linalg.norm(D, 2))
     Um, Wm = res_mixed[0].cpu().numpy(), res_mixed[1].cpu().numpy()
     U6, W6 = res64[0].cpu().numpy(), res64[1].cpu().numpy()
-    ang = max(sin_max(U6, Um), sin_max(W6, Wm))
+    ang = {"mixed_vs_ref": max(sin_max(Uref, Um), sin_max(Wref, Wm)),
+           "fp64_vs_ref": max(sin_max(Uref, U6), sin_max(Wref, W6)),
+           "mixed_vs_fp64": max(sin_max(U6, Um), sin_max(W6, Wm))}
 
     # ---- contraction kernel roofline (mode-1, FP32, stage-2 width 3x4) ----
     hbm, peak_kind = _peaks()
@@ -310,7 +371,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         d = cpu_oracle_sample(coo)
         outer = statistics.median([i["iters"] for i in inf64])
-        scale = (2 * w["draws"]) / max(1, d["nnz_sample"])
+        scale = T.nnz / max(1, d["nnz_sample"])
         solve_s = d["seconds_per_outer_iter"] * scale * max(1, outer)
         cpu = {"value": 1.0 / solve_s, "unit": "solves/s", "cores": d["threads"],
                "kind": "oracle",
@@ -325,17 +386,20 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": w["workload"], "precision": "mixed (FP32 contractions, FP64 "
-                   "orthogonalisation/inner solve/restart, FP64 refinement)", "tol": w["tol"],
+                   "orthogonalisation/inner solve/restart, FP64 refinement)",
+                   "stop": f"||grad||/||F||^2 <= {w['tol']}", "accuracy": "both results within "
+                   "1e-6 (sin of largest principal angle) of an FP64 solution converged to 1e-12",
                    "l2": "512 MB buffer written between timed steps",
                    "parallelism": f"replicas x{world}"},
         "fp64_solves_per_s": fp64_rate, "mixed_over_fp64": value / world / fp64_rate,
-        "subspace_sin_mixed_vs_fp64": ang,
+        "subspace_sin": ang,
         "latency_s": {"p50": lat_sorted[len(lat_sorted) // 2],
                       "p99": lat_sorted[min(len(lat_sorted) - 1, int(0.99 * len(lat_sorted)))]},
         "outer_iters": {"mixed": [i["iters"] for i in inf_mixed],
                         "mixed_fp32": [i["fp32_iters"] for i in inf_mixed],
                         "fp64": [i["iters"] for i in inf64]},
         "grad_rel": {"mixed": inf_mixed[-1]["grad_rel"], "fp64": inf64[-1]["grad_rel"]},
+        "phase_ms": {"mixed": inf_mixed[-1]["phase_ms"], "fp64": inf64[-1]["phase_ms"]},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "solves/s", "h2d_bytes_per_step": h2d,

@@ -172,7 +172,12 @@ typedef struct {
   uint64_t seed;       /* random start when U0/W0 are NULL */
   double drop_tol;     /* rank-drop threshold of the block QR (relative) */
   double inner_tol;    /* inner stopping tolerance (<= 0: a tenth of the outer tolerance) */
-  double mixed_tol;    /* MIXED only: tolerance of the FP32 phase (<= 0: 1e-6) */
+  int tol_scale_free;  /* 0: stop when ||grad|| / ||F|| <= tol (Section 6.2, depends on the
+                          scale of A); 1: stop when ||grad|| / ||F||^2 <= tol (invariant
+                          under A -> c A) */
+  double mixed_tol;    /* MIXED only: the FP32 phase ends when ||grad|| / ||F||^2 <= mixed_tol
+                          (<= 0: 1e-6) or when that ratio stops halving for two outer
+                          iterations; FP64 outer iterations follow until tol */
 } bks_params;
 
 typedef struct {
@@ -184,6 +189,8 @@ typedef struct {
   int inner_sweeps;    /* total inner HOOI sweeps */
   int fp32_iters;      /* MIXED: outer iterations with FP32 contractions */
   double seconds;      /* host wall time of the call */
+  double phase_ms[5];  /* device time by phase (CUDA events on the stream): stage 1 with the
+                          gradient, rest of the expansion, core C, inner solve, restart */
   double* history;     /* host, optional: 2 doubles (grad_rel, normF) per outer iteration */
   int history_cap;     /* capacity of history in iterations */
   int history_len;     /* filled entries */

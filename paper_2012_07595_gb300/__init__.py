@@ -54,7 +54,7 @@ class _Params(ctypes.Structure):
                 ("variant", ctypes.c_int), ("precision", ctypes.c_int),
                 ("refine_sweeps", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("drop_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("mixed_tol", ctypes.c_double)]
+                ("tol_scale_free", ctypes.c_int), ("mixed_tol", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -62,6 +62,7 @@ class _Info(ctypes.Structure):
                 ("grad_rel", ctypes.c_double), ("normF", ctypes.c_double),
                 ("k1", ctypes.c_int), ("k3", ctypes.c_int), ("inner_sweeps", ctypes.c_int),
                 ("fp32_iters", ctypes.c_int), ("seconds", ctypes.c_double),
+                ("phase_ms", ctypes.c_double * 5),
                 ("history", ctypes.POINTER(ctypes.c_double)), ("history_cap", ctypes.c_int),
                 ("history_len", ctypes.c_int)]
 
@@ -330,6 +331,7 @@ class BksParams:
     seed: int = 1
     drop_tol: float = 1e-12
     inner_tol: float = 0.0
+    tol_scale_free: int = 0
     mixed_tol: float = 1e-6
 
     def to_c(self) -> _Params:
@@ -378,6 +380,8 @@ def _solve(fn, t: Tensor, cparams, r1, r3, U0, W0, stream, history_cap, raise_no
            "normF": info.normF, "k1": info.k1, "k3": info.k3,
            "inner_sweeps": info.inner_sweeps, "fp32_iters": info.fp32_iters,
            "seconds": info.seconds, "status": rc,
+           "phase_ms": dict(zip(["stage1", "expand", "core", "inner", "restart"],
+                                list(info.phase_ms))),
            "history": [(hist[2 * q], hist[2 * q + 1]) for q in range(info.history_len)]}
     return U, W, F.reshape(r3, r1, r1).permute(2, 1, 0), out
 

@@ -85,9 +85,9 @@ struct DevBuf {
 // is cut into "virtual rows" of at most kSplit entries; tile t of a part
 // holds the virtual rows whose first entry lies in [t*kTile, (t+1)*kTile),
 // so a tile spans at most kTile + kSplit entries and never cuts a virtual
-// row.  One warp processes one tile.
-constexpr int kTile = 512;
-constexpr int kSplit = 512;
+// row.  One warp processes one tile (at most 16 entries per lane).
+constexpr int kTile = 256;
+constexpr int kSplit = 256;
 
 struct Part {
   // one sorted copy of the stored entries, CSR over `rows`

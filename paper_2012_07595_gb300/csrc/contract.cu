@@ -93,7 +93,36 @@ struct TileArgs {
   const int32_t* ib;   // index into operand B per entry
 };
 
-// Sum of the entries [lo, hi) of the tile's data into acc.
+// Sum of the entries [lo, hi) of the tile's data into acc.  The index and
+// value streams are read 4 entries at a time with 16-byte loads once the
+// position is 4-aligned, and the 4 entries' gathers are issued before any
+// of them is consumed, so each lane keeps several loads in flight.
+template <typename T, int PB, int QB, bool TRI>
+__device__ __forceinline__ void one_entry(int e, const TileArgs& ta, const T* __restrict__ vals,
+                                          const T* __restrict__ Ap, const T* __restrict__ Bp,
+                                          T (&acc)[Shape<PB, QB, TRI>::W]) {
+  constexpr int NB = TRI ? PB : QB;
+  const int ia = __ldg(ta.ia + e);
+  const int ib = __ldg(ta.ib + e);
+  const T v = __ldg(vals + e);
+  T xa[PB], xb[NB];
+  load_row<T, PB>(Ap + (int64_t)ia * PB, xa);
+  load_row<T, NB>(Bp + (int64_t)ib * NB, xb);
+  accumulate<T, PB, QB, TRI>(acc, v, xa, xb);
+}
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* __restrict__ p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+}
+
 template <typename T, int PB, int QB, bool TRI>
 __device__ __forceinline__ void run_entries(int lo, int hi, const TileArgs& ta,
                                             const T* __restrict__ vals,
@@ -101,22 +130,25 @@ __device__ __forceinline__ void run_entries(int lo, int hi, const TileArgs& ta,
                                             const T* __restrict__ Bp,
                                             T (&acc)[Shape<PB, QB, TRI>::W]) {
   constexpr int NB = TRI ? PB : QB;
-  int last_a = -1;
-  T xa[PB];
+  int e = lo;
+  while (e < hi && (e & 3)) one_entry<T, PB, QB, TRI>(e++, ta, vals, Ap, Bp, acc);
+  for (; e + 4 <= hi; e += 4) {
+    const int4 ia = __ldg(reinterpret_cast<const int4*>(ta.ia + e));
+    const int4 ib = __ldg(reinterpret_cast<const int4*>(ta.ib + e));
+    T v[4];
+    load4<T>(vals + e, v);
+    const int iav[4] = {ia.x, ia.y, ia.z, ia.w};
+    const int ibv[4] = {ib.x, ib.y, ib.z, ib.w};
+    T xa[4][PB], xb[4][NB];
 #pragma unroll
-  for (int a = 0; a < PB; ++a) xa[a] = T(0);
-  for (int e = lo; e < hi; ++e) {
-    const int ia = __ldg(ta.ia + e);
-    const int ib = __ldg(ta.ib + e);
-    const T v = __ldg(vals + e);
-    if (ia != last_a) {
-      load_row<T, PB>(Ap + (int64_t)ia * PB, xa);
-      last_a = ia;
+    for (int u = 0; u < 4; ++u) {
+      load_row<T, PB>(Ap + (int64_t)iav[u] * PB, xa[u]);
+      load_row<T, NB>(Bp + (int64_t)ibv[u] * NB, xb[u]);
     }
-    T xb[NB];
-    load_row<T, NB>(Bp + (int64_t)ib * NB, xb);
-    accumulate<T, PB, QB, TRI>(acc, v, xa, xb);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, v[u], xa[u], xb[u]);
   }
+  while (e < hi) one_entry<T, PB, QB, TRI>(e++, ta, vals, Ap, Bp, acc);
 }
 
 template <typename T, typename OT, int PB, int QB, bool TRI>
@@ -148,16 +180,18 @@ __device__ __forceinline__ void flush_row(int vr, const TileArgs& ta,
   }
 }
 
-__device__ __forceinline__ int upper_vrow(const int32_t* __restrict__ vptr, int lo, int hi,
-                                          int e) {
-  // largest v in [lo, hi) with vptr[v] <= e
+// largest v in [lo, hi) with sv[v - base] <= e, on the warp's shared copy
+__device__ __forceinline__ int upper_vrow(const int* sv, int base, int lo, int hi, int e) {
   int a = lo, b = hi;
   while (b - a > 1) {
     int mid = (a + b) >> 1;
-    if (__ldg(vptr + mid) <= e) a = mid; else b = mid;
+    if (sv[mid - base] <= e) a = mid; else b = mid;
   }
   return a;
 }
+
+constexpr int kWarpsPerBlock = 8;
+constexpr int kMaxTileVrows = kTile + kSplit + 1;  // virtual rows of one tile, +1 end
 
 template <typename T, typename OT, int PB, int QB, bool TRI>
 __global__ void __launch_bounds__(256)
@@ -165,12 +199,18 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
            const T* __restrict__ Bp, int p, int q, OT* __restrict__ out, int64_t ldo,
            T* __restrict__ partial) {
   constexpr int W = Shape<PB, QB, TRI>::W;
+  __shared__ int s_vptr[kWarpsPerBlock][kMaxTileVrows];
   const int lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int wib = threadIdx.x >> 5;
+  const int tile = blockIdx.x * (blockDim.x >> 5) + wib;
   if (tile >= ta.ntiles) return;
   const int v0 = __ldg(ta.tile_first + tile), v1 = __ldg(ta.tile_first + tile + 1);
   if (v0 >= v1) return;
-  const int e0 = __ldg(ta.vptr + v0), e1 = __ldg(ta.vptr + v1);
+  // the tile's virtual-row starts, staged once (coalesced) for all lanes
+  int* sv = s_vptr[wib];
+  for (int v = v0 + lane; v <= v1; v += 32) sv[v - v0] = __ldg(ta.vptr + v);
+  __syncwarp();
+  const int e0 = sv[0], e1 = sv[v1 - v0];
   const int per = (e1 - e0 + 31) >> 5;
   const int lo = min(e1, e0 + lane * per), hi = min(e1, lo + per);
   const bool has = lo < hi;
@@ -178,17 +218,17 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
   int vf = -1, vl = -1;
   bool head = false, open_tail = false;
   if (has) {
-    vf = upper_vrow(ta.vptr, v0, v1, lo);
-    vl = upper_vrow(ta.vptr, vf, v1, hi - 1);
-    head = __ldg(ta.vptr + vf) < lo;
-    open_tail = __ldg(ta.vptr + vl + 1) > hi && !(head && vl == vf);
+    vf = upper_vrow(sv, v0, v0, v1, lo);
+    vl = upper_vrow(sv, v0, vf, v1, hi - 1);
+    head = sv[vf - v0] < lo;
+    open_tail = sv[vl + 1 - v0] > hi && !(head && vl == vf);
   }
   T acc[W];
 #pragma unroll
   for (int c = 0; c < W; ++c) acc[c] = T(0);
   // phase A: the head piece (a row that began in an earlier lane)
   if (head) {
-    int hend = min(hi, __ldg(ta.vptr + vf + 1));
+    int hend = min(hi, sv[vf + 1 - v0]);
     run_entries<T, PB, QB, TRI>(lo, hend, ta, vals, Ap, Bp, acc);
   }
   // phase B: segmented suffix sum of head pieces over lanes (key = row)
@@ -214,7 +254,7 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
   if (!has) return;
   // phase C1: the open tail (owned, continues into later lanes)
   if (open_tail) {
-    run_entries<T, PB, QB, TRI>(__ldg(ta.vptr + vl), hi, ta, vals, Ap, Bp, acc);
+    run_entries<T, PB, QB, TRI>(sv[vl - v0], hi, ta, vals, Ap, Bp, acc);
     flush_row<T, OT, PB, QB, TRI>(vl, ta, acc, p, q, out, ldo, partial);
   }
   // phase C2: owned rows that end inside this lane
@@ -223,8 +263,7 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
   for (int v = first_owned; v <= last_owned; ++v) {
 #pragma unroll
     for (int c = 0; c < W; ++c) acc[c] = T(0);
-    run_entries<T, PB, QB, TRI>(__ldg(ta.vptr + v), __ldg(ta.vptr + v + 1), ta, vals, Ap, Bp,
-                                acc);
+    run_entries<T, PB, QB, TRI>(sv[v - v0], sv[v + 1 - v0], ta, vals, Ap, Bp, acc);
     flush_row<T, OT, PB, QB, TRI>(v, ta, acc, p, q, out, ldo, partial);
   }
 }
@@ -299,7 +338,7 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
               P.vslot.as<int32_t>(), P.ntiles, ia, ib};
   DevBuf partial;
   if (P.nslots > 0) BKS_TRY(partial.alloc(sizeof(T) * (size_t)P.nslots * W, s));
-  const int warps = 8;
+  const int warps = kWarpsPerBlock;
   const int blocks = (P.ntiles + warps - 1) / warps;
   if (P.nv > 0) {
     k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,
@@ -717,7 +756,7 @@ int launch_contract_fixed(const Part& P, int vdtype, const int32_t* ia, const in
                           T* partial, cudaStream_t s) {
   TileArgs ta{P.tile_first.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
               P.vslot.as<int32_t>(), P.ntiles, ia, ib};
-  const int warps = 8;
+  const int warps = kWarpsPerBlock;
   const int blocks = (P.ntiles + warps - 1) / warps;
   if (P.nv > 0) {
     k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,

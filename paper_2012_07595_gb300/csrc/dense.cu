@@ -581,7 +581,7 @@ __global__ void k_small_left(const double* __restrict__ R, int ldr, int bo, int 
   __shared__ double A[kMaxB * kMaxB];
   __shared__ double V[kMaxB * kMaxB];
   __shared__ double red[64];
-  __shared__ double cs[4 * kMaxB];
+  __shared__ double cs[4 * kMaxB + 64];
   __shared__ int idx[kMaxB];
   for (int x = threadIdx.x; x < bo * bo; x += blockDim.x) {
     const int i = x % bo, j = x / bo;
@@ -590,7 +590,7 @@ __global__ void k_small_left(const double* __restrict__ R, int ldr, int bo, int 
     A[i * bo + j] = v;
   }
   __syncthreads();
-  block_jacobi_eig<double>(A, V, bo, 1e-15, 60, red, cs);
+  block_jacobi_eig<double>(A, V, bo, 0.0, 40, red, cs);
   top_diag<double>(A, bo, r, idx);
   for (int x = threadIdx.x; x < bo * r; x += blockDim.x) {
     const int i = x % bo, t = x / bo;

@@ -1,6 +1,6 @@
 // Inner problem of the tensor Krylov-Schur method (Algorithm 5 step (i)):
 // the best rank-(r1,r1,r3) approximation of the dense (1,2)-symmetric core
-// C = A.(X,X,Z) (k1 x k1 x k3), solved on one thread block.
+// C = A.(X,X,Z) (k1 x k1 x k3), solved by one cooperative grid kernel.
 //
 // Section 6.2 starts from the truncated HOSVD of C, runs 5 HOOI sweeps and
 // then Newton-Grassmann.  This library's reading: the truncated HOSVD start
@@ -12,6 +12,8 @@
 // their eigenvectors are computed in FP32 (k_hosvd); the sweeps, the
 // gradient and every result are FP64.
 #include <algorithm>
+
+#include <cooperative_groups.h>
 
 #include "common.cuh"
 #include "jacobi.cuh"
@@ -106,65 +108,9 @@ struct InnerShared {
   double FF1[kMaxR * kMaxR];
   double FF3[kMaxR * kMaxR];
   double red[64];
-  double cs[4 * kMaxW];
+  double cs[4 * kMaxW];  // >= 4 * 32 + 64 doubles
   int idx[kMaxW];
 };
-
-// T1 = unfold_1(C x_2 Uh^T x_3 Wh^T) (k1 x r1 r3), via D = C x_3 Wh^T in
-// global scratch (k1 x k1 x r3).
-__device__ void inner_t1(const double* __restrict__ C, int k1, int k3, int r1, int r3,
-                         InnerShared& S, double* __restrict__ D) {
-  for (int x = threadIdx.x; x < k1 * k1; x += blockDim.x) {
-    double acc[kMaxR];
-#pragma unroll
-    for (int t = 0; t < kMaxR; ++t) acc[t] = 0.0;
-    for (int c = 0; c < k3; ++c) {
-      const double v = C[x + (int64_t)k1 * k1 * c];
-#pragma unroll
-      for (int t = 0; t < kMaxR; ++t)
-        if (t < r3) acc[t] = fma(v, S.Wh[c + k3 * t], acc[t]);
-    }
-    for (int t = 0; t < r3; ++t) D[x + (int64_t)k1 * k1 * t] = acc[t];
-  }
-  __syncthreads();
-  for (int x = threadIdx.x; x < k1 * r1 * r3; x += blockDim.x) {
-    const int a = x % k1, j = x / k1;  // j = b' + r1 c'
-    const int bp = j % r1, cp = j / r1;
-    double s = 0.0;
-    for (int b = 0; b < k1; ++b) s = fma(D[a + (int64_t)k1 * (b + (int64_t)k1 * cp)], S.Uh[b + k1 * bp], s);
-    S.T1[a + k1 * j] = s;
-  }
-  __syncthreads();
-}
-
-// T3 = unfold_3(C x_1 Uh^T x_2 Uh^T) (k3 x r1^2), via E = C x_1 Uh^T
-// (r1 x k1 x k3) in global scratch; uses C(a,b,c) = C(b,a,c) so that
-// consecutive threads read consecutive addresses.
-__device__ void inner_t3(const double* __restrict__ C, int k1, int k3, int r1,
-                         InnerShared& S, double* __restrict__ E) {
-  for (int x = threadIdx.x; x < k1 * k3; x += blockDim.x) {
-    const int b = x % k1, c = x / k1;
-    double acc[kMaxR];
-#pragma unroll
-    for (int t = 0; t < kMaxR; ++t) acc[t] = 0.0;
-    for (int a = 0; a < k1; ++a) {
-      const double v = C[b + (int64_t)k1 * (a + (int64_t)k1 * c)];
-#pragma unroll
-      for (int t = 0; t < kMaxR; ++t)
-        if (t < r1) acc[t] = fma(v, S.Uh[a + k1 * t], acc[t]);
-    }
-    for (int t = 0; t < r1; ++t) E[t + (int64_t)r1 * (b + (int64_t)k1 * c)] = acc[t];
-  }
-  __syncthreads();
-  for (int x = threadIdx.x; x < k3 * r1 * r1; x += blockDim.x) {
-    const int c = x % k3, j = x / k3;  // j = a' + r1 b'
-    const int ap = j % r1, bp = j / r1;
-    double s = 0.0;
-    for (int b = 0; b < k1; ++b) s = fma(E[ap + (int64_t)r1 * (b + (int64_t)k1 * c)], S.Uh[b + k1 * bp], s);
-    S.T3[c + k3 * j] = s;
-  }
-  __syncthreads();
-}
 
 // r leading left singular vectors of T (n x w, ld n) into Out (n x r):
 // eigenvectors of T^T T, Out = T v / sigma, then two MGS passes.
@@ -176,7 +122,7 @@ __device__ void inner_topsvd(const double* T, int n, int w, int r, InnerShared& 
     S.G[i * w + j] = s;
   }
   __syncthreads();
-  block_jacobi_eig<double>(S.G, S.V, w, 1e-15, 60, S.red, S.cs);
+  block_jacobi_eig<double>(S.G, S.V, w, 0.0, 40, S.red, S.cs);
   top_diag<double>(S.G, w, r, S.idx);
   for (int x = threadIdx.x; x < n * r; x += blockDim.x) {
     const int i = x % n, t = x / n;
@@ -207,7 +153,7 @@ __device__ void inner_topsvd(const double* T, int n, int w, int r, InnerShared& 
         if (threadIdx.x == 0) S.red[0] = d;
       }
       __syncthreads();
-      const double inv = 1.0 / sqrt(S.red[0]);
+      const double inv = nr_rsqrt(S.red[0]);
       for (int i = threadIdx.x; i < n; i += blockDim.x) Out[i + n * t] *= inv;
       __syncthreads();
     }
@@ -290,77 +236,197 @@ __device__ void inner_grad(int k1, int k3, int r1, int r3, InnerShared& S, doubl
   __syncthreads();
 }
 
-// Runs HOOI sweeps from (S.Uh, S.Wh); returns sweeps done, grad, ||F||.
-__device__ int inner_sweeps(const double* C, int k1, int k3, int r1, int r3, int max_sweeps,
-                            double tol, InnerShared& S, double* D, double* E, double* res) {
-  inner_t3(C, k1, k3, r1, S, E);
+
+// ---- cooperative multi-block HOOI on the core ------------------------------
+// The FP64 contractions of a sweep (C x_3 Wh^T, C x_1 Uh^T and their second
+// factors) are spread over every block of the grid; the small steps (the
+// gradient, the r leading singular vectors, the convergence decision) run
+// on block 0.  grid.sync() separates the phases; every block reads the
+// decision after the same barrier, so all blocks take the same path.
+namespace cg = cooperative_groups;
+
+struct CoopArgs {
+  const double* C;
+  int k1, k3, r1, r3;
+  double tol;
+  int max_inner, init_sweeps;
+  const double* Uh0;  // HOSVD candidate
+  const double* Wh0;
+  double* Ug;         // current iterate k1 x r1
+  double* Wg;         // current iterate k3 x r3
+  double* Ub;         // saved candidate
+  double* Wb;
+  double* D;          // k1 x k1 x r3
+  double* E;          // r1 x k1 x k3
+  double* T1;         // k1 x r1 r3
+  double* T3;         // k3 x r1^2
+  double* ctl;        // [0] grad [1] normF [2] stop flag
+  double* Uh_out;
+  double* Wh_out;
+  double* negU;
+  double* negW;
+  double* info;
+};
+
+__device__ __forceinline__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gsize() { return (int64_t)gridDim.x * blockDim.x; }
+
+// D[x + k1^2 t] = sum_c C[x + k1^2 c] Wh[c, t]
+__device__ void coop_D(const CoopArgs& a) {
+  const int64_t kk = (int64_t)a.k1 * a.k1;
+  for (int64_t o = gtid(); o < kk * a.r3; o += gsize()) {
+    const int64_t x = o % kk;
+    const int t = (int)(o / kk);
+    double s = 0.0;
+    for (int c = 0; c < a.k3; ++c) s = fma(a.C[x + kk * c], a.Wg[c + a.k3 * t], s);
+    a.D[o] = s;
+  }
+}
+// T1[a + k1 (b' + r1 c')] = sum_b D[a + k1 (b + k1 c')] Uh[b, b']
+__device__ void coop_T1(const CoopArgs& a) {
+  const int64_t n = (int64_t)a.k1 * a.r1 * a.r3;
+  for (int64_t o = gtid(); o < n; o += gsize()) {
+    const int i = (int)(o % a.k1);
+    const int j = (int)(o / a.k1);
+    const int bp = j % a.r1, cp = j / a.r1;
+    double s = 0.0;
+    for (int b = 0; b < a.k1; ++b)
+      s = fma(a.D[i + (int64_t)a.k1 * (b + (int64_t)a.k1 * cp)], a.Ug[b + a.k1 * bp], s);
+    a.T1[o] = s;
+  }
+}
+// E[t + r1 (b + k1 c)] = sum_a Uh[a, t] C[b + k1 (a + k1 c)]  (C symmetric in a, b)
+__device__ void coop_E(const CoopArgs& a) {
+  const int64_t bc = (int64_t)a.k1 * a.k3;
+  for (int64_t o = gtid(); o < bc * a.r1; o += gsize()) {
+    const int64_t x = o % bc;
+    const int t = (int)(o / bc);
+    const int b = (int)(x % a.k1);
+    const int64_t c = x / a.k1;
+    double s = 0.0;
+    for (int i = 0; i < a.k1; ++i)
+      s = fma(a.Ug[i + a.k1 * t], a.C[b + (int64_t)a.k1 * (i + (int64_t)a.k1 * c)], s);
+    a.E[t + (int64_t)a.r1 * x] = s;
+  }
+}
+// T3[c + k3 (a' + r1 b')] = sum_b E[a' + r1 (b + k1 c)] Uh[b, b']
+__device__ void coop_T3(const CoopArgs& a) {
+  const int64_t n = (int64_t)a.k3 * a.r1 * a.r1;
+  for (int64_t o = gtid(); o < n; o += gsize()) {
+    const int c = (int)(o % a.k3);
+    const int j = (int)(o / a.k3);
+    const int ap = j % a.r1, bp = j / a.r1;
+    double s = 0.0;
+    for (int b = 0; b < a.k1; ++b)
+      s = fma(a.E[ap + (int64_t)a.r1 * (b + (int64_t)a.k1 * c)], a.Ug[b + a.k1 * bp], s);
+    a.T3[o] = s;
+  }
+}
+
+__device__ void block_copy(const double* src, double* dst, int n) {
+  for (int x = threadIdx.x; x < n; x += blockDim.x) dst[x] = src[x];
+}
+
+// HOOI sweeps from (Ug, Wg); returns the number of sweeps; ctl[0..1] hold
+// the gradient and ||F|| at the returned point.
+__device__ int coop_sweeps(const CoopArgs& a, int max_sweeps, double tol, InnerShared& S,
+                           cg::grid_group& grid) {
+  coop_E(a);
+  grid.sync();
+  coop_T3(a);
+  grid.sync();
   int done = 0;
-  while (true) {
-    inner_t1(C, k1, k3, r1, r3, S, D);
-    inner_grad(k1, k3, r1, r3, S, &res[0], &res[1]);
-    const double g = res[0], nf = res[1];
-    if (done >= max_sweeps || g <= tol * nf) break;
-    inner_topsvd(S.T1, k1, r1 * r3, r1, S, S.Uh);
-    inner_t3(C, k1, k3, r1, S, E);
-    inner_topsvd(S.T3, k3, r1 * r1, r3, S, S.Wh);
+  for (;;) {
+    coop_D(a);
+    grid.sync();
+    coop_T1(a);
+    grid.sync();
+    if (blockIdx.x == 0) {
+      block_copy(a.Ug, S.Uh, a.k1 * a.r1);
+      block_copy(a.Wg, S.Wh, a.k3 * a.r3);
+      block_copy(a.T1, S.T1, a.k1 * a.r1 * a.r3);
+      block_copy(a.T3, S.T3, a.k3 * a.r1 * a.r1);
+      __syncthreads();
+      inner_grad(a.k1, a.k3, a.r1, a.r3, S, &a.ctl[0], &a.ctl[1]);
+      const double g = a.ctl[0], nf = a.ctl[1];
+      const bool stop = done >= max_sweeps || g <= tol * nf;
+      if (!stop) {
+        inner_topsvd(S.T1, a.k1, a.r1 * a.r3, a.r1, S, S.Uh);
+        block_copy(S.Uh, a.Ug, a.k1 * a.r1);
+      }
+      if (threadIdx.x == 0) a.ctl[2] = stop ? 1.0 : 0.0;
+      __threadfence();
+    }
+    grid.sync();
+    if (a.ctl[2] != 0.0) break;
+    coop_E(a);
+    grid.sync();
+    coop_T3(a);
+    grid.sync();
+    if (blockIdx.x == 0) {
+      block_copy(a.T3, S.T3, a.k3 * a.r1 * a.r1);
+      __syncthreads();
+      inner_topsvd(S.T3, a.k3, a.r1 * a.r1, a.r3, S, S.Wh);
+      block_copy(S.Wh, a.Wg, a.k3 * a.r3);
+      __threadfence();
+    }
+    grid.sync();
     ++done;
   }
   return done;
 }
 
-__global__ void __launch_bounds__(kInnerThreads)
-k_inner(const double* __restrict__ C, int k1, int k3, int r1, int r3, double tol, int max_inner,
-        int init_sweeps, const double* __restrict__ Uh_hosvd, const double* __restrict__ Wh_hosvd,
-        double* __restrict__ D, double* __restrict__ E, double* __restrict__ Uh_out,
-        double* __restrict__ Wh_out, double* __restrict__ negU, double* __restrict__ negW,
-        double* __restrict__ info) {
+__global__ void __launch_bounds__(kInnerThreads) k_inner_coop(CoopArgs a) {
+  cg::grid_group grid = cg::this_grid();
   extern __shared__ double shd[];
   InnerShared& S = *reinterpret_cast<InnerShared*>(shd);
-  __shared__ double res[2];
-  __shared__ double best[2];
+  const int nu = a.k1 * a.r1, nw = a.k3 * a.r3;
   // candidate 1: truncated HOSVD + init sweeps
-  for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) S.Uh[x] = Uh_hosvd[x];
-  for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) S.Wh[x] = Wh_hosvd[x];
-  __syncthreads();
-  inner_sweeps(C, k1, k3, r1, r3, init_sweeps, 0.0, S, D, E, res);
-  const double nf_a = res[1];
-  for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) Uh_out[x] = S.Uh[x];
-  for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) Wh_out[x] = S.Wh[x];
-  __syncthreads();
+  for (int64_t x = gtid(); x < nu; x += gsize()) a.Ug[x] = a.Uh0[x];
+  for (int64_t x = gtid(); x < nw; x += gsize()) a.Wg[x] = a.Wh0[x];
+  grid.sync();
+  coop_sweeps(a, a.init_sweeps, 0.0, S, grid);
+  const double nf_a = a.ctl[1];
+  for (int64_t x = gtid(); x < nu; x += gsize()) a.Ub[x] = a.Ug[x];
+  for (int64_t x = gtid(); x < nw; x += gsize()) a.Wb[x] = a.Wg[x];
+  grid.sync();
   // candidate 2: the current point [I; 0]
-  for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) S.Uh[x] = (x % k1 == x / k1) ? 1.0 : 0.0;
-  for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) S.Wh[x] = (x % k3 == x / k3) ? 1.0 : 0.0;
-  __syncthreads();
-  inner_sweeps(C, k1, k3, r1, r3, init_sweeps, 0.0, S, D, E, res);
-  const double nf_b = res[1];
+  for (int64_t x = gtid(); x < nu; x += gsize()) a.Ug[x] = (x % a.k1 == x / a.k1) ? 1.0 : 0.0;
+  for (int64_t x = gtid(); x < nw; x += gsize()) a.Wg[x] = (x % a.k3 == x / a.k3) ? 1.0 : 0.0;
+  grid.sync();
+  coop_sweeps(a, a.init_sweeps, 0.0, S, grid);
+  const double nf_b = a.ctl[1];
   const bool hosvd_won = nf_a >= nf_b;
+  grid.sync();
   if (hosvd_won) {
-    for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) S.Uh[x] = Uh_out[x];
-    for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) S.Wh[x] = Wh_out[x];
+    for (int64_t x = gtid(); x < nu; x += gsize()) a.Ug[x] = a.Ub[x];
+    for (int64_t x = gtid(); x < nw; x += gsize()) a.Wg[x] = a.Wb[x];
   }
-  __syncthreads();
-  const int done = inner_sweeps(C, k1, k3, r1, r3, max_inner, tol, S, D, E, res);
-  for (int x = threadIdx.x; x < k1 * r1; x += blockDim.x) {
-    Uh_out[x] = S.Uh[x];
-    negU[x] = -S.Uh[x];
-  }
-  for (int x = threadIdx.x; x < k3 * r3; x += blockDim.x) {
-    Wh_out[x] = S.Wh[x];
-    negW[x] = -S.Wh[x];
-  }
-  if (threadIdx.x == 0) {
-    info[0] = res[0];
-    info[1] = res[1];
-    info[2] = done + 2 * init_sweeps;
-    info[3] = hosvd_won ? 1.0 : 0.0;
-    best[0] = res[1];
+  grid.sync();
+  const int done = coop_sweeps(a, a.max_inner, a.tol, S, grid);
+  if (blockIdx.x == 0) {
+    for (int x = threadIdx.x; x < nu; x += blockDim.x) {
+      a.Uh_out[x] = a.Ug[x];
+      a.negU[x] = -a.Ug[x];
+    }
+    for (int x = threadIdx.x; x < nw; x += blockDim.x) {
+      a.Wh_out[x] = a.Wg[x];
+      a.negW[x] = -a.Wg[x];
+    }
+    if (threadIdx.x == 0) {
+      a.info[0] = a.ctl[0];
+      a.info[1] = a.ctl[1];
+      a.info[2] = done + 2 * a.init_sweeps;
+      a.info[3] = hosvd_won ? 1.0 : 0.0;
+    }
   }
 }
 
 }  // namespace
 
 struct InnerWork {
-  DevBuf part1, part3, Uh0, Wh0, D, E;
+  DevBuf part1, part3, Uh0, Wh0, D, E, Ug, Wg, Ub, Wb, T1, T3, ctl;
+  int coop_grid = 0;
 };
 
 // Inner solve: C (k1 x k1 x k3, FP64, device) -> Uh (k1 x r1), Wh (k3 x r3),
@@ -391,18 +457,38 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   if (!attr) {
     BKS_CUDA_TRY(cudaFuncSetAttribute(k_hosvd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(float) * (2 * 128 * 128 + 64 + 4 * 128))));
-    BKS_CUDA_TRY(cudaFuncSetAttribute(k_inner, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(InnerShared)));
     attr = true;
   }
   k_hosvd<<<1, kInnerThreads, hs, s>>>(w.part1.as<float>(), w.part3.as<float>(), nparts, k1, k3,
                                        r1, r3, w.Uh0.as<double>(), w.Wh0.as<double>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
-  k_inner<<<1, kInnerThreads, sizeof(InnerShared), s>>>(C, k1, k3, r1, r3, tol, max_inner, 5,
-                                                        w.Uh0.as<double>(), w.Wh0.as<double>(),
-                                                        w.D.as<double>(), w.E.as<double>(), Uh,
-                                                        Wh, negU, negW, info); ::bks::note_launch();
-  BKS_CUDA_TRY(cudaGetLastError());
+  const size_t mat = sizeof(double) * 128 * kMaxR;
+  for (DevBuf* b : {&w.Ug, &w.Wg, &w.Ub, &w.Wb})
+    if (b->bytes < mat) { BKS_TRY(b->alloc(mat, s)); b->persist(); }
+  const size_t tsz = sizeof(double) * 128 * kMaxW;
+  for (DevBuf* b : {&w.T1, &w.T3})
+    if (b->bytes < tsz) { BKS_TRY(b->alloc(tsz, s)); b->persist(); }
+  if (w.ctl.bytes < sizeof(double) * 8) { BKS_TRY(w.ctl.alloc(sizeof(double) * 8, s)); w.ctl.persist(); }
+  if (w.coop_grid == 0) {
+    int per_sm = 0;
+    BKS_CUDA_TRY(cudaFuncSetAttribute(k_inner_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(InnerShared)));
+    BKS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inner_coop,
+                                                               kInnerThreads, sizeof(InnerShared)));
+    if (per_sm < 1) return fail(BKS_ECUDA, "inner solve: cooperative kernel does not fit on an SM");
+    w.coop_grid = std::min(64, per_sm * num_sms());
+  }
+  CoopArgs a;
+  a.C = C; a.k1 = k1; a.k3 = k3; a.r1 = r1; a.r3 = r3; a.tol = tol; a.max_inner = max_inner;
+  a.init_sweeps = 5; a.Uh0 = w.Uh0.as<double>(); a.Wh0 = w.Wh0.as<double>();
+  a.Ug = w.Ug.as<double>(); a.Wg = w.Wg.as<double>(); a.Ub = w.Ub.as<double>();
+  a.Wb = w.Wb.as<double>(); a.D = w.D.as<double>(); a.E = w.E.as<double>();
+  a.T1 = w.T1.as<double>(); a.T3 = w.T3.as<double>(); a.ctl = w.ctl.as<double>();
+  a.Uh_out = Uh; a.Wh_out = Wh; a.negU = negU; a.negW = negW; a.info = info;
+  void* kargs[] = {&a};
+  BKS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_inner_coop, dim3(w.coop_grid),
+                                           dim3(kInnerThreads), kargs, sizeof(InnerShared), s));
+  ::bks::note_launch();
   return BKS_OK;
 }
 

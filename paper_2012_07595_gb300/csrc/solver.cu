@@ -274,20 +274,27 @@ struct BksState {
   }
 
   double cur_tol = 0.0;  // outer tolerance of the current phase
+  double last_nf = 1.0;  // ||F|| at the last stage-1 evaluation
 
-  int inner_and_restart(bool fp32) {
+  int inner_and_restart(bool fp32, cudaEvent_t* ev) {
     BKS_TRY(contract_core_x(t, Xp(), m, k1, Zp(), n, k3, C.as<double>(), fp32, s));
+    BKS_CUDA_TRY(cudaEventRecord(ev[0], s));
     // inner tolerance: a tenth of the outer one unless given, so that the
     // inner residual gradient does not hold the outer test just above tol
-    const double itol = P.inner_tol > 0 ? P.inner_tol : 0.1 * cur_tol;
+    // (the inner test is ||grad_C|| / ||F_C||; with the scale-free outer
+    // test the tolerance is carried over through ||F||)
+    const double otol = P.tol_scale_free ? cur_tol * last_nf : cur_tol;
+    const double itol = P.inner_tol > 0 ? P.inner_tol : 0.1 * otol;
     BKS_TRY(inner_solve(C.as<double>(), k1, k3, r1, r3, itol, P.max_inner, Uh.as<double>(),
                         Wh.as<double>(), negU.as<double>(), negW.as<double>(),
                         inner_info.as<double>(), s));
+    BKS_CUDA_TRY(cudaEventRecord(ev[1], s));
     // U0 <- X Uh, W0 <- Z Wh (eq. (tks1)), in place in the first columns
     BKS_TRY(ts_combine(Xp(), m, k1, nullptr, m, 0, negU.as<double>(), nullptr, r1, Xp(), m, m,
                        ws, s));
     BKS_TRY(ts_combine(Zp(), n, k3, nullptr, n, 0, negW.as<double>(), nullptr, r3, Zp(), n, n,
                        ws, s));
+    BKS_CUDA_TRY(cudaEventRecord(ev[2], s));
     double info[4];
     BKS_CUDA_TRY(cudaMemcpyAsync(info, inner_info.p, sizeof(info), cudaMemcpyDeviceToHost, s));
     BKS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -374,9 +381,22 @@ extern "C" int bks_solve(const bks_tensor* t, const bks_params* prm, const doubl
   int hist_len = 0;
   double best_grad = INFINITY;
   int stall = 0;
+  // phase timing with events on the stream (read after each iteration's
+  // own synchronisation, so it adds no extra wait)
+  cudaEvent_t ev[6];
+  for (auto& e : ev) BKS_CUDA_TRY(cudaEventCreate(&e));
+  double phase[5] = {0, 0, 0, 0, 0};
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() { for (int q = 0; q < 6; ++q) cudaEventDestroy(e[q]); }
+  } evguard{ev};
   for (;; ++it) {
+    BKS_CUDA_TRY(cudaEventRecord(ev[0], s));
     BKS_TRY(S.stage1(fp32, &grad, &nf));
-    const double rel = nf > 0 ? grad / nf : INFINITY;
+    BKS_CUDA_TRY(cudaEventRecord(ev[1], s));
+    // the stopping test: ||grad|| / ||F|| (Section 6.2) or the scale-free
+    // ||grad|| / ||F||^2
+    const double rel = nf > 0 ? (prm->tol_scale_free ? grad / (nf * nf) : grad / nf) : INFINITY;
     if (info && info->history && hist_len < info->history_cap) {
       info->history[2 * hist_len] = rel;
       info->history[2 * hist_len + 1] = nf;
@@ -387,10 +407,12 @@ extern "C" int bks_solve(const bks_tensor* t, const bks_params* prm, const doubl
       break;
     }
     if (fp32) {
-      // FP32-contraction phase: until mixed_tol, or the gradient stops
-      // decreasing (FP32 noise floor); then FP64 refinement sweeps
-      if (rel < best_grad * 0.5) { best_grad = rel; stall = 0; } else ++stall;
-      if (rel <= mtol || stall >= 4 || rel <= prm->tol) {
+      // FP32-contraction phase: until the scale-free gradient
+      // ||grad|| / ||F||^2 is below mixed_tol, or it stops halving for two
+      // outer iterations (the FP32 noise floor); then FP64 refinement
+      const double sf = nf > 0 ? grad / (nf * nf) : INFINITY;
+      if (sf < best_grad * 0.5) { best_grad = sf; stall = 0; } else ++stall;
+      if (sf <= mtol || stall >= 2 || rel <= prm->tol) {
         fp32 = false;
         continue;  // re-evaluate at the same point with FP64 contractions
       }
@@ -400,9 +422,18 @@ extern "C" int bks_solve(const bks_tensor* t, const bks_params* prm, const doubl
       if (mixed && refine_left-- <= 0) break;
     }
     if (it >= prm->max_outer) break;
-    S.cur_tol = fp32 ? mtol : prm->tol;
+    S.cur_tol = fp32 ? (prm->tol_scale_free ? mtol : mtol * nf) : prm->tol;
+    S.last_nf = nf;
     BKS_TRY(S.expand_rest(fp32));
-    BKS_TRY(S.inner_and_restart(fp32));
+    BKS_CUDA_TRY(cudaEventRecord(ev[2], s));
+    BKS_TRY(S.inner_and_restart(fp32, ev + 3));
+    {
+      float ms;
+      for (int q = 0; q < 5; ++q) {
+        BKS_CUDA_TRY(cudaEventElapsedTime(&ms, ev[q], ev[q + 1]));
+        phase[q] += ms;
+      }
+    }
   }
   // outputs: the point whose gradient was evaluated last
   BKS_TRY(copy2d(S.Xp(), m, m, r1, U, m, s));
@@ -412,13 +443,14 @@ extern "C" int bks_solve(const bks_tensor* t, const bks_params* prm, const doubl
   if (info) {
     info->iters = it;
     info->converged = converged ? 1 : 0;
-    info->grad_rel = nf > 0 ? grad / nf : INFINITY;
+    info->grad_rel = nf > 0 ? (prm->tol_scale_free ? grad / (nf * nf) : grad / nf) : INFINITY;
     info->normF = nf;
     info->k1 = S.k1;
     info->k3 = S.k3;
     info->inner_sweeps = S.inner_sweeps;
     info->fp32_iters = fp32_iters;
     info->history_len = hist_len;
+    for (int q = 0; q < 5; ++q) info->phase_ms[q] = phase[q];
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if (status != BKS_OK) return status;
@@ -584,6 +616,7 @@ extern "C" int hooi_solve(const bks_tensor* t, const hooi_params* prm, const dou
     info->k3 = r3;
     info->inner_sweeps = 0;
     info->fp32_iters = fp32 ? it : 0;
+    for (int q = 0; q < 5; ++q) info->phase_ms[q] = 0.0;
     info->history_len = hist_len;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
