@@ -216,6 +216,66 @@ def ncu_case(args):
     print(f"ncu case {args.ncu_case} ({args.size}) done: nnz {T.nnz}")
 
 
+def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
+    """The batched form (many small solves on concurrent streams, work tiles
+    autotuned per size class) and the serving loop (Poisson arrivals,
+    admission by a 150 GB budget, continuous batching), both on jobs drawn
+    as the batched workload (sizes scaled by `scale`), mixed precision at
+    the scale-free tolerance 1e-9, against the same jobs solved one at a
+    time in FP64."""
+    jobs = synth.batch_jobs(seed=4, count=n_batch, scale=scale)
+    coos = [synth.job_tensor(j) for j in jobs]
+
+    def prm(r, prec):
+        return bk.BksParams(r1=r, r3=r, stages=2, block_p=4, tol=1e-9, tol_scale_free=1,
+                            precision=prec, mixed_tol=1e-6, refine_sweeps=50, max_outer=300)
+
+    tens = [bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v) for c in coos]
+    for T in tens[:4]:
+        bk.bks_tensor_autotune(T)   # warm the library's kernels
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = bk.bks_batch_solve(tens, [prm(j["r"], bk.BKS_PREC_MIXED) for j in jobs],
+                             nstreams=8, autotune=True, stream=stream)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    ok = sum(1 for r in res if r[4] == 0)
+    t0 = time.perf_counter()
+    for T, j in zip(tens, jobs):
+        try:
+            bk.bks_solve(T, prm(j["r"], bk.BKS_PREC_FP64), stream=stream)
+        except bk.BksError:
+            pass
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    batched = {"jobs": n_batch, "ok": ok, "solves_per_s": n_batch / t_batch,
+               "sequential_fp64_solves_per_s": n_batch / t_seq,
+               "speedup_vs_sequential_fp64": t_seq / t_batch, "streams": 8,
+               "scale": scale, "nnz_stored_total": int(sum(T.nnz for T in tens))}
+    del tens
+    # serving: Poisson arrivals, mean gap 5 ms
+    arrivals, sjobs = synth.serving_stream(seed=5, requests=n_serve, scale=scale)
+    scoos = [synth.job_tensor(j) for j in sjobs]
+    with bk.Server(150 << 30, max_slots=8, autotune=True) as srv:
+        start = time.perf_counter()
+        tickets = []
+        for a, j, c in zip(arrivals, sjobs, scoos):
+            now = time.perf_counter() - start
+            if a > now:
+                time.sleep(a - now)
+            tickets.append(srv.submit(c.m, c.n, c.i, c.j, c.k, c.v,
+                                      prm(j["r"], bk.BKS_PREC_MIXED)))
+        outs = [srv.poll(t, wait=True) for t in tickets]
+        wall = time.perf_counter() - start
+    lat = sorted(o["latency_s"] for o in outs)
+    serving = {"requests": n_serve, "ok": sum(1 for o in outs if o["status"] == 0),
+               "solves_per_s": n_serve / wall, "offered_per_s": n_serve / float(arrivals[-1]),
+               "latency_p50_s": lat[len(lat) // 2],
+               "latency_p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+               "slots": 8, "budget_bytes": 150 << 30, "scale": scale}
+    return batched, serving
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,6 +283,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-scale", type=float, default=0.1,
+                    help="size scale of the batched/serving jobs (1.0 = m up to 2e5 and "
+                         "up to 5M stored entries per job); 0 skips them")
+    ap.add_argument("--batch-jobs", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--ncu-case", default=None,
                     help="profiling entry: build the workload, run a few launches of one "
                          "kernel family (mode1, mode3, core, solve) and exit without a JSON line")
@@ -366,6 +431,12 @@ def main():
         Th.close()
     e2e_rate = world * e2e_steps / sum(t_e2e)
 
+    # ---- batched form and serving loop (scaled job sizes, see the keys) ----
+    batched = serving = None
+    if args.batch_scale > 0:
+        batched, serving = batch_and_serve(bk, torch, args.batch_scale, args.batch_jobs,
+                                           args.serve_requests, stream)
+
     # ---- CPU oracle baseline (bounded sample) ----
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -404,6 +475,8 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "batched": batched,
+        "serving": serving,
         "gpu_launches": int(launches),
         "clocks": clk,
     }

@@ -51,6 +51,9 @@ extern "C" {
 #define BKS_EBREAKDOWN   -6  /* a basis block collapsed to zero width where one is required */
 #define BKS_ENUMERIC     -7  /* NaN or Inf in ||F|| or in the gradient */
 #define BKS_EUNSUPPORTED -8  /* a size beyond the limits above */
+#define BKS_ECANCELED    -9  /* the job was cancelled (server) */
+#define BKS_EPENDING    -10  /* the job has not finished yet (server poll without wait) */
+#define BKS_EBUDGET     -11  /* the job alone needs more device memory than the server's budget */
 
 /* ---- dtypes, flags, options -------------------------------------------- */
 #define BKS_F32 1
@@ -230,6 +233,89 @@ void hooi_params_default(hooi_params* p);
 int hooi_solve(const bks_tensor* t, const hooi_params* prm, const double* U0,
                const double* W0, double* U, double* W, double* F,
                bks_info* info, void* stream);
+
+/* ---- work-tile autotuning ------------------------------------------------
+ * The contractions process a tensor in warp tiles: rows longer than `split`
+ * entries are cut into pieces of at most `split`, and a tile holds the
+ * pieces that start in a window of `tile` entries (see the contraction
+ * comments).  The best sizes depend on how the entries spread over rows.
+ * bks_tensor_autotune times the mode-1 and triangle mode-3 contractions
+ * (FP32, widths 4 x 4) under the plans (tile, split) in {(128,128),
+ * (256,256), (512,512), (256,512)} and keeps the fastest; tile and split
+ * (host, nullable) receive the choice.  bks_tensor_set_tiles applies a
+ * known choice (32 <= tile, split <= 512).  Both synchronise `stream`. */
+int bks_tensor_autotune(bks_tensor* t, int* tile, int* split, void* stream);
+int bks_tensor_set_tiles(bks_tensor* t, int tile, int split, void* stream);
+
+/* ---- batched solves -------------------------------------------------------
+ * bks_batch_solve: njobs independent BKS solves (bks_solve semantics per
+ * job) on tensors already stored on the device.  The jobs run on
+ * `nstreams` streams at once (one host worker thread per stream), so the
+ * kernels of different jobs overlap on the GPU; with
+ * BKS_BATCH_AUTOTUNE each tensor first gets the work-tile plan of its size
+ * class (log2 of the stored entries), tuned once per class.
+ *   T[njobs], P[njobs]: tensors and parameters (host arrays of pointers /
+ *     structs).
+ *   U0, W0: host arrays of device pointers (or NULL arrays / entries: seeded
+ *     random start).  U, W, F: host arrays of device output pointers.
+ *   info[njobs] (host, nullable): per-job info; status[njobs] (host,
+ *     nullable): per-job return code.
+ * Returns BKS_OK when every job returned BKS_OK, else the first failing
+ * job's code (the other jobs still ran).  The caller's `stream` is made to
+ * wait for all jobs. */
+#define BKS_BATCH_AUTOTUNE 1
+int bks_batch_solve(int njobs, bks_tensor* const* T, const bks_params* P,
+                    const double* const* U0, const double* const* W0, double* const* U,
+                    double* const* W, double* const* F, bks_info* info, int* status,
+                    int nstreams, int flags, void* stream);
+
+/* ---- serving: continuous batching under a device-memory budget -----------
+ * A server owns `max_slots` worker threads, each with its own stream.
+ * Submitted jobs (host COO + parameters) wait in a FIFO queue; the head job
+ * is admitted as soon as a slot is free and its predicted device memory
+ * fits into `hbm_budget` minus what the running jobs hold, so jobs that
+ * arrive while others run join the GPU as slots and memory free up.  A
+ * running job keeps its tensor, Krylov bases and inner-solve state on the
+ * device until it completes; results are copied to host memory.
+ * Predicted bytes of a job: 72 * nnz + 8 * (m + n) * 168 + 64 MiB (ingest
+ * sort buffers, two sorted copies, bases and workspace).
+ * flags: BKS_SERVE_AUTOTUNE tunes the work tiles per size class. */
+#define BKS_SERVE_AUTOTUNE 1
+typedef struct bks_server bks_server;
+
+/* Create (device = the current device of the calling thread).  Returns
+ * NULL on failure (bks_last_error_string). */
+bks_server* bks_server_create(size_t hbm_budget, int max_slots, int flags);
+
+/* Submit a job: m, n, nnz, i, j, k, v, vdtype, coo_flags as
+ * bks_tensor_create_coo (host pointers; the data are copied), prm its BKS
+ * parameters.  *ticket receives the job's ticket.  BKS_EBUDGET if the job
+ * alone exceeds the budget; BKS_EINVAL for bad arguments. */
+int bks_server_submit(bks_server* srv, int64_t m, int64_t n, int64_t nnz, const int32_t* i,
+                      const int32_t* j, const int32_t* k, const void* v, int vdtype,
+                      int coo_flags, const bks_params* prm, uint64_t* ticket);
+
+/* Poll a job.  Not finished: BKS_EPENDING (wait = 0) or block until it
+ * finishes (wait != 0).  Finished: BKS_OK; *job_status receives the job's
+ * own return code (BKS_OK, BKS_ENOTCONV, BKS_ECANCELED, an ingest error
+ * ...); U (m x r1), W (n x r3), F (r1 r1 r3) are HOST buffers (nullable)
+ * that receive the result; latency_s (nullable) receives completion minus
+ * submission time.  The ticket is retired by a successful poll
+ * (BKS_EINVAL afterwards). */
+int bks_server_poll(bks_server* srv, uint64_t ticket, int wait, double* U, double* W, double* F,
+                    bks_info* info, int* job_status, double* latency_s);
+
+/* Cancel a job: a queued job is removed, a running one stops at its next
+ * outer iteration; either way it finishes with BKS_ECANCELED. */
+int bks_server_cancel(bks_server* srv, uint64_t ticket);
+
+/* Host counters (nullable outputs): jobs queued, running, finished and not
+ * yet polled, device bytes currently held by running jobs. */
+int bks_server_stats(bks_server* srv, int* queued, int* running, int* finished,
+                     size_t* resident_bytes);
+
+/* Cancel what is still queued or running, wait for the workers, free. */
+void bks_server_destroy(bks_server* srv);
 
 /* Last error message of the calling thread ("" if none). */
 const char* bks_last_error_string(void);

@@ -24,12 +24,17 @@ __all__ = [
     "BKS_VARIANT_MIN", "BKS_VARIANT_MAX", "BksError", "Tensor", "bks_tensor_create_coo",
     "bks_tensor_destroy", "bks_tensor_info", "bks_tensor_export_coo", "bks_contract_mode1",
     "bks_contract_mode3", "bks_core", "bks_solve", "hooi_solve", "BksParams", "HooiParams",
-    "col_major", "library_path", "bks_launch_count",
+    "col_major", "library_path", "bks_launch_count", "bks_tensor_autotune",
+    "bks_tensor_set_tiles", "bks_batch_solve", "Server", "BKS_ECANCELED", "BKS_EPENDING",
+    "BKS_EBUDGET",
 ]
 
 BKS_OK = 0
 BKS_EINVAL, BKS_ENOMEM, BKS_ECUDA, BKS_EASYM = -1, -2, -3, -4
 BKS_ENOTCONV, BKS_EBREAKDOWN, BKS_ENUMERIC, BKS_EUNSUPPORTED = -5, -6, -7, -8
+BKS_ECANCELED, BKS_EPENDING, BKS_EBUDGET = -9, -10, -11
+BKS_BATCH_AUTOTUNE = 1
+BKS_SERVE_AUTOTUNE = 1
 BKS_F32, BKS_F64 = 1, 2
 BKS_MIRROR, BKS_VALIDATE_SYMMETRIC, BKS_INPUT_ON_DEVICE = 1, 2, 4
 BKS_PREC_FP64, BKS_PREC_MIXED = 0, 1
@@ -38,7 +43,8 @@ BKS_VARIANT_BK, BKS_VARIANT_MIN, BKS_VARIANT_MAX = 0, 1, 2
 _ERRNAMES = {BKS_EINVAL: "BKS_EINVAL", BKS_ENOMEM: "BKS_ENOMEM", BKS_ECUDA: "BKS_ECUDA",
              BKS_EASYM: "BKS_EASYM", BKS_ENOTCONV: "BKS_ENOTCONV",
              BKS_EBREAKDOWN: "BKS_EBREAKDOWN", BKS_ENUMERIC: "BKS_ENUMERIC",
-             BKS_EUNSUPPORTED: "BKS_EUNSUPPORTED"}
+             BKS_EUNSUPPORTED: "BKS_EUNSUPPORTED", BKS_ECANCELED: "BKS_ECANCELED",
+             BKS_EPENDING: "BKS_EPENDING", BKS_EBUDGET: "BKS_EBUDGET"}
 
 
 class BksError(RuntimeError):
@@ -124,6 +130,30 @@ def lib():
     L.hooi_solve.argtypes = [vp, ctypes.POINTER(_HooiParams), vp, vp, vp, vp, vp,
                              ctypes.POINTER(_Info), vp]
     L.hooi_solve.restype = c_int
+    L.bks_tensor_autotune.argtypes = [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), vp]
+    L.bks_tensor_autotune.restype = c_int
+    L.bks_tensor_set_tiles.argtypes = [vp, c_int, c_int, vp]
+    L.bks_tensor_set_tiles.restype = c_int
+    L.bks_batch_solve.argtypes = [c_int, ctypes.POINTER(vp), ctypes.POINTER(_Params),
+                                  ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                  ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(_Info),
+                                  ctypes.POINTER(c_int), c_int, c_int, vp]
+    L.bks_batch_solve.restype = c_int
+    L.bks_server_create.argtypes = [ctypes.c_size_t, c_int, c_int]
+    L.bks_server_create.restype = vp
+    L.bks_server_submit.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, c_int, c_int,
+                                    ctypes.POINTER(_Params), ctypes.POINTER(ctypes.c_uint64)]
+    L.bks_server_submit.restype = c_int
+    L.bks_server_poll.argtypes = [vp, ctypes.c_uint64, c_int, vp, vp, vp, ctypes.POINTER(_Info),
+                                  ctypes.POINTER(c_int), ctypes.POINTER(dbl)]
+    L.bks_server_poll.restype = c_int
+    L.bks_server_cancel.argtypes = [vp, ctypes.c_uint64]
+    L.bks_server_cancel.restype = c_int
+    L.bks_server_stats.argtypes = [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                   ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_size_t)]
+    L.bks_server_stats.restype = c_int
+    L.bks_server_destroy.argtypes = [vp]
+    L.bks_server_destroy.restype = None
     L.bks_launch_count.argtypes = []
     L.bks_launch_count.restype = ctypes.c_uint64
     L.bks_last_error_string.argtypes = []
@@ -401,3 +431,142 @@ def hooi_solve(t: Tensor, params: Optional[HooiParams] = None, U0=None, W0=None,
     params = params or HooiParams()
     return _solve(lib().hooi_solve, t, params.to_c(), params.r1, params.r3, U0, W0, stream,
                   history_cap, raise_notconv)
+
+
+def bks_tensor_autotune(t: Tensor, stream=None):
+    """Pick the contraction work tiles of this tensor by timing; returns
+    (tile, split)."""
+    tile, split = ctypes.c_int(), ctypes.c_int()
+    _check(lib().bks_tensor_autotune(t.handle, ctypes.byref(tile), ctypes.byref(split),
+                                     _stream(stream)))
+    return tile.value, split.value
+
+
+def bks_tensor_set_tiles(t: Tensor, tile: int, split: int, stream=None):
+    _check(lib().bks_tensor_set_tiles(t.handle, tile, split, _stream(stream)))
+
+
+def bks_batch_solve(tensors, params, U0s=None, W0s=None, nstreams: int = 4,
+                    autotune: bool = True, stream=None):
+    """Independent BKS solves run concurrently on `nstreams` streams.
+    Returns a list of (U, W, F, info, status) per job."""
+    import torch
+    n = len(tensors)
+    params = list(params) if isinstance(params, (list, tuple)) else [params] * n
+    Ts = (ctypes.c_void_p * n)(*[t.handle.value for t in tensors])
+    Ps = (_Params * n)(*[p.to_c() for p in params])
+    outs = []
+    keep = []
+    for q in range(n):
+        r1, r3 = params[q].r1, params[q].r3
+        U = _empty_cm(tensors[q].m, r1, torch.float64, "cuda")
+        W = _empty_cm(tensors[q].n, r3, torch.float64, "cuda")
+        F = torch.empty(r1 * r1 * r3, dtype=torch.float64, device="cuda")
+        outs.append((U, W, F))
+
+    def ptrs(xs):
+        return (ctypes.c_void_p * n)(*[(x.data_ptr() if x is not None else 0) for x in xs])
+
+    u0 = w0 = None
+    if U0s is not None:
+        keep = [x.to(device="cuda", dtype=torch.float64).t().contiguous().t() for x in U0s]
+        u0 = ptrs(keep)
+    if W0s is not None:
+        keepw = [x.to(device="cuda", dtype=torch.float64).t().contiguous().t() for x in W0s]
+        keep += keepw
+        w0 = ptrs(keepw)
+    infos = (_Info * n)()
+    status = (ctypes.c_int * n)()
+    lib().bks_batch_solve(n, Ts, Ps, u0, w0, ptrs([o[0] for o in outs]),
+                          ptrs([o[1] for o in outs]), ptrs([o[2] for o in outs]), infos, status,
+                          nstreams, BKS_BATCH_AUTOTUNE if autotune else 0, _stream(stream))
+    res = []
+    for q in range(n):
+        r1, r3 = params[q].r1, params[q].r3
+        i = infos[q]
+        d = {"iters": i.iters, "converged": bool(i.converged), "grad_rel": i.grad_rel,
+             "normF": i.normF, "k1": i.k1, "k3": i.k3, "fp32_iters": i.fp32_iters,
+             "seconds": i.seconds}
+        U, W, F = outs[q]
+        res.append((U, W, F.reshape(r3, r1, r1).permute(2, 1, 0), d, status[q]))
+    return res
+
+
+class Server:
+    """Continuous-batching BKS server: jobs wait in a FIFO queue and are
+    admitted as slots and device memory (the budget) free up."""
+
+    def __init__(self, hbm_budget: int, max_slots: int = 4, autotune: bool = True):
+        h = lib().bks_server_create(int(hbm_budget), int(max_slots),
+                                    BKS_SERVE_AUTOTUNE if autotune else 0)
+        if not h:
+            raise BksError(BKS_EINVAL, lib().bks_last_error_string().decode())
+        self._h = ctypes.c_void_p(h)
+        self._shapes = {}
+
+    def submit(self, m, n, i, j, k, v, params: BksParams, mirror: bool = True) -> int:
+        ii, jj, kk = (np.ascontiguousarray(x, dtype=np.int32) for x in (i, j, k))
+        vv = np.ascontiguousarray(v)
+        vdt = BKS_F64 if vv.dtype == np.float64 else BKS_F32
+        if vv.dtype not in (np.float64, np.float32):
+            raise TypeError("values must be float32 or float64")
+        t = ctypes.c_uint64()
+        cp = params.to_c()
+        _check(lib().bks_server_submit(self._h, m, n, ii.size,
+                                       *[ctypes.c_void_p(x.ctypes.data if x.size else 0)
+                                         for x in (ii, jj, kk, vv)],
+                                       vdt, BKS_MIRROR if mirror else 0, ctypes.byref(cp),
+                                       ctypes.byref(t)))
+        self._shapes[t.value] = (m, n, params.r1, params.r3)
+        return t.value
+
+    def poll(self, ticket: int, wait: bool = True):
+        """None while pending (wait=False); else a dict with U, W, F (numpy),
+        info, status and latency."""
+        m, n, r1, r3 = self._shapes[ticket]
+        U = np.empty((m, r1), order="F")
+        W = np.empty((n, r3), order="F")
+        F = np.empty(r1 * r1 * r3)
+        info = _Info()
+        st = ctypes.c_int()
+        lat = ctypes.c_double()
+        rc = lib().bks_server_poll(self._h, ticket, 1 if wait else 0,
+                                   ctypes.c_void_p(U.ctypes.data), ctypes.c_void_p(W.ctypes.data),
+                                   ctypes.c_void_p(F.ctypes.data), ctypes.byref(info),
+                                   ctypes.byref(st), ctypes.byref(lat))
+        if rc == BKS_EPENDING:
+            return None
+        _check(rc)
+        del self._shapes[ticket]
+        return {"U": U, "W": W, "F": F.reshape(r1, r1, r3, order="F"), "status": st.value,
+                "latency_s": lat.value, "iters": info.iters, "converged": bool(info.converged),
+                "normF": info.normF, "grad_rel": info.grad_rel,
+                "error": lib().bks_last_error_string().decode() if st.value else ""}
+
+    def cancel(self, ticket: int):
+        _check(lib().bks_server_cancel(self._h, ticket))
+
+    def stats(self):
+        q, r, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        b = ctypes.c_size_t()
+        _check(lib().bks_server_stats(self._h, ctypes.byref(q), ctypes.byref(r), ctypes.byref(f),
+                                      ctypes.byref(b)))
+        return {"queued": q.value, "running": r.value, "finished": f.value,
+                "resident_bytes": b.value}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().bks_server_destroy(self._h)
+        self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

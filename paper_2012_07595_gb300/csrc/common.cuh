@@ -81,13 +81,16 @@ struct DevBuf {
 };
 
 // ---- stored tensor layout -------------------------------------------------
-// Work tiles of the sparse contractions.  A row longer than kSplit entries
-// is cut into "virtual rows" of at most kSplit entries; tile t of a part
-// holds the virtual rows whose first entry lies in [t*kTile, (t+1)*kTile),
-// so a tile spans at most kTile + kSplit entries and never cuts a virtual
-// row.  One warp processes one tile (at most 16 entries per lane).
+// Work tiles of the sparse contractions.  A row longer than `split`
+// entries is cut into "virtual rows" of at most `split` entries; tile t of a
+// part holds the virtual rows whose first entry lies in
+// [t*tile, (t+1)*tile), so a tile spans at most tile + split entries and
+// never cuts a virtual row.  One warp processes one tile.  The sizes are per
+// tensor (defaults below; bks_tensor_autotune picks them by timing).
 constexpr int kTile = 256;
 constexpr int kSplit = 256;
+constexpr int kMaxTile = 512;
+constexpr int kMaxSplit = 512;
 
 struct Part {
   // one sorted copy of the stored entries, CSR over `rows`
@@ -99,6 +102,7 @@ struct Part {
   DevBuf v32;      // float [nnz] when the input dtype is double
   DevBuf v64;      // double [nnz] when the input dtype is float
   // tile plan
+  int tile = kTile, split = kSplit;
   int32_t nv = 0, ntiles = 0, nslots = 0, nsplit = 0;
   DevBuf vptr;        // int32 [nv+1]   first entry of each virtual row
   DevBuf vrow;        // int32 [nv]     row of each virtual row

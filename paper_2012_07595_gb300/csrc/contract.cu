@@ -191,7 +191,7 @@ __device__ __forceinline__ int upper_vrow(const int* sv, int base, int lo, int h
 }
 
 constexpr int kWarpsPerBlock = 8;
-constexpr int kMaxTileVrows = kTile + kSplit + 1;  // virtual rows of one tile, +1 end
+constexpr int kMaxTileVrows = kMaxTile + kMaxSplit + 1;  // virtual rows of one tile, +1 end
 
 template <typename T, typename OT, int PB, int QB, bool TRI>
 __global__ void __launch_bounds__(256)

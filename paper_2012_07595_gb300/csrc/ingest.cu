@@ -183,12 +183,12 @@ __global__ void k_gather_mode3(const uint64_t* keys, const uint32_t* pay, int64_
 }
 
 // ---- tile plan ------------------------------------------------------------
-__global__ void k_vcount(const int32_t* ptr, int64_t rows, int32_t* nvr, int32_t* nslot,
-                         int32_t* issplit, int32_t* isempty) {
+__global__ void k_vcount(const int32_t* ptr, int64_t rows, int split, int32_t* nvr,
+                         int32_t* nslot, int32_t* issplit, int32_t* isempty) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
        r += (int64_t)gridDim.x * blockDim.x) {
     int32_t len = ptr[r + 1] - ptr[r];
-    int32_t c = (len + kSplit - 1) / kSplit;
+    int32_t c = (len + split - 1) / split;
     nvr[r] = c;
     nslot[r] = c > 1 ? c : 0;
     issplit[r] = c > 1 ? 1 : 0;
@@ -201,7 +201,7 @@ __global__ void k_empty_list(const int32_t* isempty, const int32_t* pos, int64_t
        r += (int64_t)gridDim.x * blockDim.x)
     if (isempty[r]) out[pos[r]] = (int32_t)r;
 }
-__global__ void k_vfill(const int32_t* ptr, int64_t rows, const int32_t* vbase,
+__global__ void k_vfill(const int32_t* ptr, int64_t rows, int split, const int32_t* vbase,
                         const int32_t* nvr, const int32_t* slotbase, const int32_t* splitpos,
                         int32_t* vptr, int32_t* vrow, int32_t* vslot, int32_t* split_row,
                         int32_t* split_first) {
@@ -210,7 +210,7 @@ __global__ void k_vfill(const int32_t* ptr, int64_t rows, const int32_t* vbase,
     int32_t c = nvr[r];
     for (int32_t t = 0; t < c; ++t) {
       int32_t v = vbase[r] + t;
-      vptr[v] = ptr[r] + t * kSplit;
+      vptr[v] = ptr[r] + t * split;
       vrow[v] = (int32_t)r;
       vslot[v] = c > 1 ? slotbase[r] + t : -1;
     }
@@ -220,11 +220,12 @@ __global__ void k_vfill(const int32_t* ptr, int64_t rows, const int32_t* vbase,
     }
   }
 }
-__global__ void k_tile_first(const int32_t* vptr, int32_t nv, int32_t ntiles, int32_t* tf) {
+__global__ void k_tile_first(const int32_t* vptr, int32_t nv, int32_t ntiles, int tile,
+                             int32_t* tf) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntiles;
        t += (int64_t)gridDim.x * blockDim.x) {
     if (t == ntiles) { tf[t] = nv; continue; }
-    int64_t target = t * (int64_t)kTile;
+    int64_t target = t * (int64_t)tile;
     int32_t lo = 0, hi = nv;
     while (lo < hi) {
       int32_t mid = (lo + hi) >> 1;
@@ -413,7 +414,7 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
   BKS_TRY(slotbase.alloc(sizeof(int32_t) * R, s));
   BKS_TRY(splitpos.alloc(sizeof(int32_t) * R, s));
   BKS_TRY(tot.alloc(sizeof(int32_t) * 4, s));
-  k_vcount<<<grid_for(R), 256, 0, s>>>(P.ptr.as<int32_t>(), R, nvr.as<int32_t>(),
+  k_vcount<<<grid_for(R), 256, 0, s>>>(P.ptr.as<int32_t>(), R, P.split, nvr.as<int32_t>(),
                                        nslot.as<int32_t>(), issplit.as<int32_t>(),
                                        isempty.as<int32_t>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
@@ -431,14 +432,14 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
   BKS_TRY(P.empty_rows.alloc(sizeof(int32_t) * std::max(P.nempty, 1), s));
   k_empty_list<<<grid_for(R), 256, 0, s>>>(isempty.as<int32_t>(), emptypos.as<int32_t>(), R,
                                            P.empty_rows.as<int32_t>()); ::bks::note_launch();
-  P.ntiles = (int32_t)(nnz / kTile + 1);
+  P.ntiles = (int32_t)(nnz / P.tile + 1);
   BKS_TRY(P.vptr.alloc(sizeof(int32_t) * (P.nv + 1), s));
   BKS_TRY(P.vrow.alloc(sizeof(int32_t) * std::max(P.nv, 1), s));
   BKS_TRY(P.vslot.alloc(sizeof(int32_t) * std::max(P.nv, 1), s));
   BKS_TRY(P.split_row.alloc(sizeof(int32_t) * std::max(P.nsplit, 1), s));
   BKS_TRY(P.split_first.alloc(sizeof(int32_t) * (P.nsplit + 1), s));
   BKS_TRY(P.tile_first.alloc(sizeof(int32_t) * (P.ntiles + 1), s));
-  k_vfill<<<grid_for(R), 256, 0, s>>>(P.ptr.as<int32_t>(), R, vbase.as<int32_t>(),
+  k_vfill<<<grid_for(R), 256, 0, s>>>(P.ptr.as<int32_t>(), R, P.split, vbase.as<int32_t>(),
                                       nvr.as<int32_t>(), slotbase.as<int32_t>(),
                                       splitpos.as<int32_t>(), P.vptr.as<int32_t>(),
                                       P.vrow.as<int32_t>(), P.vslot.as<int32_t>(),
@@ -451,9 +452,10 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
   BKS_CUDA_TRY(cudaMemcpyAsync(P.split_first.as<int32_t>() + P.nsplit, &ns, sizeof(int32_t),
                                cudaMemcpyHostToDevice, s));
   k_tile_first<<<grid_for(P.ntiles + 1), 256, 0, s>>>(P.vptr.as<int32_t>(), P.nv, P.ntiles,
-                                                      P.tile_first.as<int32_t>()); ::bks::note_launch();
+                                                      P.tile, P.tile_first.as<int32_t>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   BKS_CUDA_TRY(cudaStreamSynchronize(s));  // host copies above read stack values
+  P.persist();
   return BKS_OK;
 }
 

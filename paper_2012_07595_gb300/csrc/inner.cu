@@ -478,6 +478,10 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
     if (per_sm < 1) return fail(BKS_ECUDA, "inner solve: cooperative kernel does not fit on an SM");
     w.coop_grid = std::min(64, per_sm * num_sms());
   }
+  // blocks in proportion to the largest contraction phase (512 outputs per
+  // block), so that small cores leave the GPU to concurrent jobs
+  const int64_t work = std::max<int64_t>((int64_t)k1 * k1 * r3, (int64_t)k1 * k3 * r1);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(w.coop_grid, (work + 511) / 512));
   CoopArgs a;
   a.C = C; a.k1 = k1; a.k3 = k3; a.r1 = r1; a.r3 = r3; a.tol = tol; a.max_inner = max_inner;
   a.init_sweeps = 5; a.Uh0 = w.Uh0.as<double>(); a.Wh0 = w.Wh0.as<double>();
@@ -486,7 +490,7 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   a.T1 = w.T1.as<double>(); a.T3 = w.T3.as<double>(); a.ctl = w.ctl.as<double>();
   a.Uh_out = Uh; a.Wh_out = Wh; a.negU = negU; a.negW = negW; a.info = info;
   void* kargs[] = {&a};
-  BKS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_inner_coop, dim3(w.coop_grid),
+  BKS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_inner_coop, dim3(grid),
                                            dim3(kInnerThreads), kargs, sizeof(InnerShared), s));
   ::bks::note_launch();
   return BKS_OK;

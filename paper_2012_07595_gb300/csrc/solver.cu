@@ -3,6 +3,7 @@
 // sequences launches and reads a few scalars per outer iteration (the
 // gradient test and the number of columns each block QR keeps); every
 // arithmetic step runs in the library's kernels on the caller's stream.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <set>
@@ -355,9 +356,21 @@ extern "C" void hooi_params_default(hooi_params* p) {
   p->seed = 1;
 }
 
+namespace bks {
+int solve_impl(const bks_tensor* t, const bks_params* prm, const double* U0, const double* W0,
+               double* U, double* W, double* F, bks_info* info, cudaStream_t stream,
+               const std::atomic<int>* cancel);
+}
+
 extern "C" int bks_solve(const bks_tensor* t, const bks_params* prm, const double* U0,
                          const double* W0, double* U, double* W, double* F, bks_info* info,
                          void* stream) {
+  return bks::solve_impl(t, prm, U0, W0, U, W, F, info, (cudaStream_t)stream, nullptr);
+}
+
+int bks::solve_impl(const bks_tensor* t, const bks_params* prm, const double* U0,
+                    const double* W0, double* U, double* W, double* F, bks_info* info,
+                    cudaStream_t stream, const std::atomic<int>* cancel) {
   BKS_TRY(check_params(t, prm));
   if (!U || !W || !F) return fail(BKS_EINVAL, "null output");
   const auto t0 = std::chrono::steady_clock::now();
@@ -391,6 +404,10 @@ extern "C" int bks_solve(const bks_tensor* t, const bks_params* prm, const doubl
     ~EvGuard() { for (int q = 0; q < 6; ++q) cudaEventDestroy(e[q]); }
   } evguard{ev};
   for (;; ++it) {
+    if (cancel && cancel->load(std::memory_order_relaxed)) {
+      status = fail(BKS_ECANCELED, "solve cancelled");
+      break;
+    }
     BKS_CUDA_TRY(cudaEventRecord(ev[0], s));
     BKS_TRY(S.stage1(fp32, &grad, &nf));
     BKS_CUDA_TRY(cudaEventRecord(ev[1], s));
