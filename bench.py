@@ -228,7 +228,8 @@ def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
 
     def prm(r, prec):
         return bk.BksParams(r1=r, r3=r, stages=2, block_p=4, tol=1e-9, tol_scale_free=1,
-                            precision=prec, mixed_tol=1e-6, refine_sweeps=50, max_outer=300)
+                            precision=prec, mixed_tol=1e-6, refine_sweeps=50, max_outer=200,
+                            max_inner=100)
 
     tens = [bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v) for c in coos]
     for T in tens[:4]:

@@ -130,7 +130,8 @@ int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
  *   Scratch (the packed copies of X and Y and the partial sums of long
  *   rows) lives in a fixed 32 MiB device array inside the library, which
  *   every GPU that loads the library keeps until the process exits; a call
- *   needing more (about 4*8*m + 4*8*n + 8*32*(nnz/512) bytes in FP64)
+ *   needing more (about 4*8*m + 4*8*n + 8*32*(nnz/split) bytes in FP64,
+ *   split = 256 unless bks_tensor_autotune / set_tiles chose another)
  *   returns BKS_EUNSUPPORTED before launching anything.  The call allocates
  *   nothing.  Its first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
@@ -174,7 +175,9 @@ typedef struct {
   int refine_sweeps;   /* MIXED only: FP64 outer iterations after the FP32 phase converged */
   uint64_t seed;       /* random start when U0/W0 are NULL */
   double drop_tol;     /* rank-drop threshold of the block QR (relative) */
-  double inner_tol;    /* inner stopping tolerance (<= 0: a tenth of the outer tolerance) */
+  double inner_tol;    /* inner stopping tolerance on ||grad_C|| / ||F_C|| (<= 0: inexact
+                          inner solves, max(tol / 10, ||grad|| / ||F|| / 100) at the
+                          current outer point) */
   int tol_scale_free;  /* 0: stop when ||grad|| / ||F|| <= tol (Section 6.2, depends on the
                           scale of A); 1: stop when ||grad|| / ||F||^2 <= tol (invariant
                           under A -> c A) */
@@ -200,7 +203,9 @@ typedef struct {
 } bks_info;
 
 /* Default parameters: r1 = r3 = 2, s = 2, p = 4, tol 1e-10, max_outer 500,
- * max_inner 1000, BK, FP64, refine 1, seed 1, drop_tol 1e-12. */
+ * max_inner 1000, BK, FP64, refine 1, seed 1, drop_tol 1e-14 (a rank-drop threshold
+ * well below the gradient accuracy: near convergence the stage-1 residual
+ * columns that carry the gradient are small relative to their raw norms). */
 void bks_params_default(bks_params* p);
 
 /* bks_solve: tensor Krylov-Schur (Algorithm 5 with U = V, X = Y).

@@ -359,7 +359,7 @@ class BksParams:
     precision: int = BKS_PREC_FP64
     refine_sweeps: int = 1
     seed: int = 1
-    drop_tol: float = 1e-12
+    drop_tol: float = 1e-14
     inner_tol: float = 0.0
     tol_scale_free: int = 0
     mixed_tol: float = 1e-6

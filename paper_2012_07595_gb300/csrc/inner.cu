@@ -4,9 +4,10 @@
 //
 // Section 6.2 starts from the truncated HOSVD of C, runs 5 HOOI sweeps and
 // then Newton-Grassmann.  This library's reading: the truncated HOSVD start
-// and the current point (Uh = [I;0], Wh = [I;0]) each get 5 symmetric HOOI
-// sweeps; the one with the larger ||F|| continues with HOOI sweeps until
-// its G-gradient is below tol * ||F|| or max_inner sweeps are done.
+// gets 5 symmetric HOOI sweeps; if its ||F|| is below that of the current
+// point (Uh = [I;0], Wh = [I;0]) the current point is taken instead; the
+// chosen start continues with HOOI sweeps until its G-gradient is below
+// tol * ||F|| or max_inner sweeps are done.
 //
 // The HOSVD start only seeds the iteration, so its two Gram matrices and
 // their eigenvectors are computed in FP32 (k_hosvd); the sweeps, the
@@ -390,11 +391,11 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_coop(CoopArgs a) {
   for (int64_t x = gtid(); x < nu; x += gsize()) a.Ub[x] = a.Ug[x];
   for (int64_t x = gtid(); x < nw; x += gsize()) a.Wb[x] = a.Wg[x];
   grid.sync();
-  // candidate 2: the current point [I; 0]
+  // candidate 2: the current point [I; 0], evaluated without sweeps
   for (int64_t x = gtid(); x < nu; x += gsize()) a.Ug[x] = (x % a.k1 == x / a.k1) ? 1.0 : 0.0;
   for (int64_t x = gtid(); x < nw; x += gsize()) a.Wg[x] = (x % a.k3 == x / a.k3) ? 1.0 : 0.0;
   grid.sync();
-  coop_sweeps(a, a.init_sweeps, 0.0, S, grid);
+  coop_sweeps(a, 0, 0.0, S, grid);
   const double nf_b = a.ctl[1];
   const bool hosvd_won = nf_a >= nf_b;
   grid.sync();
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_coop(CoopArgs a) {
     if (threadIdx.x == 0) {
       a.info[0] = a.ctl[0];
       a.info[1] = a.ctl[1];
-      a.info[2] = done + 2 * a.init_sweeps;
+      a.info[2] = done + a.init_sweeps;
       a.info[3] = hosvd_won ? 1.0 : 0.0;
     }
   }

@@ -276,6 +276,7 @@ struct BksState {
 
   double cur_tol = 0.0;  // outer tolerance of the current phase
   double last_nf = 1.0;  // ||F|| at the last stage-1 evaluation
+  double last_grad_rel = 0.0;  // ||grad|| / ||F|| there
 
   int inner_and_restart(bool fp32, cudaEvent_t* ev) {
     BKS_TRY(contract_core_x(t, Xp(), m, k1, Zp(), n, k3, C.as<double>(), fp32, s));
@@ -285,7 +286,10 @@ struct BksState {
     // (the inner test is ||grad_C|| / ||F_C||; with the scale-free outer
     // test the tolerance is carried over through ||F||)
     const double otol = P.tol_scale_free ? cur_tol * last_nf : cur_tol;
-    const double itol = P.inner_tol > 0 ? P.inner_tol : 0.1 * otol;
+    // inexact inner solves: a hundred times below the current outer
+    // gradient, and at least a tenth of the outer tolerance (this library's
+    // reading; Section 6.2 uses the outer tolerance throughout)
+    const double itol = P.inner_tol > 0 ? P.inner_tol : std::max(0.1 * otol, 0.01 * last_grad_rel);
     BKS_TRY(inner_solve(C.as<double>(), k1, k3, r1, r3, itol, P.max_inner, Uh.as<double>(),
                         Wh.as<double>(), negU.as<double>(), negW.as<double>(),
                         inner_info.as<double>(), s));
@@ -339,7 +343,7 @@ extern "C" void bks_params_default(bks_params* p) {
   p->precision = BKS_PREC_FP64;
   p->refine_sweeps = 1;
   p->seed = 1;
-  p->drop_tol = 1e-12;
+  p->drop_tol = 1e-14;
   p->inner_tol = 0.0;
   p->mixed_tol = 1e-6;
 }
@@ -441,6 +445,7 @@ int bks::solve_impl(const bks_tensor* t, const bks_params* prm, const double* U0
     if (it >= prm->max_outer) break;
     S.cur_tol = fp32 ? (prm->tol_scale_free ? mtol : mtol * nf) : prm->tol;
     S.last_nf = nf;
+    S.last_grad_rel = nf > 0 ? grad / nf : 0.0;
     BKS_TRY(S.expand_rest(fp32));
     BKS_CUDA_TRY(cudaEventRecord(ev[2], s));
     BKS_TRY(S.inner_and_restart(fp32, ev + 3));

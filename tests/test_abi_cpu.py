@@ -36,10 +36,10 @@ def test_params_defaults_without_gpu():
     p = bk._Params()
     bk.lib().bks_params_default(ctypes.byref(p))
     assert (p.r1, p.r3, p.stages, p.block_p) == (2, 2, 2, 4)
-    assert p.tol == 1e-10 and p.drop_tol == 1e-12
+    assert p.tol == 1e-10 and p.drop_tol == 1e-14
     h = bk._HooiParams()
     bk.lib().hooi_params_default(ctypes.byref(h))
     assert h.grad_every == 10
     # the Python dataclass mirrors the C defaults
     d = bk.BksParams()
-    assert (d.r1, d.r3, d.stages, d.block_p, d.tol, d.drop_tol) == (2, 2, 2, 4, 1e-10, 1e-12)
+    assert (d.r1, d.r3, d.stages, d.block_p, d.tol, d.drop_tol) == (2, 2, 2, 4, 1e-10, 1e-14)
