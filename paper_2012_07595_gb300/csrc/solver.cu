@@ -65,6 +65,40 @@ __global__ void k_tri_weight(double* __restrict__ T, int64_t n, int r1) {
   }
 }
 
+// Refinement form of the core (mixed precision, FP64 phase): overwrite the
+// blocks of C that carry first-order information at the current point
+// (U, W) = (X[:, :r1], Z[:, :r3]) with FP64 values from the stage-1
+// contractions:
+//   C[x, b, c] = C[b, x, c] = (X^T A.(U,W)_{2,3})[x, b + r1 c]  (b < r1, c < r3)
+//   C[a, b, c] = C[b, a, c] = (Z^T A.(U,U)_{1,2})[c, a + b(b+1)/2] (a <= b < r1, c >= r3)
+// G1 = [X M1]^T M1 ((k1 + r1 r3) x r1 r3), G3 = [Z M3]^T M3 ((k3 + w3) x w3).
+// Each entry is written by one thread only (x < r1 only when x <= b; the
+// mode-3 block only where c >= r3), so the result is deterministic.
+__global__ void k_core_patch(double* __restrict__ C, int k1, int k3, int r1, int r3,
+                             const double* __restrict__ G1, const double* __restrict__ G3) {
+  const int w1 = r1 * r3, w3 = r1 * (r1 + 1) / 2;
+  const int n1 = k1 * w1, n3 = w3 * (k3 - r3);
+  const int64_t kk = (int64_t)k1 * k1;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n1 + n3; o += gridDim.x * blockDim.x) {
+    if (o < n1) {
+      const int x = o % k1, j = o / k1, b = j % r1, c = j / r1;
+      if (x < r1 && x > b) continue;
+      const double v = G1[x + (int64_t)(k1 + w1) * j];
+      C[x + (int64_t)k1 * b + kk * c] = v;
+      C[b + (int64_t)k1 * x + kk * c] = v;
+    } else {
+      const int y = o - n1;
+      const int c = r3 + y % (k3 - r3), t = y / (k3 - r3);
+      int b = 0;
+      while ((b + 1) * (b + 2) / 2 <= t) ++b;
+      const int a = t - b * (b + 1) / 2;
+      const double v = G3[c + (int64_t)(k3 + w3) * t];
+      C[a + (int64_t)k1 * b + kk * c] = v;
+      C[b + (int64_t)k1 * a + kk * c] = v;
+    }
+  }
+}
+
 inline int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 32));
@@ -135,6 +169,9 @@ struct BksState {
   bks_params P{};
   DenseWork ws;
   DevBuf X, Z, H1, F3wT, C, Uh, Wh, negU, negW, inner_info, scal;
+  // refinement form: FP64 stage-1 contractions kept for the core patch
+  DevBuf M1raw, M3raw, G1, G3;
+  bool keep_raw = false;
   int capX = 0, capZ = 0;
   int k1 = 0, k3 = 0;
   std::vector<Block> Ub, Wb;
@@ -164,6 +201,13 @@ struct BksState {
     BKS_TRY(negW.alloc(sizeof(double) * kBasisCap * 8, s));
     BKS_TRY(inner_info.alloc(sizeof(double) * 8, s));
     BKS_TRY(scal.alloc(sizeof(double) * 8, s));
+    if (P.precision == BKS_PREC_MIXED) {
+      const int w1 = r1 * r3, w3 = r1 * (r1 + 1) / 2;
+      BKS_TRY(M1raw.alloc(sizeof(double) * (size_t)m * w1, s));
+      BKS_TRY(M3raw.alloc(sizeof(double) * (size_t)n * w3, s));
+      BKS_TRY(G1.alloc(sizeof(double) * (size_t)(kBasisCap + kBlockMax) * w1, s));
+      BKS_TRY(G3.alloc(sizeof(double) * (size_t)(kBasisCap + kBlockMax) * w3, s));
+    }
     return BKS_OK;
   }
 
@@ -186,6 +230,7 @@ struct BksState {
     double* dst = Xp() + (size_t)m * k1;
     BKS_TRY(contract_mode1_x(t, Xp() + (size_t)m * Ub[a].off, m, wl, Zp() + (size_t)n * Wb[b].off,
                              n, wr, dst, m, fp32, s));
+    if (stage1 && keep_raw) BKS_TRY(copy2d(dst, m, m, wl * wr, M1raw.as<double>(), m, s));
     OrthOpts o;
     o.drop_tol = P.drop_tol;
     o.cap = capX - k1;
@@ -218,6 +263,7 @@ struct BksState {
     double* dst = Zp() + (size_t)n * k3;
     BKS_TRY(contract_mode3_x(t, Xp() + (size_t)m * Ub[a].off, m, wl,
                              tri ? nullptr : Xp() + (size_t)m * Ub[b].off, m, wr, dst, n, fp32, s));
+    if (stage1 && keep_raw) BKS_TRY(copy2d(dst, n, n, w, M3raw.as<double>(), n, s));
     OrthOpts o;
     o.drop_tol = P.drop_tol;
     o.cap = capZ - k3;
@@ -278,8 +324,31 @@ struct BksState {
   double last_nf = 1.0;  // ||F|| at the last stage-1 evaluation
   double last_grad_rel = 0.0;  // ||grad|| / ||F|| there
 
+  // The core C = A.(X,X,Z); in the refinement form (keep_raw) computed in
+  // FP32 and then patched with the FP64 first-order blocks.
+  int core() {
+    BKS_TRY(contract_core_x(t, Xp(), m, k1, Zp(), n, k3, C.as<double>(), fp32_core(), s));
+    if (!keep_raw) return BKS_OK;
+    const int w1 = r1 * r3, w3 = r1 * (r1 + 1) / 2;
+    BKS_TRY(ts_gram(Xp(), m, k1, M1raw.as<double>(), m, w1, m, G1.as<double>(), ws, s));
+    BKS_TRY(ts_gram(Zp(), n, k3, M3raw.as<double>(), n, w3, n, G3.as<double>(), ws, s));
+    const int tot = k1 * w1 + w3 * (k3 - r3);
+    k_core_patch<<<std::max(1, (tot + 255) / 256), 256, 0, s>>>(C.as<double>(), k1, k3, r1, r3,
+                                                               G1.as<double>(), G3.as<double>());
+    ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+    return BKS_OK;
+  }
+  bool core_fp32 = false;
+  bool fp32_core() const { return core_fp32 || keep_raw; }
+
+  int last_k1 = 0, last_k3 = 0;  // basis sizes of the last expansion
+
   int inner_and_restart(bool fp32, cudaEvent_t* ev) {
-    BKS_TRY(contract_core_x(t, Xp(), m, k1, Zp(), n, k3, C.as<double>(), fp32, s));
+    core_fp32 = fp32;
+    last_k1 = k1;
+    last_k3 = k3;
+    BKS_TRY(core());
     BKS_CUDA_TRY(cudaEventRecord(ev[0], s));
     // inner tolerance: a tenth of the outer one unless given, so that the
     // inner residual gradient does not hold the outer test just above tol
@@ -413,6 +482,9 @@ int bks::solve_impl(const bks_tensor* t, const bks_params* prm, const double* U0
       break;
     }
     BKS_CUDA_TRY(cudaEventRecord(ev[0], s));
+    // mixed precision after the FP32 phase: the refinement form (FP64
+    // stage 1, FP32 expansion and core, FP64 first-order core blocks)
+    S.keep_raw = mixed && !fp32;
     BKS_TRY(S.stage1(fp32, &grad, &nf));
     BKS_CUDA_TRY(cudaEventRecord(ev[1], s));
     // the stopping test: ||grad|| / ||F|| (Section 6.2) or the scale-free
@@ -446,7 +518,7 @@ int bks::solve_impl(const bks_tensor* t, const bks_params* prm, const double* U0
     S.cur_tol = fp32 ? (prm->tol_scale_free ? mtol : mtol * nf) : prm->tol;
     S.last_nf = nf;
     S.last_grad_rel = nf > 0 ? grad / nf : 0.0;
-    BKS_TRY(S.expand_rest(fp32));
+    BKS_TRY(S.expand_rest(fp32 || S.keep_raw));
     BKS_CUDA_TRY(cudaEventRecord(ev[2], s));
     BKS_TRY(S.inner_and_restart(fp32, ev + 3));
     {
@@ -467,8 +539,8 @@ int bks::solve_impl(const bks_tensor* t, const bks_params* prm, const double* U0
     info->converged = converged ? 1 : 0;
     info->grad_rel = nf > 0 ? (prm->tol_scale_free ? grad / (nf * nf) : grad / nf) : INFINITY;
     info->normF = nf;
-    info->k1 = S.k1;
-    info->k3 = S.k3;
+    info->k1 = S.last_k1 ? S.last_k1 : S.k1;
+    info->k3 = S.last_k3 ? S.last_k3 : S.k3;
     info->inner_sweeps = S.inner_sweeps;
     info->fp32_iters = fp32_iters;
     info->history_len = hist_len;
@@ -526,8 +598,6 @@ __global__ void k_trace_out(const double* __restrict__ G, int K, int g, double* 
 
 // tall-skinny helpers with Gram output (dense.cu internals re-exposed here
 // through ts_combine + a Gram pass built from orth_block's machinery)
-int ts_gram(const double* Q, int64_t ldq, int K, const double* B, int64_t ldb, int b,
-            int64_t m, double* G, DenseWork& ws, cudaStream_t s);
 int ts_combine_gram(const double* Q, int64_t ldq, int K, const double* B, int64_t ldb, int b,
                     const double* Mq, const double* Mb, int bo, double* Out, int64_t ldo,
                     int64_t m, double* G, DenseWork& ws, cudaStream_t s);

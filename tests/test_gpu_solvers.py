@@ -130,3 +130,30 @@ def test_mixed_precision_matches_fp64_at_1e6():
     assert O.sin_theta_max(W.cpu().numpy(), Wm.cpu().numpy()) < 1e-6
     gg, nf, _ = O.gradient_global(A, Um.cpu().numpy(), Wm.cpu().numpy())
     assert gg / nf < 1e-8
+
+
+def test_mixed_refinement_reaches_fp64_accuracy():
+    """After the FP32 phase the mixed form refines with FP64 stage-1
+    contractions and an FP32 core whose first-order blocks are FP64: it must
+    still converge to FP64 accuracy (well below the FP32 noise floor), to the
+    optimum the FP64 solve finds, in a comparable number of iterations."""
+    bk = _bk()
+    c = synth.zipf_tensor(21, 5000, 20, 60_000, 1.1)
+    A = O.symmetrise(c.m, c.n, c.i, c.j, c.k, c.v)
+    T = bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v)
+    g = synth.rng(22)
+    U0 = synth.orthonormal(g, c.m, 3); W0 = synth.orthonormal(g, c.n, 3)
+    tol = 1e-11  # the FP64 floor of ||grad||/||F|| here is about 3e-12
+    U, W, F, i64 = bk.bks_solve(T, bk.BksParams(r1=3, r3=3, stages=2, block_p=4, tol=tol),
+                                _t(U0), _t(W0))
+    pm = bk.BksParams(r1=3, r3=3, stages=2, block_p=4, tol=tol, precision=bk.BKS_PREC_MIXED,
+                      refine_sweeps=50, mixed_tol=1e-6)
+    Um, Wm, Fm, im = bk.bks_solve(T, pm, _t(U0), _t(W0))
+    assert i64["converged"] and im["converged"]
+    assert im["fp32_iters"] > 0 and im["iters"] > im["fp32_iters"]
+    assert im["iters"] <= i64["iters"] + 10
+    assert O.sin_theta_max(U.cpu().numpy(), Um.cpu().numpy()) < 1e-9
+    assert O.sin_theta_max(W.cpu().numpy(), Wm.cpu().numpy()) < 1e-9
+    gg, nf, _ = O.gradient_global(A, Um.cpu().numpy(), Wm.cpu().numpy())
+    assert gg / nf < 2e-11
+    assert abs(im["normF"] - i64["normF"]) <= 1e-12 * i64["normF"]
