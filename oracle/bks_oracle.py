@@ -534,19 +534,18 @@ def _hooi_sweeps(C, Uh, Wh, sweeps, tol):
 
 
 def inner_solve(C: np.ndarray, r1: int, r3: int, tol: float, max_inner: int = 1000,
-                init_sweeps: int = 5):
+                init_sweeps: int = 0):
     """Best rank-(r1,r1,r3) approximation of the dense (1,2)-symmetric core
     C (k1 x k1 x k3), Algorithm 5 step (i).
 
     Section 6.2 starts from the truncated HOSVD of C followed by 5 HOOI
     sweeps and then runs Newton-Grassmann.  This library's reading: the
-    truncated HOSVD start gets ``init_sweeps`` HOOI sweeps; if its ||F|| is
-    below that of the current point (Uh = [I;0], Wh = [I;0], which is
-    (U0, W0) in the bases) the current point is taken instead; the chosen
-    start continues with HOOI sweeps until its G-gradient is below ``tol``
-    relative to ||F|| or ``max_inner`` sweeps.  Keeping the current point
-    as a candidate makes ||F|| non-decreasing over the outer iterations
-    (eq. (Fnon-decr)).
+    truncated HOSVD start (after ``init_sweeps`` HOOI sweeps, none by
+    default) is compared with the current point (Uh = [I;0], Wh = [I;0],
+    which is (U0, W0) in the bases) by ||F||; the better one continues with
+    HOOI sweeps until its G-gradient is below ``tol`` relative to ||F|| or
+    ``max_inner`` sweeps.  Keeping the current point as a candidate makes
+    ||F|| non-decreasing over the outer iterations (eq. (Fnon-decr)).
     Returns (Uh, Wh, info)."""
     k1, _, k3 = C.shape
     C1 = C.reshape(k1, -1, order="F")

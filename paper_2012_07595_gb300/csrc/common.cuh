@@ -120,6 +120,21 @@ struct Part {
   }
 };
 
+// Chunks of the mode-3 copy for the large-rank cores: every slice k is cut
+// into pieces of about nnz / (4 SMs) entries; the chunks of a slice are
+// consecutive.  Built once per tensor at ingest.
+struct CorePlan {
+  int32_t nch = 0, nsl = 0;
+  DevBuf lo, hi;      // int32 [nch]: entry range of each chunk
+  DevBuf sl_k;        // int32 [nsl]: slice index k of each non-empty slice
+  DevBuf sl_first;    // int32 [nsl+1]: first chunk of each non-empty slice
+  void persist() {
+    for (DevBuf* b : {&lo, &hi, &sl_k, &sl_first}) b->persist();
+  }
+};
+
+int build_core_plan(const Part& m3, int64_t n, int64_t nnz, CorePlan& cp, cudaStream_t s);
+
 }  // namespace bks
 
 struct bks_tensor {
@@ -128,6 +143,7 @@ struct bks_tensor {
   double fro2 = 0.0;
   bks::Part m1;   // sorted by (i, k, j): rows i, columns (k, j)
   bks::Part m3;   // sorted by (k, i, j): rows k, columns (i, j)
+  bks::CorePlan cp;
 };
 
 namespace bks {

@@ -459,62 +459,72 @@ __global__ void k_core_from_tri(const T* __restrict__ Tm, int64_t n, int r1, con
 // Large rank (the Krylov core C = A.(X,X,Z), k1 up to 128): per chunk of
 // one slice k, M = sum_e v_e X[i_e,:]^T X[j_e,:] accumulated in registers
 // as 4x4 tiles of the upper block triangle; chunk partials are combined
-// with Z in a second kernel, C[a,b,c] = sum_chunk Z[k_chunk, c] M_chunk[a,b].
+// with Z in a second kernel, C[a,b,c] = sum_k Z[k,c] sum_{chunks of k} M.
+//
+// A block stages a batch of entries (v X[i,:] and X[j,:], 16-byte vector
+// gathers of the packed rows) in shared memory.  When the triangle has
+// fewer tiles than the block has threads, the threads form `ngroups`
+// groups that take the batch's entries round-robin (entry e to group
+// e mod ngroups), each with its own tile accumulators; the groups' sums
+// are added in group order at the end, so the result is deterministic.
 constexpr int kCoreThreads = 256;
-constexpr int kCoreBatch = 32;
-constexpr int kCoreTiles = 3;     // tiles per thread: (k1/4)(k1/4+1)/2 <= 768 -> k1 <= 128
 
-template <typename T>
+template <typename T, int TPT>
 __global__ void __launch_bounds__(kCoreThreads)
 k_core_chunks(const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ chunk_hi,
               const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
-              const T* __restrict__ vals, const T* __restrict__ Xp, int K, int KP,
-              T* __restrict__ Mpart) {
+              const T* __restrict__ vals, const T* __restrict__ Xp, int K, int KP, int batch,
+              int ngroups, T* __restrict__ Mpart) {
   extern __shared__ unsigned char smem_raw[];
-  T* As = reinterpret_cast<T*>(smem_raw);          // [kCoreBatch][KP]
-  T* Bs = As + kCoreBatch * KP;                     // [kCoreBatch][KP]
+  T* As = reinterpret_cast<T*>(smem_raw);          // [batch][KP]
+  T* Bs = As + (size_t)batch * KP;                  // [batch][KP]
   const int ch = blockIdx.x;
   const int lo = chunk_lo[ch], hi = chunk_hi[ch];
   const int nt = KP / 4;                            // tiles per side
   const int ntiles = nt * (nt + 1) / 2;
-  int ta[kCoreTiles], tb[kCoreTiles];
+  const int slots = kCoreThreads / ngroups;         // threads per group
+  const int g = threadIdx.x / slots, ts = threadIdx.x % slots;
+  const bool active = g < ngroups;
+  int ta[TPT], tb[TPT];
 #pragma unroll
-  for (int u = 0; u < kCoreTiles; ++u) {
-    int id = threadIdx.x + u * kCoreThreads;
+  for (int u = 0; u < TPT; ++u) {
+    const int id = ts + u * slots;
     ta[u] = -1; tb[u] = -1;
-    if (id < ntiles) {
+    if (active && id < ntiles) {
       int b = 0;
       while ((b + 1) * (b + 2) / 2 <= id) ++b;
       ta[u] = id - b * (b + 1) / 2;
       tb[u] = b;
     }
   }
-  T acc[kCoreTiles][4][4];
+  T acc[TPT][4][4];
 #pragma unroll
-  for (int u = 0; u < kCoreTiles; ++u)
+  for (int u = 0; u < TPT; ++u)
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[u][x][y] = T(0);
-  for (int base = lo; base < hi; base += kCoreBatch) {
-    const int cnt = min(kCoreBatch, hi - base);
+  for (int base = lo; base < hi; base += batch) {
+    const int cnt = min(batch, hi - base);
     __syncthreads();
-    for (int t = threadIdx.x; t < kCoreBatch * KP; t += kCoreThreads) {
-      const int e = t / KP, a = t % KP;
-      T va = T(0), vb = T(0);
-      if (e < cnt) {
-        const int idx = base + e;
-        va = vals[idx] * Xp[(int64_t)ii[idx] * KP + a];
-        vb = Xp[(int64_t)jj[idx] * KP + a];
+    for (int t = threadIdx.x; t < cnt * nt; t += kCoreThreads) {
+      const int e = t / nt, q = t % nt;
+      const int idx = base + e;
+      const T v = vals[idx];
+      T xa[4], xb[4];
+      load4(Xp + (int64_t)ii[idx] * KP + 4 * q, xa);
+      load4(Xp + (int64_t)jj[idx] * KP + 4 * q, xb);
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        As[e * KP + 4 * q + x] = v * xa[x];
+        Bs[e * KP + 4 * q + x] = xb[x];
       }
-      As[e * KP + a] = va;
-      Bs[e * KP + a] = vb;
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < kCoreTiles; ++u) {
+    for (int u = 0; u < TPT; ++u) {
       if (ta[u] < 0) continue;
-      for (int e = 0; e < cnt; ++e) {
+      for (int e = g; e < cnt; e += ngroups) {
         T xa[4], xb[4];
 #pragma unroll
         for (int x = 0; x < 4; ++x) xa[x] = As[e * KP + ta[u] * 4 + x];
@@ -528,35 +538,76 @@ k_core_chunks(const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ 
     }
   }
   T* dst = Mpart + (int64_t)ch * K * K;
+  if (ngroups == 1) {
 #pragma unroll
-  for (int u = 0; u < kCoreTiles; ++u) {
-    if (ta[u] < 0) continue;
+    for (int u = 0; u < TPT; ++u) {
+      if (ta[u] < 0) continue;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int a = ta[u] * 4 + x, b = tb[u] * 4 + y;
+          if (a < K && b < K && a <= b) dst[a + (int64_t)K * b] = acc[u][x][y];
+        }
+    }
+    return;
+  }
+  // ngroups > 1 (then TPT == 1): group sums in group order through shared
+  // memory ([ngroups][ntiles][16], reusing the staging area)
+  __syncthreads();
+  T* red = As;
+  if (ta[0] >= 0) {
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) {
-        const int a = ta[u] * 4 + x, b = tb[u] * 4 + y;
-        if (a < K && b < K && a <= b) dst[a + (int64_t)K * b] = acc[u][x][y];
-      }
+      for (int y = 0; y < 4; ++y) red[((size_t)g * ntiles + ts) * 16 + 4 * x + y] = acc[0][x][y];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < ntiles * 16; o += kCoreThreads) {
+    const int id = o / 16, xy = o % 16;
+    T sum = red[(size_t)id * 16 + xy];
+    for (int q = 1; q < ngroups; ++q) sum += red[((size_t)q * ntiles + id) * 16 + xy];
+    int b = 0;
+    while ((b + 1) * (b + 2) / 2 <= id) ++b;
+    const int a = (id - b * (b + 1) / 2) * 4 + xy / 4, bb = b * 4 + xy % 4;
+    if (a < K && bb < K && a <= bb) dst[a + (int64_t)K * bb] = sum;
   }
 }
 
-// C[a,b,c] = sum_chunk Z[k_chunk, c] M_chunk[min(a,b), max(a,b)]
-template <typename T, typename IT, typename OT>
-__global__ void k_core_combine(const T* __restrict__ Mpart, const int32_t* __restrict__ chunk_k,
-                               int nchunks, int K, const IT* __restrict__ Z, int64_t ldz, int r3,
-                               OT* __restrict__ C) {
-  const int64_t total = (int64_t)K * (K + 1) / 2 * r3;
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+// S[sl, t] = sum over the chunks of non-empty slice sl (in chunk order) of
+// M_chunk[a, b], t = a + b(b+1)/2 (a <= b).
+template <typename T>
+__global__ void k_core_slice_sum(const T* __restrict__ Mpart, const int32_t* __restrict__ sl_first,
+                                 int nsl, int K, T* __restrict__ S) {
+  const int ntri = K * (K + 1) / 2;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < (int64_t)nsl * ntri;
        o += (int64_t)gridDim.x * blockDim.x) {
-    const int ntri = K * (K + 1) / 2;
-    const int tcol = (int)(o % ntri), c = (int)(o / ntri);
+    const int t = (int)(o % ntri), sl = (int)(o / ntri);
     int b = 0;
-    while ((b + 1) * (b + 2) / 2 <= tcol) ++b;
-    const int a = tcol - b * (b + 1) / 2;
+    while ((b + 1) * (b + 2) / 2 <= t) ++b;
+    const int a = t - b * (b + 1) / 2;
+    T sum = T(0);
+    for (int ch = sl_first[sl]; ch < sl_first[sl + 1]; ++ch)
+      sum += Mpart[(int64_t)ch * K * K + a + (int64_t)K * b];
+    S[o] = sum;
+  }
+}
+
+// C[a,b,c] = C[b,a,c] = sum over non-empty slices (in order) of Z[k,c] S[sl, t].
+template <typename T, typename IT, typename OT>
+__global__ void k_core_combine(const T* __restrict__ S, const int32_t* __restrict__ sl_k, int nsl,
+                               int K, const IT* __restrict__ Z, int64_t ldz, int r3,
+                               OT* __restrict__ C) {
+  const int ntri = K * (K + 1) / 2;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < (int64_t)ntri * r3;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(o % ntri), c = (int)(o / ntri);
+    int b = 0;
+    while ((b + 1) * (b + 2) / 2 <= t) ++b;
+    const int a = t - b * (b + 1) / 2;
     T acc = T(0);
-    for (int ch = 0; ch < nchunks; ++ch)
-      acc += (T)Z[chunk_k[ch] + ldz * c] * Mpart[(int64_t)ch * K * K + a + (int64_t)K * b];
+    for (int sl = 0; sl < nsl; ++sl)
+      acc = fma((T)Z[sl_k[sl] + ldz * c], S[(int64_t)sl * ntri + t], acc);
     C[a + (int64_t)K * (b + (int64_t)K * c)] = (OT)acc;
     C[b + (int64_t)K * (a + (int64_t)K * c)] = (OT)acc;
   }
@@ -578,50 +629,74 @@ int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* 
   if (r1 > 128) return fail(BKS_EUNSUPPORTED, "core rank above 128");
   const int KP = (r1 + 3) / 4 * 4;
   const Part& P = t->m3;
-  // chunks: each slice k cut into pieces of about nnz / (4 * SMs) entries
-  const int64_t target = std::max<int64_t>(256, t->nnz / (4LL * num_sms()) + 1);
-  std::vector<int32_t> lo, hi, kk;
-  for (int64_t k = 0; k < t->n; ++k) {
-    const int32_t a = P.host_ptr[k], b = P.host_ptr[k + 1];
-    for (int64_t x = a; x < b; x += target) {
-      lo.push_back((int32_t)x);
-      hi.push_back((int32_t)std::min<int64_t>(b, x + target));
-      kk.push_back((int32_t)k);
-    }
-  }
-  const int nch = (int)lo.size();
+  const CorePlan& cp = t->cp;
+  const int nch = cp.nch;
   if (nch == 0) {
     BKS_CUDA_TRY(cudaMemsetAsync(F, 0, sizeof(OT) * (size_t)r1 * r1 * r3, s));
     return BKS_OK;
   }
-  DevBuf dlo, dhi, dk, Xp, Mp;
-  BKS_TRY(dlo.alloc(4 * nch, s));
-  BKS_TRY(dhi.alloc(4 * nch, s));
-  BKS_TRY(dk.alloc(4 * nch, s));
-  BKS_CUDA_TRY(cudaMemcpyAsync(dlo.p, lo.data(), 4 * nch, cudaMemcpyHostToDevice, s));
-  BKS_CUDA_TRY(cudaMemcpyAsync(dhi.p, hi.data(), 4 * nch, cudaMemcpyHostToDevice, s));
-  BKS_CUDA_TRY(cudaMemcpyAsync(dk.p, kk.data(), 4 * nch, cudaMemcpyHostToDevice, s));
+  DevBuf Xp, Mp, Sl;
   BKS_TRY((pack<T, IT>(U, ldu, t->m, r1, KP, Xp, s)));
   BKS_TRY(Mp.alloc(sizeof(T) * (size_t)nch * r1 * r1, s));
-  const size_t smem = sizeof(T) * 2 * kCoreBatch * KP;
+  // thread groups over the batch's entries when the triangle has fewer
+  // tiles than the block has threads
+  const int nt = KP / 4, ntiles = nt * (nt + 1) / 2;
+  const int ngroups = ntiles <= kCoreThreads ? std::min(32, kCoreThreads / ntiles) : 1;
+  const bool big = ntiles > kCoreThreads;  // k1 > 88: three tiles per thread
+  int batch = (int)std::min<size_t>(64, (64 * 1024) / (2 * sizeof(T) * (size_t)KP));
+  batch = std::max(batch, 8);
+  const size_t smem = std::max(sizeof(T) * 2 * (size_t)batch * KP,
+                               sizeof(T) * (size_t)ngroups * ntiles * 16);
+  auto kern = big ? k_core_chunks<T, 3> : k_core_chunks<T, 1>;
   if (smem > 48 * 1024)
-    BKS_CUDA_TRY(cudaFuncSetAttribute(k_core_chunks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-  k_core_chunks<T><<<nch, kCoreThreads, smem, s>>>(dlo.as<int32_t>(), dhi.as<int32_t>(),
-                                                   P.c0.as<int32_t>(), P.c1.as<int32_t>(),
-                                                   values_of<T>(P, t->vdtype), Xp.as<T>(), r1,
-                                                   KP, Mp.as<T>()); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<nch, kCoreThreads, smem, s>>>(cp.lo.as<int32_t>(), cp.hi.as<int32_t>(), P.c0.as<int32_t>(),
+                                       P.c1.as<int32_t>(), values_of<T>(P, t->vdtype), Xp.as<T>(),
+                                       r1, KP, batch, ngroups, Mp.as<T>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
-  const int64_t outs = (int64_t)r1 * (r1 + 1) / 2 * r3;
-  k_core_combine<T, IT, OT><<<grid_for(outs), 256, 0, s>>>(Mp.as<T>(), dk.as<int32_t>(), nch, r1,
-                                                           W, ldw, r3, F); ::bks::note_launch();
+  const int64_t ntri = (int64_t)r1 * (r1 + 1) / 2;
+  BKS_TRY(Sl.alloc(sizeof(T) * (size_t)cp.nsl * ntri, s));
+  k_core_slice_sum<T><<<grid_for(cp.nsl * ntri), 256, 0, s>>>(Mp.as<T>(), cp.sl_first.as<int32_t>(),
+                                                             cp.nsl, r1, Sl.as<T>()); ::bks::note_launch();
+  k_core_combine<T, IT, OT><<<grid_for(ntri * r3), 256, 0, s>>>(Sl.as<T>(), cp.sl_k.as<int32_t>(),
+                                                                cp.nsl, r1, W, ldw, r3, F); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
-  // the host vectors above were read by async copies: keep them alive
-  BKS_CUDA_TRY(cudaStreamSynchronize(s));
   return BKS_OK;
 }
 
 }  // namespace
+
+// Core chunk plan (see CorePlan): host loop over the slices of the mode-3
+// copy, uploaded once.
+int build_core_plan(const Part& m3, int64_t n, int64_t nnz, CorePlan& cp, cudaStream_t s) {
+  const int64_t target = std::max<int64_t>(256, nnz / (4LL * num_sms()) + 1);
+  std::vector<int32_t> lo, hi, slk, slf;
+  for (int64_t k = 0; k < n; ++k) {
+    const int32_t a = m3.host_ptr[k], b = m3.host_ptr[k + 1];
+    if (b <= a) continue;
+    slk.push_back((int32_t)k);
+    slf.push_back((int32_t)lo.size());
+    for (int64_t x = a; x < b; x += target) {
+      lo.push_back((int32_t)x);
+      hi.push_back((int32_t)std::min<int64_t>(b, x + target));
+    }
+  }
+  slf.push_back((int32_t)lo.size());
+  cp.nch = (int32_t)lo.size();
+  cp.nsl = (int32_t)slk.size();
+  if (cp.nch == 0) return BKS_OK;
+  BKS_TRY(cp.lo.alloc(4 * lo.size(), s));
+  BKS_TRY(cp.hi.alloc(4 * hi.size(), s));
+  BKS_TRY(cp.sl_k.alloc(4 * slk.size(), s));
+  BKS_TRY(cp.sl_first.alloc(4 * slf.size(), s));
+  BKS_CUDA_TRY(cudaMemcpyAsync(cp.lo.p, lo.data(), 4 * lo.size(), cudaMemcpyHostToDevice, s));
+  BKS_CUDA_TRY(cudaMemcpyAsync(cp.hi.p, hi.data(), 4 * hi.size(), cudaMemcpyHostToDevice, s));
+  BKS_CUDA_TRY(cudaMemcpyAsync(cp.sl_k.p, slk.data(), 4 * slk.size(), cudaMemcpyHostToDevice, s));
+  BKS_CUDA_TRY(cudaMemcpyAsync(cp.sl_first.p, slf.data(), 4 * slf.size(), cudaMemcpyHostToDevice, s));
+  // the host vectors are read by the async copies: wait before they go
+  BKS_CUDA_TRY(cudaStreamSynchronize(s));
+  return BKS_OK;
+}
 
 int contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p, const void* Y,
                    int64_t ldy, int q, void* out, int64_t ldo, int dtype, cudaStream_t s) {

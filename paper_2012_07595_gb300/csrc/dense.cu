@@ -103,13 +103,32 @@ k_ts_pass(const double* __restrict__ Q, int64_t ldq, int K, const double* __rest
   }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ gpart, int nparts, int count,
-                              double* __restrict__ G) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += gpart[(size_t)p * count + e];
-    G[e] = s;
+// G[e] = sum over the per-block partials.  A block of 8 warps takes 32
+// consecutive entries: warp w sums the partials p = w, w+8, ... in
+// increasing order, then lane-wise the 8 warp sums are added in warp order
+// (a fixed order: the result does not depend on the launch).
+constexpr int kReduceWarps = 8;
+__global__ void __launch_bounds__(32 * kReduceWarps)
+k_gram_reduce(const double* __restrict__ gpart, int nparts, int count, double* __restrict__ G) {
+  __shared__ double part[kReduceWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (e < count)
+    for (int p = w; p < nparts; p += kReduceWarps) s += gpart[(size_t)p * count + e];
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && e < count) {
+    double t = part[0][lane];
+    for (int q = 1; q < kReduceWarps; ++q) t += part[q][lane];
+    G[e] = t;
   }
+}
+
+void gram_reduce(const double* gpart, int nparts, int count, double* G, cudaStream_t s) {
+  k_gram_reduce<<<std::max(1, (count + 31) / 32), 32 * kReduceWarps, 0, s>>>(gpart, nparts,
+                                                                             count, G);
+  ::bks::note_launch();
 }
 
 // small-matrix scratch layout (doubles), all column-major
@@ -304,11 +323,20 @@ __global__ void k_orth_r3(const double* __restrict__ G, int K, int b, double* __
   const int gw = K + no;
   __shared__ double R3[kMaxB * kMaxB];
   __shared__ double Ri[kMaxB * kMaxB];
+  // S3 = Bn^T Bn - H3^T H3 on the kept columns (all entries in parallel),
+  // then its Cholesky factor on one thread (nk^3/6 operations)
+  for (int x = threadIdx.x; x < nk * nk; x += blockDim.x) {
+    const int i = x % nk, j = x / nk;
+    if (i > j) continue;
+    double v = G[K + i + gw * j];
+    for (int e = 0; e < K; ++e) v -= G[e + gw * i] * G[e + gw * j];
+    Ri[i + kMaxB * j] = v;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     for (int j = 0; j < nk; ++j) {
       for (int i = 0; i <= j; ++i) {
-        double v = G[K + i + gw * j];
-        for (int e = 0; e < K; ++e) v -= G[e + gw * i] * G[e + gw * j];
+        double v = Ri[i + kMaxB * j];
         for (int t = 0; t < i; ++t) v -= R3[t + kMaxB * i] * R3[t + kMaxB * j];
         if (i == j) {
           if (!(v > 0.0)) { flags[0] = 1; v = 1e-300; }
@@ -428,8 +456,7 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
   BKS_CUDA_TRY(cudaMemsetAsync(st, 0, 48 * sizeof(int), s));
   const int gw = K + b;
   auto reduce = [&](int count) {
-    k_gram_reduce<<<std::max(1, (count + 255) / 256), 256, 0, s>>>(ws.gpart.as<double>(), grid,
-                                                                   count, ws.gram.as<double>()); ::bks::note_launch();
+    gram_reduce(ws.gpart.as<double>(), grid, count, ws.gram.as<double>(), s);
   };
   // P1: Gram of [Q B]^T B (first projection coefficients)
   if (o.fast_first)
@@ -465,8 +492,7 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
     k_grad_prep<<<1, 256, 0, s>>>(ws.gram.as<double>(), K, b, sm + L.H, o.grad_mat, g, gM, gQ); ::bks::note_launch();
     BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, gQ, gM, g, 1, ws.gtmp.as<double>(), m, 1,
                                       ws.gpart.as<double>(), m, grid, s)));
-    k_gram_reduce<<<std::max(1, ((K + g) * g + 255) / 256), 256, 0, s>>>(
-        ws.gpart.as<double>(), grid, (K + g) * g, ws.gram2.as<double>()); ::bks::note_launch();
+    gram_reduce(ws.gpart.as<double>(), grid, (K + g) * g, ws.gram2.as<double>(), s);
     k_gram_trace<<<1, 32, 0, s>>>(ws.gram2.as<double>(), K, g, o.grad_out); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
@@ -539,8 +565,7 @@ int ts_gram(const double* Q, int64_t ldq, int K, const double* B, int64_t ldb, i
   const int grid = gram_grid(m);
   BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, nullptr, nullptr, b, 0, nullptr, 0, 1,
                                      ws.gpart.as<double>(), m, grid, s)));
-  k_gram_reduce<<<std::max(1, ((K + b) * b + 255) / 256), 256, 0, s>>>(ws.gpart.as<double>(), grid,
-                                                                      (K + b) * b, G); ::bks::note_launch();
+  gram_reduce(ws.gpart.as<double>(), grid, (K + b) * b, G, s);
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }
@@ -554,8 +579,7 @@ int ts_combine_gram(const double* Q, int64_t ldq, int K, const double* B, int64_
   const int grid = gram_grid(m);
   BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, Mq, Mb, bo, 1, Out, ldo, 1,
                                      ws.gpart.as<double>(), m, grid, s)));
-  k_gram_reduce<<<std::max(1, ((K + bo) * bo + 255) / 256), 256, 0, s>>>(ws.gpart.as<double>(),
-                                                                        grid, (K + bo) * bo, G); ::bks::note_launch();
+  gram_reduce(ws.gpart.as<double>(), grid, (K + bo) * bo, G, s);
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
 }

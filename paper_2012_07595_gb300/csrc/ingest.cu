@@ -395,8 +395,10 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   BKS_CUDA_TRY(cudaMemcpyAsync(Q.host_ptr.data(), Q.ptr.p, sizeof(int32_t) * (n + 1),
                                cudaMemcpyDeviceToHost, s));
   BKS_CUDA_TRY(cudaStreamSynchronize(s));
+  BKS_TRY(build_core_plan(Q, n, nseg, T->cp, s));
   P.persist();
   Q.persist();
+  T->cp.persist();
   return BKS_OK;
 }
 

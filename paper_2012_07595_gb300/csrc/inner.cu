@@ -4,10 +4,9 @@
 //
 // Section 6.2 starts from the truncated HOSVD of C, runs 5 HOOI sweeps and
 // then Newton-Grassmann.  This library's reading: the truncated HOSVD start
-// gets 5 symmetric HOOI sweeps; if its ||F|| is below that of the current
-// point (Uh = [I;0], Wh = [I;0]) the current point is taken instead; the
-// chosen start continues with HOOI sweeps until its G-gradient is below
-// tol * ||F|| or max_inner sweeps are done.
+// and the current point (Uh = [I;0], Wh = [I;0]) are compared by ||F||; the
+// better one continues with symmetric HOOI sweeps until its G-gradient is
+// below tol * ||F|| or max_inner sweeps are done.
 //
 // The HOSVD start only seeds the iteration, so its two Gram matrices and
 // their eigenvectors are computed in FP32 (k_hosvd); the sweeps, the
@@ -75,7 +74,8 @@ k_hosvd(const float* __restrict__ part1, const float* __restrict__ part3, int np
   float* red = V + nmax * nmax;
   float* cs = red + 64;
   __shared__ int idx[kMaxR];
-  for (int pass = 0; pass < 2; ++pass) {
+  {
+    const int pass = blockIdx.x;  // block 0: the mode-1 Gram, block 1: the mode-3 Gram
     const int n = pass == 0 ? k1 : k3;
     const int r = pass == 0 ? r1 : r3;
     const float* part = pass == 0 ? part1 : part3;
@@ -113,9 +113,46 @@ struct InnerShared {
   int idx[kMaxW];
 };
 
+// Modified Gram-Schmidt, twice, on the columns of Out (n x r, shared
+// memory; n <= 128, r <= 8), FP64; every thread of the block calls.
+__device__ void block_mgs2(double* Out, int n, int r, double* red) {
+  for (int rep = 0; rep < 2; ++rep) {
+    for (int t = 0; t < r; ++t) {
+      for (int u = 0; u < t; ++u) {
+        double d = 0.0;
+        if (threadIdx.x < 32) {
+          for (int i = threadIdx.x; i < n; i += 32) d = fma(Out[i + n * u], Out[i + n * t], d);
+          for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+          if (threadIdx.x == 0) red[0] = d;
+        }
+        __syncthreads();
+        d = red[0];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) Out[i + n * t] -= d * Out[i + n * u];
+        __syncthreads();
+      }
+      double d = 0.0;
+      if (threadIdx.x < 32) {
+        for (int i = threadIdx.x; i < n; i += 32) d = fma(Out[i + n * t], Out[i + n * t], d);
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+        if (threadIdx.x == 0) red[0] = d;
+      }
+      __syncthreads();
+      const double inv = nr_rsqrt(red[0]);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) Out[i + n * t] *= inv;
+      __syncthreads();
+    }
+  }
+}
+
 // r leading left singular vectors of T (n x w, ld n) into Out (n x r):
 // eigenvectors of T^T T, Out = T v / sigma, then two MGS passes.
-__device__ void inner_topsvd(const double* T, int n, int w, int r, InnerShared& S, double* Out) {
+// K (w x w, row-major, global) carries the eigenvector matrix from one HOOI
+// sweep to the next: with `warm` the Jacobi iteration runs on K^T G K and
+// K <- K J afterwards, so that near convergence, where G changes little
+// between sweeps, one or two Jacobi sweeps suffice; without `warm`, K is
+// set to the eigenvectors found from the identity.  Kt is w x w scratch.
+__device__ void inner_topsvd(const double* T, int n, int w, int r, InnerShared& S, double* Out,
+                             double* K, double* Kt, bool warm) {
   for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
     const int i = x % w, j = x / w;
     double s = 0.0;
@@ -123,7 +160,41 @@ __device__ void inner_topsvd(const double* T, int n, int w, int r, InnerShared& 
     S.G[i * w + j] = s;
   }
   __syncthreads();
+  if (warm) {
+    // Kt = G K, then G <- K^T Kt (upper triangle, mirrored)
+    for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
+      const int i = x / w, j = x % w;
+      double s = 0.0;
+      for (int l = 0; l < w; ++l) s = fma(S.G[i * w + l], K[l * w + j], s);
+      Kt[x] = s;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
+      const int i = x / w, j = x % w;
+      if (i > j) continue;
+      double s = 0.0;
+      for (int l = 0; l < w; ++l) s = fma(K[l * w + i], Kt[l * w + j], s);
+      S.G[i * w + j] = s;
+      S.G[j * w + i] = s;
+    }
+    __syncthreads();
+  }
   block_jacobi_eig<double>(S.G, S.V, w, 0.0, 40, S.red, S.cs);
+  if (warm) {
+    for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
+      const int i = x / w, j = x % w;
+      double s = 0.0;
+      for (int l = 0; l < w; ++l) s = fma(K[i * w + l], S.V[l * w + j], s);
+      Kt[x] = s;
+    }
+    __syncthreads();
+  }
+  for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
+    const double v = warm ? Kt[x] : S.V[x];
+    K[x] = v;
+    S.V[x] = v;
+  }
+  __syncthreads();
   top_diag<double>(S.G, w, r, S.idx);
   for (int x = threadIdx.x; x < n * r; x += blockDim.x) {
     const int i = x % n, t = x / n;
@@ -132,33 +203,7 @@ __device__ void inner_topsvd(const double* T, int n, int w, int r, InnerShared& 
     Out[i + n * t] = s;
   }
   __syncthreads();
-  // MGS twice (one column at a time; n <= 128, r <= 8)
-  for (int rep = 0; rep < 2; ++rep) {
-    for (int t = 0; t < r; ++t) {
-      for (int u = 0; u < t; ++u) {
-        double d = 0.0;
-        if (threadIdx.x < 32) {
-          for (int i = threadIdx.x; i < n; i += 32) d = fma(Out[i + n * u], Out[i + n * t], d);
-          for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-          if (threadIdx.x == 0) S.red[0] = d;
-        }
-        __syncthreads();
-        d = S.red[0];
-        for (int i = threadIdx.x; i < n; i += blockDim.x) Out[i + n * t] -= d * Out[i + n * u];
-        __syncthreads();
-      }
-      double d = 0.0;
-      if (threadIdx.x < 32) {
-        for (int i = threadIdx.x; i < n; i += 32) d = fma(Out[i + n * t], Out[i + n * t], d);
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-        if (threadIdx.x == 0) S.red[0] = d;
-      }
-      __syncthreads();
-      const double inv = nr_rsqrt(S.red[0]);
-      for (int i = threadIdx.x; i < n; i += blockDim.x) Out[i + n * t] *= inv;
-      __syncthreads();
-    }
-  }
+  block_mgs2(Out, n, r, S.red);
 }
 
 // G-gradient of the inner problem at (Uh, Wh) from T1 (at Uh, Wh) and T3
@@ -262,6 +307,9 @@ struct CoopArgs {
   double* T1;         // k1 x r1 r3
   double* T3;         // k3 x r1^2
   double* ctl;        // [0] grad [1] normF [2] stop flag
+  double* K1;         // r1 r3 x r1 r3: eigenvectors carried across sweeps (mode 1)
+  double* K3;         // r1^2 x r1^2 (mode 3)
+  double* Kt;         // scratch
   double* Uh_out;
   double* Wh_out;
   double* negU;
@@ -352,7 +400,7 @@ __device__ int coop_sweeps(const CoopArgs& a, int max_sweeps, double tol, InnerS
       const double g = a.ctl[0], nf = a.ctl[1];
       const bool stop = done >= max_sweeps || g <= tol * nf;
       if (!stop) {
-        inner_topsvd(S.T1, a.k1, a.r1 * a.r3, a.r1, S, S.Uh);
+        inner_topsvd(S.T1, a.k1, a.r1 * a.r3, a.r1, S, S.Uh, a.K1, a.Kt, done > 0);
         block_copy(S.Uh, a.Ug, a.k1 * a.r1);
       }
       if (threadIdx.x == 0) a.ctl[2] = stop ? 1.0 : 0.0;
@@ -367,7 +415,7 @@ __device__ int coop_sweeps(const CoopArgs& a, int max_sweeps, double tol, InnerS
     if (blockIdx.x == 0) {
       block_copy(a.T3, S.T3, a.k3 * a.r1 * a.r1);
       __syncthreads();
-      inner_topsvd(S.T3, a.k3, a.r1 * a.r1, a.r3, S, S.Wh);
+      inner_topsvd(S.T3, a.k3, a.r1 * a.r1, a.r3, S, S.Wh, a.K3, a.Kt, done > 0);
       block_copy(S.Wh, a.Wg, a.k3 * a.r3);
       __threadfence();
     }
@@ -382,9 +430,20 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_coop(CoopArgs a) {
   extern __shared__ double shd[];
   InnerShared& S = *reinterpret_cast<InnerShared*>(shd);
   const int nu = a.k1 * a.r1, nw = a.k3 * a.r3;
-  // candidate 1: truncated HOSVD + init sweeps
-  for (int64_t x = gtid(); x < nu; x += gsize()) a.Ug[x] = a.Uh0[x];
-  for (int64_t x = gtid(); x < nw; x += gsize()) a.Wg[x] = a.Wh0[x];
+  // candidate 1: truncated HOSVD (+ init sweeps).  Its FP32 eigenvectors
+  // are orthonormalised in FP64 first: ||F|| is compared between points of
+  // the Stiefel manifolds, and a start whose columns are longer than one
+  // would win the comparison by its length.
+  if (blockIdx.x == 0) {
+    block_copy(a.Uh0, S.Uh, nu);
+    block_copy(a.Wh0, S.Wh, nw);
+    __syncthreads();
+    block_mgs2(S.Uh, a.k1, a.r1, S.red);
+    block_mgs2(S.Wh, a.k3, a.r3, S.red);
+    block_copy(S.Uh, a.Ug, nu);
+    block_copy(S.Wh, a.Wg, nw);
+    __threadfence();
+  }
   grid.sync();
   coop_sweeps(a, a.init_sweeps, 0.0, S, grid);
   const double nf_a = a.ctl[1];
@@ -426,7 +485,7 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_coop(CoopArgs a) {
 }  // namespace
 
 struct InnerWork {
-  DevBuf part1, part3, Uh0, Wh0, D, E, Ug, Wg, Ub, Wb, T1, T3, ctl;
+  DevBuf part1, part3, Uh0, Wh0, D, E, Ug, Wg, Ub, Wb, T1, T3, ctl, K;
   int coop_grid = 0;
 };
 
@@ -460,7 +519,7 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
                                       (int)(sizeof(float) * (2 * 128 * 128 + 64 + 4 * 128))));
     attr = true;
   }
-  k_hosvd<<<1, kInnerThreads, hs, s>>>(w.part1.as<float>(), w.part3.as<float>(), nparts, k1, k3,
+  k_hosvd<<<2, kInnerThreads, hs, s>>>(w.part1.as<float>(), w.part3.as<float>(), nparts, k1, k3,
                                        r1, r3, w.Uh0.as<double>(), w.Wh0.as<double>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   const size_t mat = sizeof(double) * 128 * kMaxR;
@@ -470,6 +529,10 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   for (DevBuf* b : {&w.T1, &w.T3})
     if (b->bytes < tsz) { BKS_TRY(b->alloc(tsz, s)); b->persist(); }
   if (w.ctl.bytes < sizeof(double) * 8) { BKS_TRY(w.ctl.alloc(sizeof(double) * 8, s)); w.ctl.persist(); }
+  if (w.K.bytes < sizeof(double) * 3 * kMaxW * kMaxW) {
+    BKS_TRY(w.K.alloc(sizeof(double) * 3 * kMaxW * kMaxW, s));
+    w.K.persist();
+  }
   if (w.coop_grid == 0) {
     int per_sm = 0;
     BKS_CUDA_TRY(cudaFuncSetAttribute(k_inner_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -485,10 +548,11 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(w.coop_grid, (work + 511) / 512));
   CoopArgs a;
   a.C = C; a.k1 = k1; a.k3 = k3; a.r1 = r1; a.r3 = r3; a.tol = tol; a.max_inner = max_inner;
-  a.init_sweeps = 5; a.Uh0 = w.Uh0.as<double>(); a.Wh0 = w.Wh0.as<double>();
+  a.init_sweeps = 0; a.Uh0 = w.Uh0.as<double>(); a.Wh0 = w.Wh0.as<double>();
   a.Ug = w.Ug.as<double>(); a.Wg = w.Wg.as<double>(); a.Ub = w.Ub.as<double>();
   a.Wb = w.Wb.as<double>(); a.D = w.D.as<double>(); a.E = w.E.as<double>();
   a.T1 = w.T1.as<double>(); a.T3 = w.T3.as<double>(); a.ctl = w.ctl.as<double>();
+  a.K1 = w.K.as<double>(); a.K3 = a.K1 + kMaxW * kMaxW; a.Kt = a.K3 + kMaxW * kMaxW;
   a.Uh_out = Uh; a.Wh_out = Wh; a.negU = negU; a.negW = negW; a.info = info;
   void* kargs[] = {&a};
   BKS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_inner_coop, dim3(grid),

@@ -22,6 +22,7 @@ CASES = {
     "long_rows": lambda: synth.random_coo(2, 50, 4, 30_000),
     "zipf": lambda: synth.zipf_tensor(3, 20_000, 23, 200_000, 1.1),
     "tiny": lambda: synth.random_coo(4, 7, 3, 20),
+    "zipf_mid": lambda: synth.zipf_tensor(5, 3000, 23, 60_000, 1.1),
 }
 
 
@@ -93,9 +94,12 @@ def test_deterministic_bits():
 
 
 @pytest.mark.parametrize("name", ["uniform_small", "zipf"])
-@pytest.mark.parametrize("r1,r3", [(2, 2), (3, 2), (5, 5), (14, 9), (36, 21)])
+@pytest.mark.parametrize("r1,r3", [(2, 2), (3, 2), (5, 5), (9, 4), (14, 9), (36, 21), (70, 40),
+                                   (100, 30)])
 def test_core_fp64(name, r1, r3):
     import torch
+    if name == "zipf" and r1 > 36:
+        pytest.skip("the oracle's m x r1 r3 intermediate is large; covered on uniform_small")
     bk, A, T = _setup(name)
     g = synth.rng(15)
     U = g.standard_normal((A.m, r1)); W = g.standard_normal((A.n, r3))
@@ -103,6 +107,25 @@ def test_core_fp64(name, r1, r3):
     ref = O.core(A, U, W)
     assert rel_err(got, ref) < 1e-12
     assert np.allclose(got, got.transpose(1, 0, 2), rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("r1,r3", [(9, 4), (36, 21), (100, 12)])
+def test_core_fp32_within_summation_bound(r1, r3):
+    """FP32 core (grouped chunk sums, per-slice combine): every entry within
+    a recursive-summation bound of the FP64 oracle, n eps32 sum|terms| with
+    n the longest chunk."""
+    import torch
+    bk, A, T = _setup("zipf_mid", np.float32)
+    g = synth.rng(17)
+    U = g.standard_normal((A.m, r1)); W = g.standard_normal((A.n, r3))
+    got = bk.bks_core(T, torch.tensor(U, device="cuda", dtype=torch.float32),
+                      torch.tensor(W, device="cuda", dtype=torch.float32)).cpu().numpy()
+    ref = O.core(A, U, W)
+    absref = O.core(O.SymTensor(A.m, A.n, A.i, A.j, A.k, np.abs(A.v)), np.abs(U), np.abs(W))
+    longest = int(np.bincount(A.k, minlength=A.n).max())
+    bound = 2 * (longest + 4) * np.finfo(np.float32).eps * absref
+    assert np.all(np.abs(got - ref) <= bound)
+    assert np.array_equal(got, got.transpose(1, 0, 2))
 
 
 def test_ragged_widths_and_leading_dimensions():
