@@ -469,13 +469,36 @@ __global__ void k_core_from_tri(const T* __restrict__ Tm, int64_t n, int r1, con
 // are added in group order at the end, so the result is deterministic.
 constexpr int kCoreThreads = 256;
 
+// 16-byte shared-memory vector access (4 floats, or 4 doubles as two
+// 16-byte halves); p is 16-byte aligned
+template <typename T>
+__device__ __forceinline__ void store4_shared(T* p, const T (&x)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(x[0], x[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void load4_shared(const T* p, T (&x)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+  } else {
+    const double2 q0 = reinterpret_cast<const double2*>(p)[0];
+    const double2 q1 = reinterpret_cast<const double2*>(p)[1];
+    x[0] = q0.x; x[1] = q0.y; x[2] = q1.x; x[3] = q1.y;
+  }
+}
+
 template <typename T, int TPT>
 __global__ void __launch_bounds__(kCoreThreads)
 k_core_chunks(const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ chunk_hi,
               const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
               const T* __restrict__ vals, const T* __restrict__ Xp, int K, int KP, int batch,
               int ngroups, T* __restrict__ Mpart) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* As = reinterpret_cast<T*>(smem_raw);          // [batch][KP]
   T* Bs = As + (size_t)batch * KP;                  // [batch][KP]
   const int ch = blockIdx.x;
@@ -515,10 +538,9 @@ k_core_chunks(const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ 
       load4(Xp + (int64_t)ii[idx] * KP + 4 * q, xa);
       load4(Xp + (int64_t)jj[idx] * KP + 4 * q, xb);
 #pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        As[e * KP + 4 * q + x] = v * xa[x];
-        Bs[e * KP + 4 * q + x] = xb[x];
-      }
+      for (int x = 0; x < 4; ++x) xa[x] *= v;
+      store4_shared(As + e * KP + 4 * q, xa);
+      store4_shared(Bs + e * KP + 4 * q, xb);
     }
     __syncthreads();
 #pragma unroll
@@ -526,10 +548,8 @@ k_core_chunks(const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ 
       if (ta[u] < 0) continue;
       for (int e = g; e < cnt; e += ngroups) {
         T xa[4], xb[4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x) xa[x] = As[e * KP + ta[u] * 4 + x];
-#pragma unroll
-        for (int y = 0; y < 4; ++y) xb[y] = Bs[e * KP + tb[u] * 4 + y];
+        load4_shared(As + e * KP + ta[u] * 4, xa);
+        load4_shared(Bs + e * KP + tb[u] * 4, xb);
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll

@@ -11,6 +11,7 @@
 // Every pass reads each row of Q and B once; the (K+b) x b Gram partials
 // are reduced in a fixed order, so the result is bitwise reproducible.
 #include <algorithm>
+#include <type_traits>
 
 #include "dense.cuh"
 #include "jacobi.cuh"
@@ -26,24 +27,29 @@ constexpr int kMaxB = 32;         // columns of B and of the output
 constexpr int kGramPerThread = (kMaxK + kMaxB) * kMaxB / kTSThreads;  // 24
 
 // Out = B*Mb - Q*Mq for a tile of rows; optional Gram [Q Out]^T Out.
-// C is the arithmetic type (float for the fast first round).
+// CU is the arithmetic type of the update, CG that of the Gram (float for
+// the fast first round).  The tile is staged in shared memory in the
+// arithmetic type when both are the same (one conversion per element
+// loaded, none per multiply-add), else in double.
 template <typename CU, typename CG>
 __global__ void __launch_bounds__(kTSThreads)
 k_ts_pass(const double* __restrict__ Q, int64_t ldq, int K, const double* __restrict__ B,
           int64_t ldb, int b, const double* __restrict__ Mq, const double* __restrict__ Mb,
           int bo, int update, double* __restrict__ Out, int64_t ldo, int gram,
           double* __restrict__ gpart, int64_t m) {
-  extern __shared__ double sm[];
+  using ST = typename std::conditional<std::is_same<CU, CG>::value, CG, double>::type;
+  extern __shared__ double sm_raw[];
+  ST* sm = reinterpret_cast<ST*>(sm_raw);
   const int LD = kRT + 1;
-  double* Qs = sm;                         // [K][LD]
-  double* Bs = Qs + (size_t)K * LD;        // [b][LD]
-  double* Os = Bs + (size_t)b * LD;        // [bo][LD]
-  double* Ms = Os + (size_t)kMaxB * LD;    // Mq [K][bo] then Mb [b][bo]
+  ST* Qs = sm;                             // [K][LD]
+  ST* Bs = Qs + (size_t)K * LD;            // [b][LD]
+  ST* Os = Bs + (size_t)b * LD;            // [bo][LD]
+  ST* Ms = Os + (size_t)kMaxB * LD;        // Mq [K][bo] then Mb [b][bo]
   const int tid = threadIdx.x;
   if (update) {
-    for (int x = tid; x < K * bo; x += blockDim.x) Ms[x] = Mq[(x / bo) + (int64_t)K * (x % bo)];
+    for (int x = tid; x < K * bo; x += blockDim.x) Ms[x] = (ST)Mq[(x / bo) + (int64_t)K * (x % bo)];
     for (int x = tid; x < b * bo; x += blockDim.x)
-      Ms[K * bo + x] = Mb[(x / bo) + (int64_t)b * (x % bo)];
+      Ms[K * bo + x] = (ST)Mb[(x / bo) + (int64_t)b * (x % bo)];
   }
   const int ocols = update ? bo : b;
   const int gw = K + ocols;  // Gram rows
@@ -59,22 +65,22 @@ k_ts_pass(const double* __restrict__ Q, int64_t ldq, int K, const double* __rest
       const int c = x / kRT, r = x % kRT;
       double val = 0.0;
       if (r < rows) val = c < K ? Q[r0 + r + ldq * c] : B[r0 + r + ldb * (c - K)];
-      (c < K ? Qs + (size_t)c * LD : Bs + (size_t)(c - K) * LD)[r] = val;
+      (c < K ? Qs + (size_t)c * LD : Bs + (size_t)(c - K) * LD)[r] = (ST)val;
     }
     __syncthreads();
-    const double* O = Bs;
+    const ST* O = Bs;
     if (update) {
       for (int x = tid; x < bo * kRT; x += blockDim.x) {
         const int j = x / kRT, r = x % kRT;
         CU sacc = CU(0);
         for (int d = 0; d < b; ++d) sacc += (CU)Bs[d * LD + r] * (CU)Ms[K * bo + d * bo + j];
         for (int e = 0; e < K; ++e) sacc -= (CU)Qs[e * LD + r] * (CU)Ms[e * bo + j];
-        Os[j * LD + r] = (double)sacc;
+        Os[j * LD + r] = (ST)sacc;
       }
       __syncthreads();
       for (int x = tid; x < bo * kRT; x += blockDim.x) {
         const int j = x / kRT, r = x % kRT;
-        if (r < rows) Out[r0 + r + ldo * j] = Os[j * LD + r];
+        if (r < rows) Out[r0 + r + ldo * j] = (double)Os[j * LD + r];
       }
       O = Os;
     }
@@ -84,8 +90,8 @@ k_ts_pass(const double* __restrict__ Q, int64_t ldq, int K, const double* __rest
         const int id = tid + u * kTSThreads;
         if (id < gw * ocols) {
           const int i = id % gw, j = id / gw;
-          const double* zi = i < K ? Qs + (size_t)i * LD : O + (size_t)(i - K) * LD;
-          const double* oj = O + (size_t)j * LD;
+          const ST* zi = i < K ? Qs + (size_t)i * LD : O + (size_t)(i - K) * LD;
+          const ST* oj = O + (size_t)j * LD;
           CG s = acc[u];
           for (int r = 0; r < rows; ++r) s += (CG)zi[r] * (CG)oj[r];
           acc[u] = s;
@@ -467,9 +473,13 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
                                       ws.gpart.as<double>(), m, grid, s)));
   reduce(gw * b);
   k_orth_r1<<<1, 256, 0, s>>>(ws.gram.as<double>(), K, b, sm); ::bks::note_launch();
-  // P2: B1 = B - Q H1 (in place) and the FP64 Gram of [Q B1]^T B1
+  // P2: B1 = B - Q H1 (in place) and the Gram of [Q B1]^T B1 (FP32 with
+  // fast_first: the input block then carries FP32 rounding anyway, the
+  // first Cholesky from it only has to leave a well-conditioned block for
+  // the FP64 round P3/P4, and the deferral test res > 1e-3 proj needs a
+  // few digits of res only)
   if (o.fast_first)
-    BKS_TRY((launch_ts<float, double>(Q, ldq, K, B, ldb, b, sm + L.Mq, sm + L.Mb, b, 1, B, ldb, 1,
+    BKS_TRY((launch_ts<float, float>(Q, ldq, K, B, ldb, b, sm + L.Mq, sm + L.Mb, b, 1, B, ldb, 1,
                                      ws.gpart.as<double>(), m, grid, s)));
   else
     BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, sm + L.Mq, sm + L.Mb, b, 1, B, ldb, 1,

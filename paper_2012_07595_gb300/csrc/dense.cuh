@@ -23,7 +23,7 @@ struct OrthOpts {
   double drop_tol = 0.0;          // rank-drop threshold relative to the raw column norm
   int cap = 1 << 30;              // at most this many new columns
   bool two_level = false;         // defer unresolved columns to a second level (needs B = Q + ldq*K)
-  bool fast_first = false;        // first projection round in FP32 arithmetic
+  bool fast_first = false;        // first projection round and its Gram in FP32 arithmetic
   const double* raw = nullptr;    // device raw column norms (b) to test drops against, or null
   double* raw_out = nullptr;      // device: receives the raw column norms
   double* grad_out = nullptr;     // device scalar: ||(B - Q H) M||_F^2 (projected block times M)
@@ -38,8 +38,9 @@ struct OrthOpts {
 // B[:, 0:bo] holds the new orthonormal columns (dropped columns removed).
 // Single-level mode also returns H (K x b, ld K) and R (bo x b, ld b) with
 // B_in = Q H + B_out R up to the dropped residuals.  With `fast_first` the
-// first projection round runs in FP32 arithmetic (reorthogonalisation and
-// QR stay FP64).
+// first projection round and the Gram of the first Cholesky QR run in FP32
+// arithmetic (for blocks that carry FP32 rounding already); the second
+// projection and Cholesky QR stay FP64.
 int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int b, int64_t m,
                const OrthOpts& o, double* H, double* R, int* bo_host, DenseWork& ws,
                cudaStream_t s);

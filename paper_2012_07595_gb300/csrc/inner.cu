@@ -24,7 +24,8 @@ namespace {
 
 constexpr int kInnerThreads = 512;
 constexpr int kMaxR = 8;                 // r1, r3 <= 8
-constexpr int kMaxW = kMaxR * kMaxR;     // r1*r3 and r1^2 <= 64
+constexpr int kMaxW = kMaxR * kMaxR;     // r1^2 <= 64
+constexpr int kMaxW1 = 32;               // r1*r3 <= 32
 
 inline int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
@@ -85,7 +86,8 @@ k_hosvd(const float* __restrict__ part1, const float* __restrict__ part3, int np
       A[x] = s;
     }
     __syncthreads();
-    block_jacobi_eig<float>(A, V, n, 1e-6f, 30, red, cs);
+    // a start only: eigenvectors to a relative threshold of 1e-4
+    block_jacobi_eig<float>(A, V, n, 1e-4f, 30, red, cs);
     top_diag<float>(A, n, r, idx);
     double* out = pass == 0 ? Uh : Wh;
     for (int x = threadIdx.x; x < n * r; x += blockDim.x) {
@@ -100,10 +102,13 @@ k_hosvd(const float* __restrict__ part1, const float* __restrict__ part3, int np
 struct InnerShared {
   double Uh[128 * kMaxR];
   double Wh[128 * kMaxR];
-  double T1[128 * kMaxW];    // k1 x (r1 r3), column b + r1 c
+  double T1[128 * kMaxW1];   // k1 x (r1 r3), column b + r1 c
   double T3[128 * kMaxW];    // k3 x r1^2,    column a + r1 b
   double G[kMaxW * kMaxW];   // small Gram
   double V[kMaxW * kMaxW];
+  float Gf[kMaxW * kMaxW];   // FP32 copy for the first eigen-decomposition
+  float Vf[kMaxW * kMaxW];
+  double lam[kMaxW];
   double F1[kMaxR * kMaxW];
   double F3[kMaxR * kMaxW];
   double FF1[kMaxR * kMaxR];
@@ -112,6 +117,67 @@ struct InnerShared {
   double cs[4 * kMaxW];  // >= 4 * 32 + 64 doubles
   int idx[kMaxW];
 };
+
+// Block-wide sums of three values, returned to thread 0 (other threads get
+// partial values): a shuffle tree in each warp, then a shuffle tree over
+// the warps' sums in warp 0 (a fixed order).  Every thread must call.
+__device__ void block_sum3(double& a, double& b, double& c) {
+  __shared__ double part[3][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    part[0][wid] = a;
+    part[1][wid] = b;
+    part[2][wid] = c;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    a = lane < nw ? part[0][lane] : 0.0;
+    b = lane < nw ? part[1][lane] : 0.0;
+    c = lane < nw ? part[2][lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+      c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+  }
+  __syncthreads();
+}
+
+// Block-wide maxima of three values, returned to thread 0 (the same tree
+// as block_sum3).  Every thread must call.
+__device__ void block_max3(double& a, double& b, double& c) {
+  __shared__ double part[3][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+    c = fmax(c, __shfl_down_sync(0xffffffffu, c, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    part[0][wid] = a;
+    part[1][wid] = b;
+    part[2][wid] = c;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    a = lane < nw ? part[0][lane] : 0.0;
+    b = lane < nw ? part[1][lane] : 0.0;
+    c = lane < nw ? part[2][lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
+      b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+      c = fmax(c, __shfl_down_sync(0xffffffffu, c, o));
+    }
+  }
+  __syncthreads();
+}
 
 // Modified Gram-Schmidt, twice, on the columns of Out (n x r, shared
 // memory; n <= 128, r <= 8), FP64; every thread of the block calls.
@@ -144,15 +210,156 @@ __device__ void block_mgs2(double* Out, int n, int r, double* red) {
   }
 }
 
+// One Cholesky QR pass on the nearly orthonormal columns of Out (n x r,
+// shared, r <= 8): Gram Out^T Out, its Cholesky factor R on one thread,
+// Out <- Out R^-1 row by row.  Falls back to two MGS passes when the Gram
+// is not numerically positive definite.  W: 2 r^2 doubles of shared scratch.
+__device__ void block_cholqr(double* Out, int n, int r, double* W, double* red) {
+  double* G = W;          // r x r Gram, then R (upper), column-major
+  double* Ri = W + r * r; // R^-1
+  for (int x = threadIdx.x; x < r * r; x += blockDim.x) {
+    const int i = x % r, j = x / r;
+    if (i > j) continue;
+    double s = 0.0;
+    for (int t = 0; t < n; ++t) s = fma(Out[t + n * i], Out[t + n * j], s);
+    G[x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    for (int j = 0; j < r && ok; ++j) {
+      for (int i = 0; i <= j; ++i) {
+        double v = G[i + r * j];
+        for (int t = 0; t < i; ++t) v -= G[t + r * i] * G[t + r * j];
+        if (i == j) {
+          if (!(v > 1e-8 * G[j + r * j] + 1e-300)) { ok = false; break; }
+          G[j + r * j] = sqrt(v);
+        } else {
+          G[i + r * j] = v / G[i + r * i];
+        }
+      }
+    }
+    if (ok) {
+      for (int j = 0; j < r; ++j)
+        for (int i = j; i >= 0; --i) {
+          double v = (i == j) ? 1.0 : 0.0;
+          for (int t = i + 1; t <= j; ++t) v -= G[i + r * t] * Ri[t + r * j];
+          Ri[i + r * j] = v / G[i + r * i];
+        }
+    }
+    red[0] = ok ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (red[0] == 0.0) {
+    block_mgs2(Out, n, r, red);
+    return;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double row[kMaxR], o[kMaxR];
+    for (int t = 0; t < r; ++t) row[t] = Out[i + n * t];
+    for (int j = 0; j < r; ++j) {
+      double v = 0.0;
+      for (int t = 0; t <= j; ++t) v = fma(row[t], Ri[t + r * j], v);
+      o[j] = v;
+    }
+    for (int j = 0; j < r; ++j) Out[i + n * j] = o[j];
+  }
+  __syncthreads();
+}
+
+// Eigen-decomposition of the small symmetric G (w x w, FP64, shared):
+// cyclic Jacobi in FP32 on a rounded copy (to its rounding floor), then
+// steps of the iterative
+// refinement of Ogita & Aishima (Japan J. Indust. Appl. Math. 35, 2018) in
+// FP64.  With X the current eigenvector matrix, R = I - X^T X,
+// S = X^T G X, lambda_i = s_ii / (1 - r_ii), the correction X <- X (I + E)
+// has e_ii = r_ii / 2 and, for eigenvalues farther apart than
+// delta = 2 (||offdiag S|| + ||lambda|| ||R||), e_ij = (s_ij + lambda_j r_ij) /
+// (lambda_j - lambda_i); closer pairs get r_ij / 2 (they are a cluster and
+// only their joint span is determined).  Each step squares the relative
+// error; the steps stop after one whose largest correction is below 1e-8
+// (at most four), which takes the FP32 vectors to FP64 accuracy; only FP64
+// matrix products remain, which keeps the FP64 instruction count (a slow
+// pipe on this GPU) small.  On return S.V holds X (row-major,
+// V[i*w + j] = component i of vector j) and S.lam the eigenvalues.
+// P, R, E: w x w FP64 scratch (global).  Every thread of the block calls.
+__device__ void block_eig_refined(int w, InnerShared& S, double* P, double* R, double* E) {
+  for (int x = threadIdx.x; x < w * w; x += blockDim.x) S.Gf[x] = (float)S.G[x];
+  __syncthreads();
+  // one warp: its steps synchronise with __syncwarp only
+  block_jacobi_eig<float>(S.Gf, S.Vf, w, 0.f, 40, reinterpret_cast<float*>(S.red),
+                          reinterpret_cast<float*>(S.cs));
+  for (int x = threadIdx.x; x < w * w; x += blockDim.x) S.V[x] = (double)S.Vf[x];
+  __syncthreads();
+  double* X = S.V;
+  for (int step = 0; step < 4; ++step) {
+    for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
+      const int i = x / w, j = x % w;
+      double pg = 0.0, rr = 0.0;
+      for (int l = 0; l < w; ++l) {
+        pg = fma(S.G[i * w + l], X[l * w + j], pg);
+        rr = fma(X[l * w + i], X[l * w + j], rr);
+      }
+      P[x] = pg;                      // G X
+      R[x] = (i == j ? 1.0 : 0.0) - rr;  // I - X^T X
+    }
+    __syncthreads();
+    double off = 0.0, rn = 0.0, ln = 0.0;
+    for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
+      const int i = x / w, j = x % w;
+      double sv = 0.0;
+      for (int l = 0; l < w; ++l) sv = fma(X[l * w + i], P[l * w + j], sv);
+      E[x] = sv;                      // S = X^T G X (held in E for now)
+      if (i != j) off = fma(sv, sv, off);
+      rn = fma(R[x], R[x], rn);
+      if (i == j) {
+        const double lv = sv / (1.0 - R[x]);
+        S.lam[i] = lv;
+        ln = fma(lv, lv, ln);
+      }
+    }
+    block_sum3(off, rn, ln);
+    if (threadIdx.x == 0) S.red[0] = 2.0 * (sqrt(off) + sqrt(ln) * sqrt(rn));
+    __syncthreads();
+    const double delta = S.red[0];
+    // E <- correction (in place: entry x reads only S(x) = E[x], R and lam)
+    double emax = 0.0;
+    for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
+      const int i = x / w, j = x % w;
+      double e;
+      if (i == j) {
+        e = 0.5 * R[x];
+      } else {
+        const double gap = S.lam[j] - S.lam[i];
+        e = fabs(gap) > delta ? (E[x] + S.lam[j] * R[x]) / gap : 0.5 * R[x];
+      }
+      E[x] = e;
+      emax = fmax(emax, fabs(e));
+    }
+    double d1 = 0.0, d2 = 0.0;
+    block_max3(emax, d1, d2);
+    if (threadIdx.x == 0) S.red[1] = emax;
+    __syncthreads();
+    // X <- X + X E (into P, then back)
+    for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
+      const int i = x / w, j = x % w;
+      double v = X[x];
+      for (int l = 0; l < w; ++l) v = fma(X[i * w + l], E[l * w + j], v);
+      P[x] = v;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < w * w; x += blockDim.x) X[x] = P[x];
+    __syncthreads();
+    // the error left after a step is about the square of its correction
+    if (S.red[1] < 1e-8) break;
+  }
+}
+
 // r leading left singular vectors of T (n x w, ld n) into Out (n x r):
-// eigenvectors of T^T T, Out = T v / sigma, then two MGS passes.
-// K (w x w, row-major, global) carries the eigenvector matrix from one HOOI
-// sweep to the next: with `warm` the Jacobi iteration runs on K^T G K and
-// K <- K J afterwards, so that near convergence, where G changes little
-// between sweeps, one or two Jacobi sweeps suffice; without `warm`, K is
-// set to the eigenvectors found from the identity.  Kt is w x w scratch.
+// eigenvectors of T^T T (block_eig_refined), Out = T v / sigma, then one
+// Cholesky QR pass.  P, R, E: w x w FP64 scratch.
 __device__ void inner_topsvd(const double* T, int n, int w, int r, InnerShared& S, double* Out,
-                             double* K, double* Kt, bool warm) {
+                             double* P, double* R, double* E) {
   for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
     const int i = x % w, j = x / w;
     double s = 0.0;
@@ -160,50 +367,21 @@ __device__ void inner_topsvd(const double* T, int n, int w, int r, InnerShared& 
     S.G[i * w + j] = s;
   }
   __syncthreads();
-  if (warm) {
-    // Kt = G K, then G <- K^T Kt (upper triangle, mirrored)
-    for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
-      const int i = x / w, j = x % w;
-      double s = 0.0;
-      for (int l = 0; l < w; ++l) s = fma(S.G[i * w + l], K[l * w + j], s);
-      Kt[x] = s;
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
-      const int i = x / w, j = x % w;
-      if (i > j) continue;
-      double s = 0.0;
-      for (int l = 0; l < w; ++l) s = fma(K[l * w + i], Kt[l * w + j], s);
-      S.G[i * w + j] = s;
-      S.G[j * w + i] = s;
-    }
-    __syncthreads();
-  }
-  block_jacobi_eig<double>(S.G, S.V, w, 0.0, 40, S.red, S.cs);
-  if (warm) {
-    for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
-      const int i = x / w, j = x % w;
-      double s = 0.0;
-      for (int l = 0; l < w; ++l) s = fma(K[i * w + l], S.V[l * w + j], s);
-      Kt[x] = s;
-    }
-    __syncthreads();
-  }
-  for (int x = threadIdx.x; x < w * w; x += blockDim.x) {
-    const double v = warm ? Kt[x] : S.V[x];
-    K[x] = v;
-    S.V[x] = v;
-  }
+  block_eig_refined(w, S, P, R, E);
+  // the r largest eigenvalues (descending) on the diagonal of S.G
+  for (int i = threadIdx.x; i < w; i += blockDim.x) S.G[i * w + i] = S.lam[i];
   __syncthreads();
   top_diag<double>(S.G, w, r, S.idx);
+  // Out = T v_t / sqrt(lambda_t): orthonormal up to the eigenvectors' error
   for (int x = threadIdx.x; x < n * r; x += blockDim.x) {
     const int i = x % n, t = x / n;
     double s = 0.0;
     for (int j = 0; j < w; ++j) s = fma(T[i + n * j], S.V[j * w + S.idx[t]], s);
-    Out[i + n * t] = s;
+    const double lt = S.lam[S.idx[t]];
+    Out[i + n * t] = lt > 0.0 ? s * nr_rsqrt(lt) : s;
   }
   __syncthreads();
-  block_mgs2(Out, n, r, S.red);
+  block_cholqr(Out, n, r, S.G, S.red);
 }
 
 // G-gradient of the inner problem at (Uh, Wh) from T1 (at Uh, Wh) and T3
@@ -261,23 +439,10 @@ __device__ void inner_grad(int k1, int k3, int r1, int r3, InnerShared& S, doubl
     g3 = fma(d, d, g3);
   }
   for (int x = threadIdx.x; x < r1 * w1; x += blockDim.x) nf = fma(S.F1[x], S.F1[x], nf);
-  for (int o = 16; o > 0; o >>= 1) {
-    g1 += __shfl_down_sync(0xffffffffu, g1, o);
-    g3 += __shfl_down_sync(0xffffffffu, g3, o);
-    nf += __shfl_down_sync(0xffffffffu, nf, o);
-  }
-  __shared__ double part[3][32];
-  if ((threadIdx.x & 31) == 0) {
-    part[0][threadIdx.x >> 5] = g1;
-    part[1][threadIdx.x >> 5] = g3;
-    part[2][threadIdx.x >> 5] = nf;
-  }
-  __syncthreads();
+  block_sum3(g1, g3, nf);
   if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += part[0][w]; b += part[1][w]; c += part[2][w]; }
-    *gout = sqrt(2.0 * a + b);
-    *fout = sqrt(c);
+    *gout = sqrt(2.0 * g1 + g3);
+    *fout = sqrt(nf);
   }
   __syncthreads();
 }
@@ -307,9 +472,9 @@ struct CoopArgs {
   double* T1;         // k1 x r1 r3
   double* T3;         // k3 x r1^2
   double* ctl;        // [0] grad [1] normF [2] stop flag
-  double* K1;         // r1 r3 x r1 r3: eigenvectors carried across sweeps (mode 1)
-  double* K3;         // r1^2 x r1^2 (mode 3)
-  double* Kt;         // scratch
+  double* P;          // three w x w FP64 scratch matrices of the eigensolver
+  double* R;
+  double* E2;
   double* Uh_out;
   double* Wh_out;
   double* negU;
@@ -400,7 +565,7 @@ __device__ int coop_sweeps(const CoopArgs& a, int max_sweeps, double tol, InnerS
       const double g = a.ctl[0], nf = a.ctl[1];
       const bool stop = done >= max_sweeps || g <= tol * nf;
       if (!stop) {
-        inner_topsvd(S.T1, a.k1, a.r1 * a.r3, a.r1, S, S.Uh, a.K1, a.Kt, done > 0);
+        inner_topsvd(S.T1, a.k1, a.r1 * a.r3, a.r1, S, S.Uh, a.P, a.R, a.E2);
         block_copy(S.Uh, a.Ug, a.k1 * a.r1);
       }
       if (threadIdx.x == 0) a.ctl[2] = stop ? 1.0 : 0.0;
@@ -415,7 +580,7 @@ __device__ int coop_sweeps(const CoopArgs& a, int max_sweeps, double tol, InnerS
     if (blockIdx.x == 0) {
       block_copy(a.T3, S.T3, a.k3 * a.r1 * a.r1);
       __syncthreads();
-      inner_topsvd(S.T3, a.k3, a.r1 * a.r1, a.r3, S, S.Wh, a.K3, a.Kt, done > 0);
+      inner_topsvd(S.T3, a.k3, a.r1 * a.r1, a.r3, S, S.Wh, a.P, a.R, a.E2);
       block_copy(S.Wh, a.Wg, a.k3 * a.r3);
       __threadfence();
     }
@@ -512,7 +677,8 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   k_hosvd_grams<<<nparts, 256, 0, s>>>(C, k1, k3, w.part1.as<float>(), w.part3.as<float>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   const int nmax = std::max(k1, k3);
-  const size_t hs = sizeof(float) * (2 * (size_t)nmax * nmax + 64 + 4 * (size_t)nmax);
+  // A, V (nmax^2 each), red (64), cs (the one-warp Jacobi needs 128)
+  const size_t hs = sizeof(float) * (2 * (size_t)nmax * nmax + 64 + std::max<size_t>(128, 4 * (size_t)nmax));
   static bool attr = false;
   if (!attr) {
     BKS_CUDA_TRY(cudaFuncSetAttribute(k_hosvd, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -552,7 +718,7 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   a.Ug = w.Ug.as<double>(); a.Wg = w.Wg.as<double>(); a.Ub = w.Ub.as<double>();
   a.Wb = w.Wb.as<double>(); a.D = w.D.as<double>(); a.E = w.E.as<double>();
   a.T1 = w.T1.as<double>(); a.T3 = w.T3.as<double>(); a.ctl = w.ctl.as<double>();
-  a.K1 = w.K.as<double>(); a.K3 = a.K1 + kMaxW * kMaxW; a.Kt = a.K3 + kMaxW * kMaxW;
+  a.P = w.K.as<double>(); a.R = a.P + kMaxW * kMaxW; a.E2 = a.R + kMaxW * kMaxW;
   a.Uh_out = Uh; a.Wh_out = Wh; a.negU = negU; a.negW = negW; a.info = info;
   void* kargs[] = {&a};
   BKS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_inner_coop, dim3(grid),

@@ -11,16 +11,20 @@ namespace bks {
 // overwritten by a nearly diagonal matrix; V: n x n in shared memory,
 // receives the eigenvectors (columns).  Every thread of the block must call.
 // `red` is 64 elements of shared scratch, `cs` 4*64.  Threshold Jacobi: a
-// pair is rotated only while |a_pq| > eps sqrt(a_pp a_qq) and |a_pq| >
-// 1e-2 eps trace(A); the sweeps stop after a sweep without rotations.
+// pair is rotated only while |a_pq| > tol sqrt(a_pp a_qq) and |a_pq| >
+// f trace(A), tol = the unit roundoff unless a larger tol is given and
+// f = 1e-2 tol in FP64, 4 units of roundoff in FP32; the sweeps stop after
+// a sweep without rotations.
 // For FP64 the rotation angle is computed in FP32 from FP64 differences and
 // the pair (c, s) is then normalised in FP64, so every rotation is
 // orthogonal to FP64 precision while costing few FP64 instructions (the
-// angle's accuracy only sets how fast a_pq goes to zero).  Returns the
-// number of sweeps.
+// angle's accuracy only sets how fast a_pq goes to zero).  In FP32 the
+// angle is exact to working precision and the rotated a_pq is set to zero
+// (the rounding residue would otherwise keep the threshold test from ever
+// passing when the diagonal entries differ by orders of magnitude).
+// Returns the number of sweeps.
 template <typename T>
 __device__ int block_jacobi_eig(T* A, T* V, int n, T tol, int max_sweeps, T* red, T* cs) {
-  (void)tol;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int x = tid; x < n * n; x += nt) V[x] = (x % n == x / n) ? T(1) : T(0);
   if (tid == 0) {
@@ -30,9 +34,13 @@ __device__ int block_jacobi_eig(T* A, T* V, int n, T tol, int max_sweeps, T* red
   }
   __syncthreads();
   if (n <= 1) return 0;
-  const T eps = sizeof(T) == 4 ? T(1.1920929e-7) : T(2.220446049250313e-16);
+  const T ulp = sizeof(T) == 4 ? T(1.1920929e-7) : T(2.220446049250313e-16);
+  const T eps = tol > ulp ? tol : ulp;
   const T eps2 = eps * eps;
-  const T floor2 = (T(1e-2) * eps * red[0]) * (T(1e-2) * eps * red[0]);
+  // absolute floor: in FP32 entries below a few units of roundoff of the
+  // trace are rounding noise of the other rotations
+  const T fl = sizeof(T) == 4 ? T(4) * ulp : T(1e-2) * eps;
+  const T floor2 = (fl * red[0]) * (fl * red[0]);
   const int N = (n + 1) & ~1;  // even number of players (one dummy if n is odd)
   const int half = N / 2;
   int sweep = 0;
@@ -96,8 +104,8 @@ __device__ int block_jacobi_eig(T* A, T* V, int n, T tol, int max_sweeps, T* red
         if (q < 0) continue;
         T c = cs[4 * pi], s = cs[4 * pi + 1];
         T apk = A[p * n + k], aqk = A[q * n + k];
-        A[p * n + k] = c * apk - s * aqk;
-        A[q * n + k] = s * apk + c * aqk;
+        A[p * n + k] = (sizeof(T) == 4 && k == q) ? T(0) : c * apk - s * aqk;
+        A[q * n + k] = (sizeof(T) == 4 && k == p) ? T(0) : s * apk + c * aqk;
       }
       __syncthreads();
     }
@@ -161,8 +169,8 @@ __device__ __forceinline__ double nr_rsqrt(double a) {
 // sweeps stop when a sweep rotates nothing.  V receives the eigenvectors
 // (columns).  cs is shared scratch of 128 elements of T.  Only the calling
 // warp may touch A, V, cs.  Used in single precision, where the rotations
-// run at the full instruction rate; FP64 accuracy is restored afterwards
-// by a Rayleigh-Ritz correction (see the inner solve).
+// run at the full instruction rate; the inner solve then refines the
+// vectors to FP64 accuracy.
 __device__ __forceinline__ float rcp_t(float a) { return 1.0f / a; }
 __device__ __forceinline__ double rcp_t(double a) { return nr_rcp(a); }
 __device__ __forceinline__ float rsqrt_t(float a) { return rsqrtf(a); }
