@@ -131,7 +131,7 @@ int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
  *   rows) lives in a fixed 32 MiB device array inside the library, which
  *   every GPU that loads the library keeps until the process exits; a call
  *   needing more (about 4*8*m + 4*8*n + 8*32*(nnz/split) bytes in FP64,
- *   split = 256 unless bks_tensor_autotune / set_tiles chose another)
+ *   split = 512 unless bks_tensor_autotune / set_tiles chose another)
  *   returns BKS_EUNSUPPORTED before launching anything.  The call allocates
  *   nothing.  Its first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
@@ -239,16 +239,19 @@ int hooi_solve(const bks_tensor* t, const hooi_params* prm, const double* U0,
                const double* W0, double* U, double* W, double* F,
                bks_info* info, void* stream);
 
-/* ---- work-tile autotuning ------------------------------------------------
- * The contractions process a tensor in warp tiles: rows longer than `split`
- * entries are cut into pieces of at most `split`, and a tile holds the
- * pieces that start in a window of `tile` entries (see the contraction
- * comments).  The best sizes depend on how the entries spread over rows.
+/* ---- work-plan autotuning ------------------------------------------------
+ * The contractions process a tensor by rows: rows longer than `split`
+ * entries are cut into pieces of at most `split` (their partial sums are
+ * added in a fixed order by a second kernel); pieces and rows longer than
+ * `tile` entries take one warp each, the others one lane each, 32 to a
+ * warp in order of decreasing length.  The best sizes depend on how the
+ * entries spread over rows.  The default is (tile, split) = (16, 512).
  * bks_tensor_autotune times the mode-1 and triangle mode-3 contractions
- * (FP32, widths 4 x 4) under the plans (tile, split) in {(128,128),
- * (256,256), (512,512), (256,512)} and keeps the fastest; tile and split
+ * (FP32, widths 4 x 4) under the plans (tile, split) in {(8,512),
+ * (32,512), (16,1024), (16,512)} and keeps the fastest; tile and split
  * (host, nullable) receive the choice.  bks_tensor_set_tiles applies a
- * known choice (32 <= tile, split <= 512).  Both synchronise `stream`. */
+ * known choice (1 <= tile <= 64, 128 <= split <= 4096; else BKS_EINVAL).
+ * Both synchronise `stream`. */
 int bks_tensor_autotune(bks_tensor* t, int* tile, int* split, void* stream);
 int bks_tensor_set_tiles(bks_tensor* t, int tile, int split, void* stream);
 

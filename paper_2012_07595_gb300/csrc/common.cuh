@@ -81,16 +81,19 @@ struct DevBuf {
 };
 
 // ---- stored tensor layout -------------------------------------------------
-// Work tiles of the sparse contractions.  A row longer than `split`
-// entries is cut into "virtual rows" of at most `split` entries; tile t of a
-// part holds the virtual rows whose first entry lies in
-// [t*tile, (t+1)*tile), so a tile spans at most tile + split entries and
-// never cuts a virtual row.  One warp processes one tile.  The sizes are per
-// tensor (defaults below; bks_tensor_autotune picks them by timing).
-constexpr int kTile = 256;
-constexpr int kSplit = 256;
-constexpr int kMaxTile = 512;
-constexpr int kMaxSplit = 512;
+// Work plan of the sparse contractions.  A row longer than `split` entries
+// is cut into "virtual rows" of at most `split` entries (their sums go to
+// per-piece partials that a second kernel adds in a fixed order).  Virtual
+// rows of at most `tile` entries ("short") are processed one per lane, 32
+// to a warp, in order of decreasing length so that the lanes of a warp run
+// loops of nearly equal trip count; longer ones are processed one per warp
+// with the lanes striding over the entries.  The sizes are per tensor
+// (defaults below; bks_tensor_autotune picks them by timing).
+constexpr int kTile = 16;
+constexpr int kSplit = 512;
+constexpr int kMaxTile = 64;
+constexpr int kMinSplit = 128;
+constexpr int kMaxSplit = 4096;
 
 struct Part {
   // one sorted copy of the stored entries, CSR over `rows`
@@ -103,18 +106,19 @@ struct Part {
   DevBuf v64;      // double [nnz] when the input dtype is float
   // tile plan
   int tile = kTile, split = kSplit;
-  int32_t nv = 0, ntiles = 0, nslots = 0, nsplit = 0;
+  int32_t nv = 0, nslots = 0, nsplit = 0;
+  int32_t nvec = 0, nshortv = 0;  // virtual rows taken one per warp / one per lane
   DevBuf vptr;        // int32 [nv+1]   first entry of each virtual row
   DevBuf vrow;        // int32 [nv]     row of each virtual row
   DevBuf vslot;       // int32 [nv]     partial-sum slot, -1 if the row is not cut
-  DevBuf tile_first;  // int32 [ntiles+1] first virtual row of each tile
+  DevBuf vorder;      // int32 [nv]: the nvec warp rows, then the short rows by decreasing length
   DevBuf split_row;   // int32 [nsplit]   rows that were cut
   DevBuf split_first; // int32 [nsplit+1] their first slot (slots are consecutive)
   int32_t nempty = 0;
   DevBuf empty_rows;  // int32 [nempty] rows without entries (their output is zero)
   std::vector<int32_t> host_ptr;  // host copy of ptr (kept for the mode-3 copy only)
   void persist() {
-    for (DevBuf* b : {&ptr, &c0, &c1, &v, &v32, &v64, &vptr, &vrow, &vslot, &tile_first,
+    for (DevBuf* b : {&ptr, &c0, &c1, &v, &v32, &v64, &vptr, &vrow, &vslot, &vorder,
                       &split_row, &split_first, &empty_rows})
       b->persist();
   }

@@ -84,19 +84,34 @@ __device__ __forceinline__ void accumulate(T (&acc)[Shape<PB, QB, TRI>::W], T v,
 }
 
 struct TileArgs {
-  const int32_t* tile_first;
+  const int32_t* vorder;  // the nvec warp rows, then the short rows by decreasing length
   const int32_t* vptr;
   const int32_t* vrow;
   const int32_t* vslot;
-  int32_t ntiles;
+  int32_t nvec, nshortv;
   const int32_t* ia;   // index into operand A per entry
   const int32_t* ib;   // index into operand B per entry
 };
 
-// Sum of the entries [lo, hi) of the tile's data into acc.  The index and
-// value streams are read 4 entries at a time with 16-byte loads once the
-// position is 4-aligned, and the 4 entries' gathers are issued before any
-// of them is consumed, so each lane keeps several loads in flight.
+// Row load from global or shared memory (the B operand may be staged in
+// shared memory), 16 bytes at a time when the row size allows.
+template <typename T, int N>
+__device__ __forceinline__ void load_row_any(const T* base, T (&x)[N]) {
+  if constexpr (sizeof(T) * N % 16 == 0) {
+#pragma unroll
+    for (int t = 0; t < (int)(sizeof(T) * N / 16); ++t) {
+      const float4 q = reinterpret_cast<const float4*>(base)[t];
+      const T* qq = reinterpret_cast<const T*>(&q);
+#pragma unroll
+      for (int u = 0; u < (int)(16 / sizeof(T)); ++u) x[t * (16 / sizeof(T)) + u] = qq[u];
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < N; ++t) x[t] = base[t];
+  }
+}
+
+// One entry's products into acc: v * A[ia,:]^T B[ib,:].
 template <typename T, int PB, int QB, bool TRI>
 __device__ __forceinline__ void one_entry(int e, const TileArgs& ta, const T* __restrict__ vals,
                                           const T* __restrict__ Ap, const T* __restrict__ Bp,
@@ -107,7 +122,7 @@ __device__ __forceinline__ void one_entry(int e, const TileArgs& ta, const T* __
   const T v = __ldg(vals + e);
   T xa[PB], xb[NB];
   load_row<T, PB>(Ap + (int64_t)ia * PB, xa);
-  load_row<T, NB>(Bp + (int64_t)ib * NB, xb);
+  load_row_any<T, NB>(Bp + (int64_t)ib * NB, xb);
   accumulate<T, PB, QB, TRI>(acc, v, xa, xb);
 }
 
@@ -121,34 +136,6 @@ __device__ __forceinline__ void load4(const T* __restrict__ p, T (&v)[4]) {
     double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   }
-}
-
-template <typename T, int PB, int QB, bool TRI>
-__device__ __forceinline__ void run_entries(int lo, int hi, const TileArgs& ta,
-                                            const T* __restrict__ vals,
-                                            const T* __restrict__ Ap,
-                                            const T* __restrict__ Bp,
-                                            T (&acc)[Shape<PB, QB, TRI>::W]) {
-  constexpr int NB = TRI ? PB : QB;
-  int e = lo;
-  while (e < hi && (e & 3)) one_entry<T, PB, QB, TRI>(e++, ta, vals, Ap, Bp, acc);
-  for (; e + 4 <= hi; e += 4) {
-    const int4 ia = __ldg(reinterpret_cast<const int4*>(ta.ia + e));
-    const int4 ib = __ldg(reinterpret_cast<const int4*>(ta.ib + e));
-    T v[4];
-    load4<T>(vals + e, v);
-    const int iav[4] = {ia.x, ia.y, ia.z, ia.w};
-    const int ibv[4] = {ib.x, ib.y, ib.z, ib.w};
-    T xa[4][PB], xb[4][NB];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      load_row<T, PB>(Ap + (int64_t)iav[u] * PB, xa[u]);
-      load_row<T, NB>(Bp + (int64_t)ibv[u] * NB, xb[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, v[u], xa[u], xb[u]);
-  }
-  while (e < hi) one_entry<T, PB, QB, TRI>(e++, ta, vals, Ap, Bp, acc);
 }
 
 template <typename T, typename OT, int PB, int QB, bool TRI>
@@ -180,93 +167,184 @@ __device__ __forceinline__ void flush_row(int vr, const TileArgs& ta,
   }
 }
 
-// largest v in [lo, hi) with sv[v - base] <= e, on the warp's shared copy
-__device__ __forceinline__ int upper_vrow(const int* sv, int base, int lo, int hi, int e) {
-  int a = lo, b = hi;
-  while (b - a > 1) {
-    int mid = (a + b) >> 1;
-    if (sv[mid - base] <= e) a = mid; else b = mid;
+constexpr int kWarpsPerBlock = 4;
+
+constexpr int next_pow2(int x) { return x <= 1 ? 1 : 2 * next_pow2((x + 1) / 2); }
+
+// One level of a recursive-halving sum over the lanes: each lane holds N
+// values; the lanes with bit `o` set keep the upper half and receive it
+// from the partner lane (lane ^ o), the others keep the lower half, so that
+// every lane ends with N/2 sums.  With N = 1 the value is added as it is.
+template <typename T, int N>
+__device__ __forceinline__ void halve(T* a, int lane, int o) {
+  if constexpr (N >= 2) {
+    constexpr int H = N / 2;
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int c = 0; c < H; ++c) {
+      const T send = upper ? a[c] : a[H + c];
+      const T keep = upper ? a[H + c] : a[c];
+      a[c] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  } else {
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
   }
-  return a;
 }
 
-constexpr int kWarpsPerBlock = 8;
-constexpr int kMaxTileVrows = kMaxTile + kMaxSplit + 1;  // virtual rows of one tile, +1 end
-
+// Warp sum of acc[W] (five halving levels, a fixed order), written to the
+// virtual row's output row or partial slot by the lanes that hold each sum.
 template <typename T, typename OT, int PB, int QB, bool TRI>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void warp_reduce_flush(int vr, const TileArgs& ta,
+                                                  const T (&acc)[Shape<PB, QB, TRI>::W], int p,
+                                                  int q, OT* __restrict__ out, int64_t ldo,
+                                                  T* __restrict__ partial, int lane) {
+  constexpr int W = Shape<PB, QB, TRI>::W;
+  constexpr int W2 = next_pow2(W);
+  T a[W2];
+#pragma unroll
+  for (int c = 0; c < W2; ++c) a[c] = c < W ? acc[c] : T(0);
+  halve<T, W2>(a, lane, 16);
+  halve<T, (W2 / 2 > 1 ? W2 / 2 : 1)>(a, lane, 8);
+  halve<T, (W2 / 4 > 1 ? W2 / 4 : 1)>(a, lane, 4);
+  halve<T, (W2 / 8 > 1 ? W2 / 8 : 1)>(a, lane, 2);
+  halve<T, (W2 / 16 > 1 ? W2 / 16 : 1)>(a, lane, 1);
+  // index of a[0] in this lane, and whether this lane is the first of the
+  // lanes that hold the same sums
+  int base = 0;
+  bool writer = true;
+  {
+    int n = W2;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      if (n >= 2) {
+        n >>= 1;
+        if (lane & o) base += n;
+      } else if (lane & o) {
+        writer = false;
+      }
+    }
+  }
+  if (!writer) return;
+  constexpr int R = W2 / 32 > 1 ? W2 / 32 : 1;
+  const int slot = __ldg(ta.vslot + vr);
+  const int64_t row = __ldg(ta.vrow + vr);
+#pragma unroll
+  for (int c = 0; c < R; ++c) {
+    const int idx = base + c;
+    if (idx >= W) continue;
+    if (slot >= 0) {
+      partial[(int64_t)slot * W + idx] = a[c];
+      continue;
+    }
+    if constexpr (TRI) {
+      int b = 0;
+      while ((b + 1) * (b + 2) / 2 <= idx) ++b;
+      if (b < p) out[row + ldo * idx] = (OT)a[c];
+    } else {
+      const int aa = idx % PB, bb = idx / PB;
+      if (aa < p && bb < q) out[row + ldo * (aa + p * bb)] = (OT)a[c];
+    }
+  }
+}
+
+// Mode-1 / mode-3 contraction over the work plan (see common.cuh):
+// warps [0, nvec) take one long virtual row each, the lanes striding over
+// its entries 4 at a time (coalesced index and value loads) and the lane
+// sums combined by warp_reduce_flush; the following warps take 32 short
+// virtual rows each, one per lane, ordered by decreasing length, each lane
+// summing its row in registers.  No atomics: the sums have a fixed order.
+template <typename T, typename OT, int PB, int QB, bool TRI>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
-           const T* __restrict__ Bp, int p, int q, OT* __restrict__ out, int64_t ldo,
+           const T* Bp, int bstage, int p, int q, OT* __restrict__ out, int64_t ldo,
            T* __restrict__ partial) {
   constexpr int W = Shape<PB, QB, TRI>::W;
-  __shared__ int s_vptr[kWarpsPerBlock][kMaxTileVrows];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int tile = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (tile >= ta.ntiles) return;
-  const int v0 = __ldg(ta.tile_first + tile), v1 = __ldg(ta.tile_first + tile + 1);
-  if (v0 >= v1) return;
-  // the tile's virtual-row starts, staged once (coalesced) for all lanes
-  int* sv = s_vptr[wib];
-  for (int v = v0 + lane; v <= v1; v += 32) sv[v - v0] = __ldg(ta.vptr + v);
-  __syncwarp();
-  const int e0 = sv[0], e1 = sv[v1 - v0];
-  const int per = (e1 - e0 + 31) >> 5;
-  const int lo = min(e1, e0 + lane * per), hi = min(e1, lo + per);
-  const bool has = lo < hi;
-
-  int vf = -1, vl = -1;
-  bool head = false, open_tail = false;
-  if (has) {
-    vf = upper_vrow(sv, v0, v0, v1, lo);
-    vl = upper_vrow(sv, v0, vf, v1, hi - 1);
-    head = sv[vf - v0] < lo;
-    open_tail = sv[vl + 1 - v0] > hi && !(head && vl == vf);
+  constexpr int NB = TRI ? PB : QB;
+  // a small B operand (bstage > 0 rows, e.g. the n x q block of the mode-1
+  // contraction) is copied to shared memory once per block: its gathers
+  // then cost no L1 tag lookups
+  extern __shared__ __align__(16) unsigned char bsm_raw[];
+  if (bstage > 0) {
+    T* bs = reinterpret_cast<T*>(bsm_raw);
+    for (int x = threadIdx.x; x < bstage * NB; x += blockDim.x) bs[x] = Bp[x];
+    __syncthreads();
+    Bp = bs;
   }
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   T acc[W];
 #pragma unroll
   for (int c = 0; c < W; ++c) acc[c] = T(0);
-  // phase A: the head piece (a row that began in an earlier lane)
-  if (head) {
-    int hend = min(hi, sv[vf + 1 - v0]);
-    run_entries<T, PB, QB, TRI>(lo, hend, ta, vals, Ap, Bp, acc);
-  }
-  // phase B: segmented suffix sum of head pieces over lanes (key = row)
-  int key = head ? vf : -1 - lane;
+  if (gw < ta.nvec) {
+    const int vr = __ldg(ta.vorder + gw);
+    const int s = __ldg(ta.vptr + vr), e = __ldg(ta.vptr + vr + 1);
+    int x = s + lane;
+    // software pipeline: the next group's indices and values are loaded
+    // while the current group's gathers are in flight
+    int iav[4], ibv[4];
+    T v[4];
+    if (x + 96 < e) {
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int ok = __shfl_down_sync(0xffffffffu, key, o);
-    bool take = (lane + o < 32) && ok == key;
-#pragma unroll
-    for (int c = 0; c < W; ++c) {
-      T other = __shfl_down_sync(0xffffffffu, acc[c], o);
-      if (take) acc[c] += other;
+      for (int u = 0; u < 4; ++u) {
+        iav[u] = __ldg(ta.ia + x + 32 * u);
+        ibv[u] = __ldg(ta.ib + x + 32 * u);
+        v[u] = __ldg(vals + x + 32 * u);
+      }
     }
-  }
-  // the owner of an open tail starts from the sum of the later lanes' heads
-  int nkey = __shfl_down_sync(0xffffffffu, key, 1);
-  bool carry = open_tail && lane < 31 && nkey == vl;
+    while (x + 96 < e) {
+      T xa[4][PB], xb[4][NB];
 #pragma unroll
-  for (int c = 0; c < W; ++c) {
-    T other = __shfl_down_sync(0xffffffffu, acc[c], 1);
-    acc[c] = carry ? other : T(0);
-  }
-  if (!has) return;
-  // phase C1: the open tail (owned, continues into later lanes)
-  if (open_tail) {
-    run_entries<T, PB, QB, TRI>(sv[vl - v0], hi, ta, vals, Ap, Bp, acc);
-    flush_row<T, OT, PB, QB, TRI>(vl, ta, acc, p, q, out, ldo, partial);
-  }
-  // phase C2: owned rows that end inside this lane
-  const int first_owned = head ? vf + 1 : vf;
-  const int last_owned = open_tail ? vl - 1 : vl;
-  for (int v = first_owned; v <= last_owned; ++v) {
+      for (int u = 0; u < 4; ++u) {
+        load_row<T, PB>(Ap + (int64_t)iav[u] * PB, xa[u]);
+        load_row_any<T, NB>(Bp + (int64_t)ibv[u] * NB, xb[u]);
+      }
+      T vc[4] = {v[0], v[1], v[2], v[3]};
+      x += 128;
+      if (x + 96 < e) {
 #pragma unroll
-    for (int c = 0; c < W; ++c) acc[c] = T(0);
-    run_entries<T, PB, QB, TRI>(sv[v - v0], sv[v + 1 - v0], ta, vals, Ap, Bp, acc);
-    flush_row<T, OT, PB, QB, TRI>(v, ta, acc, p, q, out, ldo, partial);
+        for (int u = 0; u < 4; ++u) {
+          iav[u] = __ldg(ta.ia + x + 32 * u);
+          ibv[u] = __ldg(ta.ib + x + 32 * u);
+          v[u] = __ldg(vals + x + 32 * u);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, vc[u], xa[u], xb[u]);
+    }
+    for (; x < e; x += 32) one_entry<T, PB, QB, TRI>(x, ta, vals, Ap, Bp, acc);
+    warp_reduce_flush<T, OT, PB, QB, TRI>(vr, ta, acc, p, q, out, ldo, partial, lane);
+    return;
   }
+  const int sidx = (gw - ta.nvec) * 32 + lane;
+  if (sidx >= ta.nshortv) return;
+  const int vr = __ldg(ta.vorder + ta.nvec + sidx);
+  const int s = __ldg(ta.vptr + vr), e = __ldg(ta.vptr + vr + 1);
+  int x = s;
+  for (; x + 4 <= e; x += 4) {
+    int iav[4], ibv[4];
+    T v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      iav[u] = __ldg(ta.ia + x + u);
+      ibv[u] = __ldg(ta.ib + x + u);
+      v[u] = __ldg(vals + x + u);
+    }
+    T xa[4][PB], xb[4][NB];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      load_row<T, PB>(Ap + (int64_t)iav[u] * PB, xa[u]);
+      load_row_any<T, NB>(Bp + (int64_t)ibv[u] * NB, xb[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, v[u], xa[u], xb[u]);
+  }
+  for (; x < e; ++x) one_entry<T, PB, QB, TRI>(x, ta, vals, Ap, Bp, acc);
+  flush_row<T, OT, PB, QB, TRI>(vr, ta, acc, p, q, out, ldo, partial);
 }
+
+// number of warps of a plan
+inline int plan_warps(const Part& P) { return P.nvec + (P.nshortv + 31) / 32; }
+
 
 // Rows cut into pieces: add the pieces' partial sums in a fixed order.
 template <typename T, typename OT, int PB, int QB, bool TRI>
@@ -331,18 +409,23 @@ template <> const double* values_of<double>(const Part& P, int vdtype) {
 // One launch pair (tile kernel + piece reduction) for fixed buckets.
 template <typename T, typename OT, int PB, int QB, bool TRI>
 int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib,
-                    const T* Ap, const T* Bp, int p, int q, OT* out, int64_t ldo,
+                    const T* Ap, const T* Bp, int64_t brows, int p, int q, OT* out, int64_t ldo,
                     cudaStream_t s) {
   constexpr int W = Shape<PB, QB, TRI>::W;
-  TileArgs ta{P.tile_first.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
-              P.vslot.as<int32_t>(), P.ntiles, ia, ib};
+  constexpr int NB = TRI ? PB : QB;
+  // B operands of at most 16 KB are staged in shared memory
+  const int bstage = (brows * NB * (int64_t)sizeof(T) <= 16384) ? (int)brows : 0;
+  const size_t bsm = (size_t)bstage * NB * sizeof(T);
+  TileArgs ta{P.vorder.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
+              P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib};
   DevBuf partial;
   if (P.nslots > 0) BKS_TRY(partial.alloc(sizeof(T) * (size_t)P.nslots * W, s));
   const int warps = kWarpsPerBlock;
-  const int blocks = (P.ntiles + warps - 1) / warps;
+  const int blocks = (plan_warps(P) + warps - 1) / warps;
   if (P.nv > 0) {
-    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,
-                                                                 Bp, p, q, out, ldo, partial.as<T>()); ::bks::note_launch();
+    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, bsm, s>>>(ta, values_of<T>(P, vdtype), Ap,
+                                                                   Bp, bstage, p, q, out, ldo,
+                                                                   partial.as<T>()); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (P.nsplit > 0) {
@@ -362,17 +445,20 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
 
 template <typename T, typename OT>
 int dispatch(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib, const T* Ap,
-             int PB, const T* Bp, int QB, bool tri, int p, int q, OT* out, int64_t ldo,
-             cudaStream_t s) {
+             int PB, const T* Bp, int QB, int64_t brows, bool tri, int p, int q, OT* out,
+             int64_t ldo, cudaStream_t s) {
 #define BKS_CASE(pb, qb)                                                                      \
   if (!tri && PB == pb && QB == qb)                                                           \
-    return launch_contract<T, OT, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, out, ldo, s);
+    return launch_contract<T, OT, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, brows, p, q, out, ldo, s);
   BKS_CASE(2, 2) BKS_CASE(2, 4) BKS_CASE(2, 8) BKS_CASE(4, 2) BKS_CASE(4, 4) BKS_CASE(4, 8)
   BKS_CASE(8, 2) BKS_CASE(8, 4)
 #undef BKS_CASE
-  if (tri && PB == 2) return launch_contract<T, OT, 2, 2, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
-  if (tri && PB == 4) return launch_contract<T, OT, 4, 4, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
-  if (tri && PB == 8) return launch_contract<T, OT, 8, 8, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
+  if (tri && PB == 2)
+    return launch_contract<T, OT, 2, 2, true>(P, vdtype, ia, ib, Ap, Bp, brows, p, p, out, ldo, s);
+  if (tri && PB == 4)
+    return launch_contract<T, OT, 4, 4, true>(P, vdtype, ia, ib, Ap, Bp, brows, p, p, out, ldo, s);
+  if (tri && PB == 8)
+    return launch_contract<T, OT, 8, 8, true>(P, vdtype, ia, ib, Ap, Bp, brows, p, p, out, ldo, s);
   return fail(BKS_EUNSUPPORTED, "contraction bucket not instantiated");
 }
 
@@ -399,8 +485,8 @@ int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
     BKS_TRY((pack<T, IT>(Y + ldy * q0, ldy, t->n, qq, QB, Yp, s)));
     // columns a + p*(q0 + b) of the full output start at column p*q0
     BKS_TRY((dispatch<T, OT>(t->m1, t->vdtype, t->m1.c1.as<int32_t>(), t->m1.c0.as<int32_t>(),
-                        Xp.as<T>(), PB, Yp.as<T>(), QB, false, p, qq, out + ldo * (p * q0), ldo,
-                        s)));
+                        Xp.as<T>(), PB, Yp.as<T>(), QB, t->n, false, p, qq,
+                        out + ldo * (p * q0), ldo, s)));
   }
   return BKS_OK;
 }
@@ -413,7 +499,7 @@ int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
   BKS_TRY((pack<T, IT>(X, ldx, t->m, p, PB, Xp, s)));
   if (!X2)
     return dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
-                       Xp.as<T>(), PB, Xp.as<T>(), PB, true, p, p, out, ldo, s);
+                       Xp.as<T>(), PB, Xp.as<T>(), PB, t->m, true, p, p, out, ldo, s);
   const int qchunk = PB == 8 ? 4 : 8;
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
@@ -421,8 +507,8 @@ int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
     DevBuf X2p;
     BKS_TRY((pack<T, IT>(X2 + ldx2 * q0, ldx2, t->m, qq, QB, X2p, s)));
     BKS_TRY((dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
-                        Xp.as<T>(), PB, X2p.as<T>(), QB, false, p, qq, out + ldo * (p * q0), ldo,
-                        s)));
+                        Xp.as<T>(), PB, X2p.as<T>(), QB, t->m, false, p, qq,
+                        out + ldo * (p * q0), ldo, s)));
   }
   return BKS_OK;
 }
@@ -847,15 +933,19 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 template <typename T, typename OT, int PB, int QB, bool TRI>
 int launch_contract_fixed(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib,
-                          const T* Ap, const T* Bp, int p, int q, OT* out, int64_t ldo,
-                          T* partial, cudaStream_t s) {
-  TileArgs ta{P.tile_first.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
-              P.vslot.as<int32_t>(), P.ntiles, ia, ib};
+                          const T* Ap, const T* Bp, int64_t brows, int p, int q, OT* out,
+                          int64_t ldo, T* partial, cudaStream_t s) {
+  constexpr int NB = TRI ? PB : QB;
+  const int bstage = (brows * NB * (int64_t)sizeof(T) <= 16384) ? (int)brows : 0;
+  const size_t bsm = (size_t)bstage * NB * sizeof(T);
+  TileArgs ta{P.vorder.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
+              P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib};
   const int warps = kWarpsPerBlock;
-  const int blocks = (P.ntiles + warps - 1) / warps;
+  const int blocks = (plan_warps(P) + warps - 1) / warps;
   if (P.nv > 0) {
-    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,
-                                                                 Bp, p, q, out, ldo, partial); ::bks::note_launch();
+    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, bsm, s>>>(ta, values_of<T>(P, vdtype), Ap,
+                                                                   Bp, bstage, p, q, out, ldo,
+                                                                   partial); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (P.nsplit > 0) {
@@ -874,14 +964,14 @@ int launch_contract_fixed(const Part& P, int vdtype, const int32_t* ia, const in
 }
 
 template <typename T>
-int dispatch_fixed(const Part& P, int vdtype, const T* Ap, int PB, const T* Bp, int QB, int p,
-                   int q, T* out, int64_t ldo, T* partial, cudaStream_t s) {
+int dispatch_fixed(const Part& P, int vdtype, const T* Ap, int PB, const T* Bp, int QB,
+                   int64_t brows, int p, int q, T* out, int64_t ldo, T* partial, cudaStream_t s) {
   const int32_t* ia = P.c1.as<int32_t>();
   const int32_t* ib = P.c0.as<int32_t>();
 #define BKS_FIXED_CASE(pb, qb)                                                               \
   if (PB == pb && QB == qb)                                                                  \
-    return launch_contract_fixed<T, T, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, out, \
-                                                      ldo, partial, s);
+    return launch_contract_fixed<T, T, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, brows, p, q, \
+                                                      out, ldo, partial, s);
   BKS_FIXED_CASE(2, 2) BKS_FIXED_CASE(2, 4) BKS_FIXED_CASE(2, 8) BKS_FIXED_CASE(4, 2)
   BKS_FIXED_CASE(4, 4) BKS_FIXED_CASE(4, 8) BKS_FIXED_CASE(8, 2) BKS_FIXED_CASE(8, 4)
 #undef BKS_FIXED_CASE
@@ -918,8 +1008,8 @@ int mode1_noalloc_typed(const bks_tensor* t, const T* X, int64_t ldx, int p, con
     // stream order: the previous chunk's kernels finish reading Yp first
     k_pack<T, T><<<grid_for(t->n), 256, 0, s>>>(Y + ldy * q0, ldy, t->n, qq, QB, Yp); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
-    BKS_TRY(dispatch_fixed<T>(P, t->vdtype, Xp, PB, Yp, QB, p, qq, out + ldo * (p * q0), ldo,
-                              partial, s));
+    BKS_TRY(dispatch_fixed<T>(P, t->vdtype, Xp, PB, Yp, QB, t->n, p, qq, out + ldo * (p * q0),
+                              ldo, partial, s));
   }
   return BKS_OK;
 }

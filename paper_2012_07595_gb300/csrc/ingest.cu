@@ -220,19 +220,37 @@ __global__ void k_vfill(const int32_t* ptr, int64_t rows, int split, const int32
     }
   }
 }
-__global__ void k_tile_first(const int32_t* vptr, int32_t nv, int32_t ntiles, int tile,
-                             int32_t* tf) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntiles;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    if (t == ntiles) { tf[t] = nv; continue; }
-    int64_t target = t * (int64_t)tile;
-    int32_t lo = 0, hi = nv;
-    while (lo < hi) {
-      int32_t mid = (lo + hi) >> 1;
-      if ((int64_t)vptr[mid] < target) lo = mid + 1; else hi = mid;
-    }
-    tf[t] = lo;
+
+// Work classes of the virtual rows: length > tile -> one warp each
+// (isvec), else one lane each; the short ones get the sort key tile - len so
+// that a stable sort orders them by decreasing length.
+__global__ void k_vclass(const int32_t* vptr, int32_t nv, int tile, int32_t* isvec,
+                         int32_t* isshort) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t len = vptr[v + 1] - vptr[v];
+    isvec[v] = len > tile ? 1 : 0;
+    isshort[v] = len > tile ? 0 : 1;
   }
+}
+__global__ void k_vsplit_lists(const int32_t* vptr, int32_t nv, int tile, const int32_t* isvec,
+                               const int32_t* vecpos, const int32_t* shortpos, int32_t* vorder,
+                               uint64_t* skeys, uint32_t* svals) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (isvec[v]) {
+      vorder[vecpos[v]] = (int32_t)v;
+    } else {
+      const int32_t len = vptr[v + 1] - vptr[v];
+      skeys[shortpos[v]] = (uint64_t)(tile - len);
+      svals[shortpos[v]] = (uint32_t)v;
+    }
+  }
+}
+__global__ void k_copy_u32(const uint32_t* in, int64_t n, int32_t* out) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x)
+    out[x] = (int32_t)in[x];
 }
 
 __global__ void k_expand_rows(const int32_t* ptr, int64_t rows, int32_t* out) {
@@ -434,13 +452,11 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
   BKS_TRY(P.empty_rows.alloc(sizeof(int32_t) * std::max(P.nempty, 1), s));
   k_empty_list<<<grid_for(R), 256, 0, s>>>(isempty.as<int32_t>(), emptypos.as<int32_t>(), R,
                                            P.empty_rows.as<int32_t>()); ::bks::note_launch();
-  P.ntiles = (int32_t)(nnz / P.tile + 1);
   BKS_TRY(P.vptr.alloc(sizeof(int32_t) * (P.nv + 1), s));
   BKS_TRY(P.vrow.alloc(sizeof(int32_t) * std::max(P.nv, 1), s));
   BKS_TRY(P.vslot.alloc(sizeof(int32_t) * std::max(P.nv, 1), s));
   BKS_TRY(P.split_row.alloc(sizeof(int32_t) * std::max(P.nsplit, 1), s));
   BKS_TRY(P.split_first.alloc(sizeof(int32_t) * (P.nsplit + 1), s));
-  BKS_TRY(P.tile_first.alloc(sizeof(int32_t) * (P.ntiles + 1), s));
   k_vfill<<<grid_for(R), 256, 0, s>>>(P.ptr.as<int32_t>(), R, P.split, vbase.as<int32_t>(),
                                       nvr.as<int32_t>(), slotbase.as<int32_t>(),
                                       splitpos.as<int32_t>(), P.vptr.as<int32_t>(),
@@ -453,9 +469,43 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
   int32_t ns = P.nslots;
   BKS_CUDA_TRY(cudaMemcpyAsync(P.split_first.as<int32_t>() + P.nsplit, &ns, sizeof(int32_t),
                                cudaMemcpyHostToDevice, s));
-  k_tile_first<<<grid_for(P.ntiles + 1), 256, 0, s>>>(P.vptr.as<int32_t>(), P.nv, P.ntiles,
-                                                      P.tile, P.tile_first.as<int32_t>()); ::bks::note_launch();
-  BKS_CUDA_TRY(cudaGetLastError());
+  // classes and the processing order of the virtual rows
+  if (P.nv > 0) {
+    DevBuf isvec, isshort, vecpos, shortpos, skeys, svals, tot2;
+    BKS_TRY(isvec.alloc(sizeof(int32_t) * P.nv, s));
+    BKS_TRY(isshort.alloc(sizeof(int32_t) * P.nv, s));
+    BKS_TRY(vecpos.alloc(sizeof(int32_t) * P.nv, s));
+    BKS_TRY(shortpos.alloc(sizeof(int32_t) * P.nv, s));
+    BKS_TRY(tot2.alloc(sizeof(int32_t) * 2, s));
+    k_vclass<<<grid_for(P.nv), 256, 0, s>>>(P.vptr.as<int32_t>(), P.nv, P.tile,
+                                            isvec.as<int32_t>(), isshort.as<int32_t>()); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+    BKS_TRY(exclusive_scan_i32(isvec.as<int32_t>(), vecpos.as<int32_t>(), P.nv, tot2.as<int32_t>(), s));
+    BKS_TRY(exclusive_scan_i32(isshort.as<int32_t>(), shortpos.as<int32_t>(), P.nv,
+                               tot2.as<int32_t>() + 1, s));
+    int32_t h2[2];
+    BKS_CUDA_TRY(cudaMemcpyAsync(h2, tot2.p, sizeof(h2), cudaMemcpyDeviceToHost, s));
+    BKS_CUDA_TRY(cudaStreamSynchronize(s));
+    P.nvec = h2[0];
+    P.nshortv = h2[1];
+    BKS_TRY(P.vorder.alloc(sizeof(int32_t) * P.nv, s));
+    BKS_TRY(skeys.alloc(sizeof(uint64_t) * std::max(P.nshortv, 1), s));
+    BKS_TRY(svals.alloc(sizeof(uint32_t) * std::max(P.nshortv, 1), s));
+    k_vsplit_lists<<<grid_for(P.nv), 256, 0, s>>>(P.vptr.as<int32_t>(), P.nv, P.tile,
+                                                  isvec.as<int32_t>(), vecpos.as<int32_t>(),
+                                                  shortpos.as<int32_t>(), P.vorder.as<int32_t>(),
+                                                  skeys.as<uint64_t>(), svals.as<uint32_t>()); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+    if (P.nshortv > 0) {
+      BKS_TRY(radix_sort_pairs(skeys.as<uint64_t>(), svals.as<uint32_t>(), P.nshortv,
+                               bits_for(P.tile + 1), s));
+      k_copy_u32<<<grid_for(P.nshortv), 256, 0, s>>>(svals.as<uint32_t>(), P.nshortv,
+                                                      P.vorder.as<int32_t>() + P.nvec); ::bks::note_launch();
+      BKS_CUDA_TRY(cudaGetLastError());
+    }
+  } else {
+    P.nvec = P.nshortv = 0;
+  }
   BKS_CUDA_TRY(cudaStreamSynchronize(s));  // host copies above read stack values
   P.persist();
   return BKS_OK;

@@ -1,8 +1,9 @@
 // Autotuner of the contraction work tiles: for a stored tensor, time the
 // mode-1 and triangle mode-3 contractions (FP32, widths 4 x 4) under a few
 // (tile, split) plans and keep the fastest.  Power-law tensors differ in how
-// their entries spread over rows, and the best cut between "short rows share
-// a warp" and "long rows are split into pieces" depends on that spread.
+// their entries spread over rows, and the best cuts between "rows on one
+// lane", "rows on one warp" and "rows split into pieces" depend on that
+// spread.
 #include <algorithm>
 #include <vector>
 
@@ -23,7 +24,7 @@ int rebuild(bks_tensor* t, int tile, int split, cudaStream_t s) {
 }  // namespace
 
 int autotune_tensor(bks_tensor* t, cudaStream_t s, int* tile_out, int* split_out) {
-  static const int cand[][2] = {{128, 128}, {256, 256}, {512, 512}, {256, 512}};
+  static const int cand[][2] = {{8, 512}, {32, 512}, {16, 1024}, {16, 512}};
   const int p = 4;
   DevBuf X, Y, out;
   BKS_TRY(X.alloc(sizeof(float) * (size_t)t->m * p, s));
@@ -67,8 +68,8 @@ int autotune_tensor(bks_tensor* t, cudaStream_t s, int* tile_out, int* split_out
 }
 
 int set_tiles(bks_tensor* t, int tile, int split, cudaStream_t s) {
-  if (tile < 32 || split < 32 || tile > kMaxTile || split > kMaxSplit)
-    return fail(BKS_EINVAL, "tile and split must be in [32, 512]");
+  if (tile < 1 || split < kMinSplit || tile > kMaxTile || split > kMaxSplit)
+    return fail(BKS_EINVAL, "tile must be in [1, 64] and split in [128, 4096]");
   if (t->m1.tile == tile && t->m1.split == split) return BKS_OK;
   BKS_TRY(rebuild(t, tile, split, s));
   BKS_CUDA_TRY(cudaStreamSynchronize(s));

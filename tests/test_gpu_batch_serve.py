@@ -60,10 +60,12 @@ def test_autotune_keeps_results():
     Y = torch.tensor(g.standard_normal((c.n, 3)), device="cuda")
     before = bk.bks_contract_mode1(T, X, Y).cpu().numpy()
     tile, split = bk.bks_tensor_autotune(T)
-    assert tile in (128, 256, 512) and split in (128, 256, 512)
+    assert (tile, split) in {(8, 512), (32, 512), (16, 1024), (16, 512)}
     after = bk.bks_contract_mode1(T, X, Y).cpu().numpy()
     assert np.abs(after - before).max() <= 1e-12 * max(1.0, np.abs(before).max())
-    for tl, sp in [(32, 32), (128, 512), (512, 128)]:
+    # every row on a warp; long rows cut into many pieces; all but the
+    # longest rows on single lanes
+    for tl, sp in [(1, 128), (16, 128), (64, 4096)]:
         bk.bks_tensor_set_tiles(T, tl, sp)
         got = bk.bks_contract_mode1(T, X, Y).cpu().numpy()
         assert np.abs(got - before).max() <= 1e-12 * max(1.0, np.abs(before).max())
@@ -73,6 +75,8 @@ def test_autotune_keeps_results():
         assert np.abs(tri - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
     with pytest.raises(bk.BksError):
         bk.bks_tensor_set_tiles(T, 8, 8)
+    with pytest.raises(bk.BksError):
+        bk.bks_tensor_set_tiles(T, 65, 1024)
 
 
 def test_batch_matches_solo():
