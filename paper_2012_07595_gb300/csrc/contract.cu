@@ -93,24 +93,6 @@ struct TileArgs {
   const int32_t* ib;   // index into operand B per entry
 };
 
-// Row load from global or shared memory (the B operand may be staged in
-// shared memory), 16 bytes at a time when the row size allows.
-template <typename T, int N>
-__device__ __forceinline__ void load_row_any(const T* base, T (&x)[N]) {
-  if constexpr (sizeof(T) * N % 16 == 0) {
-#pragma unroll
-    for (int t = 0; t < (int)(sizeof(T) * N / 16); ++t) {
-      const float4 q = reinterpret_cast<const float4*>(base)[t];
-      const T* qq = reinterpret_cast<const T*>(&q);
-#pragma unroll
-      for (int u = 0; u < (int)(16 / sizeof(T)); ++u) x[t * (16 / sizeof(T)) + u] = qq[u];
-    }
-  } else {
-#pragma unroll
-    for (int t = 0; t < N; ++t) x[t] = base[t];
-  }
-}
-
 // One entry's products into acc: v * A[ia,:]^T B[ib,:].
 template <typename T, int PB, int QB, bool TRI>
 __device__ __forceinline__ void one_entry(int e, const TileArgs& ta, const T* __restrict__ vals,
@@ -122,7 +104,7 @@ __device__ __forceinline__ void one_entry(int e, const TileArgs& ta, const T* __
   const T v = __ldg(vals + e);
   T xa[PB], xb[NB];
   load_row<T, PB>(Ap + (int64_t)ia * PB, xa);
-  load_row_any<T, NB>(Bp + (int64_t)ib * NB, xb);
+  load_row<T, NB>(Bp + (int64_t)ib * NB, xb);
   accumulate<T, PB, QB, TRI>(acc, v, xa, xb);
 }
 
@@ -256,20 +238,10 @@ __device__ __forceinline__ void warp_reduce_flush(int vr, const TileArgs& ta,
 template <typename T, typename OT, int PB, int QB, bool TRI>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
-           const T* Bp, int bstage, int p, int q, OT* __restrict__ out, int64_t ldo,
+           const T* __restrict__ Bp, int p, int q, OT* __restrict__ out, int64_t ldo,
            T* __restrict__ partial) {
   constexpr int W = Shape<PB, QB, TRI>::W;
   constexpr int NB = TRI ? PB : QB;
-  // a small B operand (bstage > 0 rows, e.g. the n x q block of the mode-1
-  // contraction) is copied to shared memory once per block: its gathers
-  // then cost no L1 tag lookups
-  extern __shared__ __align__(16) unsigned char bsm_raw[];
-  if (bstage > 0) {
-    T* bs = reinterpret_cast<T*>(bsm_raw);
-    for (int x = threadIdx.x; x < bstage * NB; x += blockDim.x) bs[x] = Bp[x];
-    __syncthreads();
-    Bp = bs;
-  }
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   T acc[W];
@@ -296,7 +268,7 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         load_row<T, PB>(Ap + (int64_t)iav[u] * PB, xa[u]);
-        load_row_any<T, NB>(Bp + (int64_t)ibv[u] * NB, xb[u]);
+        load_row<T, NB>(Bp + (int64_t)ibv[u] * NB, xb[u]);
       }
       T vc[4] = {v[0], v[1], v[2], v[3]};
       x += 128;
@@ -333,7 +305,7 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       load_row<T, PB>(Ap + (int64_t)iav[u] * PB, xa[u]);
-      load_row_any<T, NB>(Bp + (int64_t)ibv[u] * NB, xb[u]);
+      load_row<T, NB>(Bp + (int64_t)ibv[u] * NB, xb[u]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, v[u], xa[u], xb[u]);
@@ -409,13 +381,9 @@ template <> const double* values_of<double>(const Part& P, int vdtype) {
 // One launch pair (tile kernel + piece reduction) for fixed buckets.
 template <typename T, typename OT, int PB, int QB, bool TRI>
 int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib,
-                    const T* Ap, const T* Bp, int64_t brows, int p, int q, OT* out, int64_t ldo,
+                    const T* Ap, const T* Bp, int p, int q, OT* out, int64_t ldo,
                     cudaStream_t s) {
   constexpr int W = Shape<PB, QB, TRI>::W;
-  constexpr int NB = TRI ? PB : QB;
-  // B operands of at most 16 KB are staged in shared memory
-  const int bstage = (brows * NB * (int64_t)sizeof(T) <= 16384) ? (int)brows : 0;
-  const size_t bsm = (size_t)bstage * NB * sizeof(T);
   TileArgs ta{P.vorder.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
               P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib};
   DevBuf partial;
@@ -423,9 +391,9 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
   const int warps = kWarpsPerBlock;
   const int blocks = (plan_warps(P) + warps - 1) / warps;
   if (P.nv > 0) {
-    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, bsm, s>>>(ta, values_of<T>(P, vdtype), Ap,
-                                                                   Bp, bstage, p, q, out, ldo,
-                                                                   partial.as<T>()); ::bks::note_launch();
+    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,
+                                                                 Bp, p, q, out, ldo,
+                                                                 partial.as<T>()); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (P.nsplit > 0) {
@@ -445,20 +413,20 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
 
 template <typename T, typename OT>
 int dispatch(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib, const T* Ap,
-             int PB, const T* Bp, int QB, int64_t brows, bool tri, int p, int q, OT* out,
+             int PB, const T* Bp, int QB, bool tri, int p, int q, OT* out,
              int64_t ldo, cudaStream_t s) {
 #define BKS_CASE(pb, qb)                                                                      \
   if (!tri && PB == pb && QB == qb)                                                           \
-    return launch_contract<T, OT, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, brows, p, q, out, ldo, s);
+    return launch_contract<T, OT, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, out, ldo, s);
   BKS_CASE(2, 2) BKS_CASE(2, 4) BKS_CASE(2, 8) BKS_CASE(4, 2) BKS_CASE(4, 4) BKS_CASE(4, 8)
   BKS_CASE(8, 2) BKS_CASE(8, 4)
 #undef BKS_CASE
   if (tri && PB == 2)
-    return launch_contract<T, OT, 2, 2, true>(P, vdtype, ia, ib, Ap, Bp, brows, p, p, out, ldo, s);
+    return launch_contract<T, OT, 2, 2, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
   if (tri && PB == 4)
-    return launch_contract<T, OT, 4, 4, true>(P, vdtype, ia, ib, Ap, Bp, brows, p, p, out, ldo, s);
+    return launch_contract<T, OT, 4, 4, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
   if (tri && PB == 8)
-    return launch_contract<T, OT, 8, 8, true>(P, vdtype, ia, ib, Ap, Bp, brows, p, p, out, ldo, s);
+    return launch_contract<T, OT, 8, 8, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
   return fail(BKS_EUNSUPPORTED, "contraction bucket not instantiated");
 }
 
@@ -485,7 +453,7 @@ int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
     BKS_TRY((pack<T, IT>(Y + ldy * q0, ldy, t->n, qq, QB, Yp, s)));
     // columns a + p*(q0 + b) of the full output start at column p*q0
     BKS_TRY((dispatch<T, OT>(t->m1, t->vdtype, t->m1.c1.as<int32_t>(), t->m1.c0.as<int32_t>(),
-                        Xp.as<T>(), PB, Yp.as<T>(), QB, t->n, false, p, qq,
+                        Xp.as<T>(), PB, Yp.as<T>(), QB, false, p, qq,
                         out + ldo * (p * q0), ldo, s)));
   }
   return BKS_OK;
@@ -499,7 +467,7 @@ int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
   BKS_TRY((pack<T, IT>(X, ldx, t->m, p, PB, Xp, s)));
   if (!X2)
     return dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
-                       Xp.as<T>(), PB, Xp.as<T>(), PB, t->m, true, p, p, out, ldo, s);
+                       Xp.as<T>(), PB, Xp.as<T>(), PB, true, p, p, out, ldo, s);
   const int qchunk = PB == 8 ? 4 : 8;
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
@@ -507,7 +475,7 @@ int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
     DevBuf X2p;
     BKS_TRY((pack<T, IT>(X2 + ldx2 * q0, ldx2, t->m, qq, QB, X2p, s)));
     BKS_TRY((dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
-                        Xp.as<T>(), PB, X2p.as<T>(), QB, t->m, false, p, qq,
+                        Xp.as<T>(), PB, X2p.as<T>(), QB, false, p, qq,
                         out + ldo * (p * q0), ldo, s)));
   }
   return BKS_OK;
@@ -933,19 +901,16 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 template <typename T, typename OT, int PB, int QB, bool TRI>
 int launch_contract_fixed(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib,
-                          const T* Ap, const T* Bp, int64_t brows, int p, int q, OT* out,
+                          const T* Ap, const T* Bp, int p, int q, OT* out,
                           int64_t ldo, T* partial, cudaStream_t s) {
-  constexpr int NB = TRI ? PB : QB;
-  const int bstage = (brows * NB * (int64_t)sizeof(T) <= 16384) ? (int)brows : 0;
-  const size_t bsm = (size_t)bstage * NB * sizeof(T);
   TileArgs ta{P.vorder.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
               P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib};
   const int warps = kWarpsPerBlock;
   const int blocks = (plan_warps(P) + warps - 1) / warps;
   if (P.nv > 0) {
-    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, bsm, s>>>(ta, values_of<T>(P, vdtype), Ap,
-                                                                   Bp, bstage, p, q, out, ldo,
-                                                                   partial); ::bks::note_launch();
+    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,
+                                                                 Bp, p, q, out, ldo,
+                                                                 partial); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (P.nsplit > 0) {
@@ -965,12 +930,12 @@ int launch_contract_fixed(const Part& P, int vdtype, const int32_t* ia, const in
 
 template <typename T>
 int dispatch_fixed(const Part& P, int vdtype, const T* Ap, int PB, const T* Bp, int QB,
-                   int64_t brows, int p, int q, T* out, int64_t ldo, T* partial, cudaStream_t s) {
+                   int p, int q, T* out, int64_t ldo, T* partial, cudaStream_t s) {
   const int32_t* ia = P.c1.as<int32_t>();
   const int32_t* ib = P.c0.as<int32_t>();
 #define BKS_FIXED_CASE(pb, qb)                                                               \
   if (PB == pb && QB == qb)                                                                  \
-    return launch_contract_fixed<T, T, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, brows, p, q, \
+    return launch_contract_fixed<T, T, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, \
                                                       out, ldo, partial, s);
   BKS_FIXED_CASE(2, 2) BKS_FIXED_CASE(2, 4) BKS_FIXED_CASE(2, 8) BKS_FIXED_CASE(4, 2)
   BKS_FIXED_CASE(4, 4) BKS_FIXED_CASE(4, 8) BKS_FIXED_CASE(8, 2) BKS_FIXED_CASE(8, 4)
@@ -1008,7 +973,7 @@ int mode1_noalloc_typed(const bks_tensor* t, const T* X, int64_t ldx, int p, con
     // stream order: the previous chunk's kernels finish reading Yp first
     k_pack<T, T><<<grid_for(t->n), 256, 0, s>>>(Y + ldy * q0, ldy, t->n, qq, QB, Yp); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
-    BKS_TRY(dispatch_fixed<T>(P, t->vdtype, Xp, PB, Yp, QB, t->n, p, qq, out + ldo * (p * q0),
+    BKS_TRY(dispatch_fixed<T>(P, t->vdtype, Xp, PB, Yp, QB, p, qq, out + ldo * (p * q0),
                               ldo, partial, s));
   }
   return BKS_OK;
