@@ -176,14 +176,20 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# DRAM bytes (read + write) of k_contract<float,float,4,4,0> in one ncu
+# capture of the 500,000 x 500,000 x 200 case (`--ncu-case mode1 --size mid`)
+MID_TRAFFIC_BYTES = 203_607_808 + 34_899_712
+MID_NNZ = 11_777_770
 LARGE = {"m": 1_000_000, "n": 200, "draws": 60_000_000, "zipf_s": 1.2, "seed": 3, "r": 5}
 
 
 def large_roofline(bk, torch, stream, flush, hbm, peak_kind):
     """The contraction roofline case: the mode-1 contraction on the
     1e6 x 1e6 x 200 Zipf(1.2) tensor (FP32 values, mirrored, duplicates
-    summed), with the stage-2 block shape of a rank-5 BK(2,4) solve: X has
-    5 columns, Y 4 (output 20 columns).  One timed call = pack of X and Y,
+    summed), with the 4 x 4 block shape of BK(2,4) (X and Y 4 columns,
+    output 16).  `traffic`: DRAM bytes of k_contract measured by ncu on the
+    500,000 x 500,000 x 200 case (11,777,770 stored, same kernel and plan),
+    scaled to this launch by stored entries.  One timed call = pack of X and Y,
     the contraction kernel, the piece reduction of long rows and the zero
     rows; algorithmic bytes = index and value streams + row pointers + X and
     Y read once + output written once (gathers served by L2 not counted)."""
@@ -192,7 +198,7 @@ def large_roofline(bk, torch, stream, flush, hbm, peak_kind):
                             values="absnormal", vdtype=np.float32)
     T = bk.bks_tensor_create_coo(coo.m, coo.n, coo.i, coo.j, coo.k, coo.v)
     del coo
-    m, n, p, q = L["m"], L["n"], L["r"], 4
+    m, n, p, q = L["m"], L["n"], 4, 4
     g = synth.rng(11)
     X = torch.tensor(g.standard_normal((m, p)), device="cuda", dtype=torch.float32)
     Y = torch.tensor(g.standard_normal((n, q)), device="cuda", dtype=torch.float32)
@@ -214,12 +220,15 @@ def large_roofline(bk, torch, stream, flush, hbm, peak_kind):
     alg = nnz * (4 + 4 + 4) + (m + 1) * 4 + m * p * 4 + n * q * 4 + m * p * q * 4
     ach = alg / kt / 1e9
     T.close()
-    return {"kernel": "bks_contract_mode1 FP32 (pack + k_contract<float,float,8,4> + piece "
+    traffic = int(MID_TRAFFIC_BYTES * nnz / MID_NNZ)
+    return {"kernel": "bks_contract_mode1 FP32 (pack + k_contract<float,float,4,4> + piece "
                       "reduction + zero rows)",
             "workload": f"zipf1.2 (1,2)-symmetric 1e6 x 1e6 x 200, {nnz} stored "
-                        f"({L['draws']} draws mirrored, duplicates summed), X 5 cols, Y 4 cols",
+                        f"({L['draws']} draws mirrored, duplicates summed), X 4 cols, Y 4 cols",
             "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "peak_kind": peak_kind, "traffic": None, "alg_bytes_per_launch": alg,
+            "peak_kind": peak_kind, "traffic": traffic,
+            "traffic_note": "ncu dram bytes of k_contract on the 11.8M-entry case, scaled by "
+                            "stored entries", "alg_bytes_per_launch": alg,
             "median_launch_s": kt, "nnz_stored": nnz}
 
 
