@@ -90,6 +90,32 @@ def test_small_planted_workload_parity(seed):
     assert all(b >= a * (1 - 1e-12) for a, b in zip(norms, norms[1:]))
 
 
+@pytest.mark.parametrize("variant,s,p", [("min", 3, 2), ("max", 2, 2), ("bk", 3, 2)])
+def test_schedule_variants_parity(variant, s, p):
+    """min-BK (Algorithm 4, Table 1), max-BK (Table 2) and a 3-stage BK on
+    the 300x300x100 planted workload, FP64, tol 1e-10: same start on both
+    sides; same basis sizes, ||F|| within 1e-10 relative, subspaces within
+    1e-8."""
+    bk = _bk()
+    coo, _ = synth.small_planted(1)
+    A = O.symmetrise(coo.m, coo.n, coo.i, coo.j, coo.k, coo.v)
+    T = bk.bks_tensor_create_coo(coo.m, coo.n, coo.i, coo.j, coo.k, coo.v)
+    g = synth.rng(103)
+    U0 = synth.orthonormal(g, A.m, 2); W0 = synth.orthonormal(g, A.n, 2)
+    ro = O.bks(A, U0, W0, s=s, p=p, tol=1e-10, variant=variant)
+    code = {"bk": bk.BKS_VARIANT_BK, "min": bk.BKS_VARIANT_MIN, "max": bk.BKS_VARIANT_MAX}[variant]
+    U, W, F, info = bk.bks_solve(T, bk.BksParams(r1=2, r3=2, stages=s, block_p=p, tol=1e-10,
+                                                 variant=code), _t(U0), _t(W0))
+    assert ro.converged and info["converged"]
+    # basis sizes of the last expansion: the schedule's counts less the
+    # columns dropped as dependent (max-BK drops some near convergence)
+    want = O.schedule_counts(2, 2, s, p, variant, m=A.m, n=A.n)[-1]
+    assert 2 < info["k1"] <= want[0] and 2 < info["k3"] <= want[1]
+    assert abs(info["normF"] - ro.normF) <= 1e-10 * ro.normF
+    assert O.sin_theta_max(ro.U, U.cpu().numpy()) < 1e-8
+    assert O.sin_theta_max(ro.W, W.cpu().numpy()) < 1e-8
+
+
 @pytest.mark.parametrize("rho", [1e-2, 1e-3])
 def test_example1_bks_hooi_agree_with_oracle(rho):
     bk = _bk()
