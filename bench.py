@@ -38,7 +38,7 @@ WORKLOAD = {
     "workload": "zipf1.1 (1,2)-symmetric 100000x100000x50, ~5.0M stored (4.055M draws, "
                 "mirrored, duplicates summed), rank (3,3,3), BK(s=2,p=4) -> (k1,k3)=(36,21)",
     "m": 100_000, "n": 50, "draws": 4_055_000, "zipf_s": 1.1, "seed": 2,
-    "r": 3, "stages": 2, "block_p": 4, "tol": 1e-9, "mixed_tol": 1e-6, "tol_scale_free": 1,
+    "r": 3, "stages": 2, "block_p": 4, "tol": 1e-9, "mixed_tol": 1e-4, "tol_scale_free": 1,
 }
 # The stopping test of both forms is the scale-free ||grad|| / ||F||^2 <= 1e-9
 # (the paper's ||grad|| / ||F|| grows with the scale of A: ||F|| ~ 5e4 here);
@@ -294,7 +294,7 @@ def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
 
     def prm(r, prec):
         return bk.BksParams(r1=r, r3=r, stages=2, block_p=4, tol=1e-9, tol_scale_free=1,
-                            precision=prec, mixed_tol=1e-6, refine_sweeps=50, max_outer=200,
+                            precision=prec, mixed_tol=1e-4, refine_sweeps=50, max_outer=200,
                             max_inner=100)
 
     tens = [bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v) for c in coos]

@@ -172,7 +172,8 @@ typedef struct {
   int max_inner;       /* inner HOOI sweep cap per outer iteration */
   int variant;         /* BKS_VARIANT_* */
   int precision;       /* BKS_PREC_FP64 or BKS_PREC_MIXED */
-  int refine_sweeps;   /* MIXED only: FP64 outer iterations after the FP32 phase converged */
+  int refine_sweeps;   /* MIXED only: at most this many outer iterations in the refinement
+                          form after the FP32 phase */
   uint64_t seed;       /* random start when U0/W0 are NULL */
   double drop_tol;     /* rank-drop threshold of the block QR (relative) */
   double inner_tol;    /* inner stopping tolerance on ||grad_C|| / ||F_C|| (<= 0: inexact
@@ -182,8 +183,11 @@ typedef struct {
                           scale of A); 1: stop when ||grad|| / ||F||^2 <= tol (invariant
                           under A -> c A) */
   double mixed_tol;    /* MIXED only: the FP32 phase ends when ||grad|| / ||F||^2 <= mixed_tol
-                          (<= 0: 1e-6) or when that ratio stops halving for two outer
-                          iterations; FP64 outer iterations follow until tol */
+                          (<= 0: 1e-4) or when that ratio stops halving for two outer
+                          iterations; outer iterations in the refinement form follow until
+                          tol (FP64 stage-1 contractions, gradient and stopping test; FP32
+                          later Krylov blocks and core C with its first-order blocks
+                          replaced by FP64 projections of the stage-1 results) */
 } bks_params;
 
 typedef struct {
@@ -203,7 +207,7 @@ typedef struct {
 } bks_info;
 
 /* Default parameters: r1 = r3 = 2, s = 2, p = 4, tol 1e-10, max_outer 500,
- * max_inner 1000, BK, FP64, refine 1, seed 1, drop_tol 1e-14 (a rank-drop threshold
+ * max_inner 1000, BK, FP64, refine 1, seed 1, mixed_tol 1e-4, drop_tol 1e-14 (a rank-drop threshold
  * well below the gradient accuracy: near convergence the stage-1 residual
  * columns that carry the gradient are small relative to their raw norms). */
 void bks_params_default(bks_params* p);

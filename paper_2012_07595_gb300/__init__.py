@@ -362,7 +362,7 @@ class BksParams:
     drop_tol: float = 1e-14
     inner_tol: float = 0.0
     tol_scale_free: int = 0
-    mixed_tol: float = 1e-6
+    mixed_tol: float = 1e-4
 
     def to_c(self) -> _Params:
         p = _Params()

@@ -414,7 +414,7 @@ extern "C" void bks_params_default(bks_params* p) {
   p->seed = 1;
   p->drop_tol = 1e-14;
   p->inner_tol = 0.0;
-  p->mixed_tol = 1e-6;
+  p->mixed_tol = 1e-4;
 }
 
 extern "C" void hooi_params_default(hooi_params* p) {
@@ -458,7 +458,7 @@ int bks::solve_impl(const bks_tensor* t, const bks_params* prm, const double* U0
   else BKS_TRY(random_orthonormal(prm->seed, 3, n, r3, S.Zp(), S.ws, s));
 
   const bool mixed = prm->precision == BKS_PREC_MIXED;
-  const double mtol = prm->mixed_tol > 0 ? prm->mixed_tol : 1e-6;
+  const double mtol = prm->mixed_tol > 0 ? prm->mixed_tol : 1e-4;
   bool fp32 = mixed;
   int it = 0, fp32_iters = 0, refine_left = std::max(0, prm->refine_sweeps);
   double grad = 0, nf = 0;
