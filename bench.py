@@ -150,7 +150,7 @@ def run_reference(args):
     metric (BKS solves/s), each step a bounded sample (one outer iteration
     on a half-index row sample) extrapolated to a full solve."""
     coo = make_input()
-    outer_iters = 30  # outer iterations of a solve at this tolerance (GPU run: see its line)
+    outer_iters = 6  # outer iterations of an FP64 solve at this tolerance (the GPU FP64 solve's count)
     times = []
     for s in range(args.warmup + args.steps):
         d = cpu_oracle_sample(coo)
