@@ -125,7 +125,7 @@ struct Part {
 };
 
 // Chunks of the mode-3 copy for the large-rank cores: every slice k is cut
-// into pieces of about nnz / (4 SMs) entries; the chunks of a slice are
+// into pieces of about nnz / (16 SMs) entries; the chunks of a slice are
 // consecutive.  Built once per tensor at ingest.
 struct CorePlan {
   int32_t nch = 0, nsl = 0;

@@ -743,7 +743,9 @@ int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* 
 // Core chunk plan (see CorePlan): host loop over the slices of the mode-3
 // copy, uploaded once.
 int build_core_plan(const Part& m3, int64_t n, int64_t nnz, CorePlan& cp, cudaStream_t s) {
-  const int64_t target = std::max<int64_t>(256, nnz / (4LL * num_sms()) + 1);
+  // about 16 chunks per SM: several waves of blocks, so that uneven
+  // chunk times even out across the SMs
+  const int64_t target = std::max<int64_t>(256, nnz / (16LL * num_sms()) + 1);
   std::vector<int32_t> lo, hi, slk, slf;
   for (int64_t k = 0; k < n; ++k) {
     const int32_t a = m3.host_ptr[k], b = m3.host_ptr[k + 1];

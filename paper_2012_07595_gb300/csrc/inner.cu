@@ -86,8 +86,8 @@ k_hosvd(const float* __restrict__ part1, const float* __restrict__ part3, int np
       A[x] = s;
     }
     __syncthreads();
-    // a start only: eigenvectors to a relative threshold of 1e-4
-    block_jacobi_eig<float>(A, V, n, 1e-4f, 30, red, cs);
+    // a start only: a relative threshold of 1e-4 and at most 6 sweeps
+    block_jacobi_eig<float>(A, V, n, 1e-4f, 6, red, cs);
     top_diag<float>(A, n, r, idx);
     double* out = pass == 0 ? Uh : Wh;
     for (int x = threadIdx.x; x < n * r; x += blockDim.x) {
