@@ -195,56 +195,75 @@ __global__ void k_orth_r2(const double* __restrict__ G, int K, int b, double dro
   __shared__ double R[kMaxB * kMaxB];
   __shared__ int pos[kMaxB];
   __shared__ int dpos[kMaxB];
+  __shared__ double Sd[kMaxB];  // the projected diagonal before elimination
   for (int x = threadIdx.x; x < b * b; x += blockDim.x) {
     const int i = x % b, j = x / b;
     double s = G[K + i + gw * j];
     for (int e = 0; e < K; ++e) s -= G[e + gw * i] * G[e + gw * j];
     S[x] = s;
     R[x] = 0.0;
+    if (i == j) Sd[i] = s;
   }
   if (raw_in)
     for (int c = threadIdx.x; c < b; c += blockDim.x) sm[L.raw + c] = raw_in[c];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int nk = 0, nd = 0;
-    bool deferring = false;
-    for (int c = 0; c < b; ++c) {
-      if (deferring) {
-        dpos[nd++] = c;
-        sm[L.kept + c] = 2;
-        continue;
-      }
-      for (int t = 0; t < nk; ++t) {
-        const int kt = pos[t];
-        double v = S[kt + b * c];
-        for (int u = 0; u < t; ++u) v -= R[u + b * kt] * R[u + b * c];
-        R[t + b * c] = v / R[t + b * kt];
-      }
-      double d = S[c + b * c];
-      for (int t = 0; t < nk; ++t) d -= R[t + b * c] * R[t + b * c];
-      const double raw = sm[L.raw + c];
-      const double res = sqrt(fmax(d, 0.0));
-      const double proj = sqrt(fmax(S[c + b * c], 0.0));
-      // with no kept column before it at this level, d_c is the Gram
-      // diagonal itself and is always resolved (every level decides at
-      // least its first column)
-      const bool resolved = nk == 0 || res > 1e-3 * proj;
+  // Right-looking form of the left-to-right elimination: after column c is
+  // kept as the t-th column, every later column c' gets R[t, c'] (one
+  // division per column, in parallel) and the trailing Gram entries lose
+  // R[t, c'] R[t, c''], in the same order of t as a column-by-column
+  // substitution.  Thread 0 only takes the per-column decisions.
+  __shared__ int s_nk, s_nd, s_def, s_cls;
+  if (threadIdx.x == 0) { s_nk = 0; s_nd = 0; s_def = 0; }
+  __syncthreads();
+  for (int c = 0; c < b; ++c) {
+    if (threadIdx.x == 0) {
       int cls = 0;  // 0 drop, 1 keep, 2 defer
-      if (nk < cap && raw > 0.0) {
-        if (resolved) cls = res > drop_tol * raw ? 1 : 0;
-        else if (two_level) { cls = 2; deferring = true; }
+      if (s_def) {
+        cls = 2;
+      } else {
+        const int nk = s_nk;
+        const double d = S[c + b * c];  // the trailing diagonal: d_c
+        const double raw = sm[L.raw + c];
+        const double res = sqrt(fmax(d, 0.0));
+        const double proj = sqrt(fmax(Sd[c], 0.0));
+        // with no kept column before it at this level, d_c is the Gram
+        // diagonal itself and is always resolved (every level decides at
+        // least its first column)
+        const bool resolved = nk == 0 || res > 1e-3 * proj;
+        if (nk < cap && raw > 0.0) {
+          if (resolved) cls = res > drop_tol * raw ? 1 : 0;
+          else if (two_level) { cls = 2; s_def = 1; }
+        }
+        if (cls == 1) {
+          R[nk + b * c] = res;
+          pos[nk] = c;
+        }
       }
-      if (cls == 1) {
-        R[nk + b * c] = res;
-        pos[nk++] = c;
-      } else if (cls == 2) {
-        dpos[nd++] = c;
-      }
+      if (cls == 2) dpos[s_nd++] = c;
       sm[L.kept + c] = cls;
+      s_cls = cls;
     }
-    status[0] = nk;
-    status[2] = nd;
-    for (int t = 0; t < nd; ++t) status[8 + t] = dpos[t];
+    __syncthreads();
+    if (s_cls != 1) continue;
+    const int t = s_nk;
+    const double rcc = R[t + b * c];
+    for (int c2 = c + 1 + threadIdx.x; c2 < b; c2 += blockDim.x) R[t + b * c2] = S[c + b * c2] / rcc;
+    __syncthreads();
+    for (int x = threadIdx.x; x < b * b; x += blockDim.x) {
+      const int i = x % b, j = x / b;
+      if (i > c && j >= i) S[i + b * j] -= R[t + b * i] * R[t + b * j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_nk = t + 1;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // rows of R for deferred columns stay zero, as in the column form
+    for (int t = 0; t < s_nd; ++t)
+      for (int u = 0; u < s_nk; ++u) R[u + b * dpos[t]] = 0.0;
+    status[0] = s_nk;
+    status[2] = s_nd;
+    for (int t = 0; t < s_nd; ++t) status[8 + t] = dpos[t];
   }
   __syncthreads();
   const int nk = status[0], nd = status[2];
@@ -256,11 +275,14 @@ __global__ void k_orth_r2(const double* __restrict__ G, int K, int b, double dro
   }
   __syncthreads();
   double* Ri = sm + L.Rinv;  // nk x nk, ld b
+  __shared__ double dinv2[kMaxB];
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) dinv2[i] = 1.0 / R[i + b * pos[i]];
+  __syncthreads();
   for (int j = threadIdx.x; j < nk; j += blockDim.x) {
     for (int i = nk - 1; i >= 0; --i) {
       double v = (i == j) ? 1.0 : 0.0;
       for (int t = i + 1; t <= j; ++t) v -= R[i + b * pos[t]] * Ri[t + b * j];
-      Ri[i + b * j] = (i <= j) ? v / R[i + b * pos[i]] : 0.0;
+      Ri[i + b * j] = (i <= j) ? v * dinv2[i] : 0.0;
     }
   }
   __syncthreads();
@@ -339,27 +361,38 @@ __global__ void k_orth_r3(const double* __restrict__ G, int K, int b, double* __
     Ri[i + kMaxB * j] = v;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int j = 0; j < nk; ++j) {
-      for (int i = 0; i <= j; ++i) {
-        double v = Ri[i + kMaxB * j];
-        for (int t = 0; t < i; ++t) v -= R3[t + kMaxB * i] * R3[t + kMaxB * j];
-        if (i == j) {
-          if (!(v > 0.0)) { flags[0] = 1; v = 1e-300; }
-          R3[i + kMaxB * j] = sqrt(v);
-        } else {
-          R3[i + kMaxB * j] = v / R3[i + kMaxB * i];
-        }
-      }
-      for (int i = j + 1; i < nk; ++i) R3[i + kMaxB * j] = 0.0;
+  // right-looking Cholesky: one pivot per step, the row and the trailing
+  // update in parallel (the same order of subtraction as a column-by-column
+  // factorisation)
+  for (int c = 0; c < nk; ++c) {
+    if (threadIdx.x == 0) {
+      double v = Ri[c + kMaxB * c];
+      if (!(v > 0.0)) { flags[0] = 1; v = 1e-300; }
+      R3[c + kMaxB * c] = sqrt(v);
     }
+    __syncthreads();
+    const double rcc = R3[c + kMaxB * c];
+    for (int c2 = c + 1 + threadIdx.x; c2 < nk; c2 += blockDim.x)
+      R3[c + kMaxB * c2] = Ri[c + kMaxB * c2] / rcc;
+    __syncthreads();
+    for (int x = threadIdx.x; x < nk * nk; x += blockDim.x) {
+      const int i = x % nk, j = x / nk;
+      if (i > c && j >= i) Ri[i + kMaxB * j] -= R3[c + kMaxB * i] * R3[c + kMaxB * j];
+    }
+    __syncthreads();
   }
+  __shared__ double dinv3[kMaxB];
+  for (int x = threadIdx.x; x < nk * nk; x += blockDim.x) {
+    const int i = x % nk, j = x / nk;
+    if (i > j) R3[i + kMaxB * j] = 0.0;
+  }
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) dinv3[i] = 1.0 / R3[i + kMaxB * i];
   __syncthreads();
   for (int j = threadIdx.x; j < nk; j += blockDim.x) {
     for (int i = nk - 1; i >= 0; --i) {
       double v = (i == j) ? 1.0 : 0.0;
       for (int t = i + 1; t <= j; ++t) v -= R3[i + kMaxB * t] * Ri[t + kMaxB * j];
-      Ri[i + kMaxB * j] = (i <= j) ? v / R3[i + kMaxB * i] : 0.0;
+      Ri[i + kMaxB * j] = (i <= j) ? v * dinv3[i] : 0.0;
     }
   }
   __syncthreads();
