@@ -112,13 +112,14 @@ struct Part {
   DevBuf vrow;        // int32 [nv]     row of each virtual row
   DevBuf vslot;       // int32 [nv]     partial-sum slot, -1 if the row is not cut
   DevBuf vorder;      // int32 [nv]: the nvec warp rows, then the short rows by decreasing length
+  DevBuf vitems;      // int4 [nv]: per vorder position (first entry, end, row, slot)
   DevBuf split_row;   // int32 [nsplit]   rows that were cut
   DevBuf split_first; // int32 [nsplit+1] their first slot (slots are consecutive)
   int32_t nempty = 0;
   DevBuf empty_rows;  // int32 [nempty] rows without entries (their output is zero)
   std::vector<int32_t> host_ptr;  // host copy of ptr (kept for the mode-3 copy only)
   void persist() {
-    for (DevBuf* b : {&ptr, &c0, &c1, &v, &v32, &v64, &vptr, &vrow, &vslot, &vorder,
+    for (DevBuf* b : {&ptr, &c0, &c1, &v, &v32, &v64, &vptr, &vrow, &vslot, &vorder, &vitems,
                       &split_row, &split_first, &empty_rows})
       b->persist();
   }

@@ -84,6 +84,7 @@ __device__ __forceinline__ void accumulate(T (&acc)[Shape<PB, QB, TRI>::W], T v,
 }
 
 struct TileArgs {
+  const int4* items;      // per work item (vorder order): first entry, end, row, slot
   const int32_t* vorder;  // the nvec warp rows, then the short rows by decreasing length
   const int32_t* vptr;
   const int32_t* vrow;
@@ -121,19 +122,17 @@ __device__ __forceinline__ void load4(const T* __restrict__ p, T (&v)[4]) {
 }
 
 template <typename T, typename OT, int PB, int QB, bool TRI>
-__device__ __forceinline__ void flush_row(int vr, const TileArgs& ta,
+__device__ __forceinline__ void flush_row(int64_t row, int slot,
                                           const T (&acc)[Shape<PB, QB, TRI>::W], int p, int q,
                                           OT* __restrict__ out, int64_t ldo,
                                           T* __restrict__ partial) {
   constexpr int W = Shape<PB, QB, TRI>::W;
-  const int slot = __ldg(ta.vslot + vr);
   if (slot >= 0) {
     T* dst = partial + (int64_t)slot * W;
 #pragma unroll
     for (int c = 0; c < W; ++c) dst[c] = acc[c];
     return;
   }
-  const int64_t row = __ldg(ta.vrow + vr);
   if constexpr (TRI) {
 #pragma unroll
     for (int b = 0; b < PB; ++b)
@@ -176,7 +175,7 @@ __device__ __forceinline__ void halve(T* a, int lane, int o) {
 // Warp sum of acc[W] (five halving levels, a fixed order), written to the
 // virtual row's output row or partial slot by the lanes that hold each sum.
 template <typename T, typename OT, int PB, int QB, bool TRI>
-__device__ __forceinline__ void warp_reduce_flush(int vr, const TileArgs& ta,
+__device__ __forceinline__ void warp_reduce_flush(int64_t row, int slot,
                                                   const T (&acc)[Shape<PB, QB, TRI>::W], int p,
                                                   int q, OT* __restrict__ out, int64_t ldo,
                                                   T* __restrict__ partial, int lane) {
@@ -208,8 +207,6 @@ __device__ __forceinline__ void warp_reduce_flush(int vr, const TileArgs& ta,
   }
   if (!writer) return;
   constexpr int R = W2 / 32 > 1 ? W2 / 32 : 1;
-  const int slot = __ldg(ta.vslot + vr);
-  const int64_t row = __ldg(ta.vrow + vr);
 #pragma unroll
   for (int c = 0; c < R; ++c) {
     const int idx = base + c;
@@ -248,8 +245,8 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
 #pragma unroll
   for (int c = 0; c < W; ++c) acc[c] = T(0);
   if (gw < ta.nvec) {
-    const int vr = __ldg(ta.vorder + gw);
-    const int s = __ldg(ta.vptr + vr), e = __ldg(ta.vptr + vr + 1);
+    const int4 it = __ldg(ta.items + gw);
+    const int s = it.x, e = it.y;
     int x = s + lane;
     // software pipeline: the next group's indices and values are loaded
     // while the current group's gathers are in flight
@@ -284,13 +281,13 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
       for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, vc[u], xa[u], xb[u]);
     }
     for (; x < e; x += 32) one_entry<T, PB, QB, TRI>(x, ta, vals, Ap, Bp, acc);
-    warp_reduce_flush<T, OT, PB, QB, TRI>(vr, ta, acc, p, q, out, ldo, partial, lane);
+    warp_reduce_flush<T, OT, PB, QB, TRI>(it.z, it.w, acc, p, q, out, ldo, partial, lane);
     return;
   }
   const int sidx = (gw - ta.nvec) * 32 + lane;
   if (sidx >= ta.nshortv) return;
-  const int vr = __ldg(ta.vorder + ta.nvec + sidx);
-  const int s = __ldg(ta.vptr + vr), e = __ldg(ta.vptr + vr + 1);
+  const int4 it = __ldg(ta.items + ta.nvec + sidx);
+  const int s = it.x, e = it.y;
   int x = s;
   for (; x + 4 <= e; x += 4) {
     int iav[4], ibv[4];
@@ -311,7 +308,7 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
     for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, v[u], xa[u], xb[u]);
   }
   for (; x < e; ++x) one_entry<T, PB, QB, TRI>(x, ta, vals, Ap, Bp, acc);
-  flush_row<T, OT, PB, QB, TRI>(vr, ta, acc, p, q, out, ldo, partial);
+  flush_row<T, OT, PB, QB, TRI>(it.z, it.w, acc, p, q, out, ldo, partial);
 }
 
 // number of warps of a plan
@@ -384,8 +381,8 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
                     const T* Ap, const T* Bp, int p, int q, OT* out, int64_t ldo,
                     cudaStream_t s) {
   constexpr int W = Shape<PB, QB, TRI>::W;
-  TileArgs ta{P.vorder.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
-              P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib};
+  TileArgs ta{P.vitems.as<int4>(), P.vorder.as<int32_t>(), P.vptr.as<int32_t>(),
+              P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib};
   DevBuf partial;
   if (P.nslots > 0) BKS_TRY(partial.alloc(sizeof(T) * (size_t)P.nslots * W, s));
   const int warps = kWarpsPerBlock;
@@ -905,8 +902,8 @@ template <typename T, typename OT, int PB, int QB, bool TRI>
 int launch_contract_fixed(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib,
                           const T* Ap, const T* Bp, int p, int q, OT* out,
                           int64_t ldo, T* partial, cudaStream_t s) {
-  TileArgs ta{P.vorder.as<int32_t>(), P.vptr.as<int32_t>(), P.vrow.as<int32_t>(),
-              P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib};
+  TileArgs ta{P.vitems.as<int4>(), P.vorder.as<int32_t>(), P.vptr.as<int32_t>(),
+              P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib};
   const int warps = kWarpsPerBlock;
   const int blocks = (plan_warps(P) + warps - 1) / warps;
   if (P.nv > 0) {
