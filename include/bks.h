@@ -131,7 +131,8 @@ int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
  *   rows) lives in a fixed 32 MiB device array inside the library, which
  *   every GPU that loads the library keeps until the process exits; a call
  *   needing more (about 4*8*m + 4*8*n + 8*32*(nnz/split) bytes in FP64,
- *   split = 512 unless bks_tensor_autotune / set_tiles chose another)
+ *   split = 512, or 1024 from 16M stored entries, unless
+ *   bks_tensor_autotune / set_tiles chose another)
  *   returns BKS_EUNSUPPORTED before launching anything.  The call allocates
  *   nothing.  Its first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
@@ -249,7 +250,8 @@ int hooi_solve(const bks_tensor* t, const hooi_params* prm, const double* U0,
  * added in a fixed order by a second kernel); pieces and rows longer than
  * `tile` entries take one warp each, the others one lane each, 32 to a
  * warp in order of decreasing length.  The best sizes depend on how the
- * entries spread over rows.  The default is (tile, split) = (16, 512).
+ * entries spread over rows.  The default is (tile, split) = (16, 512), and
+ * (64, 1024) for tensors with at least 16M stored entries.
  * bks_tensor_autotune times the mode-1 and triangle mode-3 contractions
  * (FP32, widths 4 x 4) under the plans (tile, split) in {(8,512),
  * (32,512), (16,1024), (16,512)} and keeps the fastest; tile and split

@@ -12,15 +12,18 @@
 //
 // with (A, ia, B, ib) = (X, j, Y, k) for mode 1 and (X, i, X2, j) for mode 3.
 //
-// Kernel design (one warp per tile of <= kTile + kSplit consecutive
-// entries, see common.cuh): each lane takes a contiguous run of the tile's
-// entries and accumulates PB x QB products in registers.  Rows (virtual
-// rows) that cross lanes are combined by a segmented suffix sum over the
-// lanes (shuffles, fixed order); rows longer than kSplit write per-piece
-// partial sums that a second kernel adds in a fixed order.  No atomics:
-// the result is bitwise reproducible.  The dense operands are gathered from
-// row-major copies padded to PB (QB) columns, built by a pack kernel, so
-// one entry costs one 8-32 byte gather per operand.
+// Kernel design (work plan in common.cuh): rows longer than `split` are cut
+// into pieces whose partial sums a second kernel adds in a fixed order.
+// Rows and pieces longer than `tile` entries take one warp each: the lanes
+// stride over the entries (coalesced index and value loads, the next group
+// loaded while the current one's gathers are in flight) and the lane sums
+// are combined by a recursive-halving shuffle reduction.  Shorter rows take
+// one lane each, 32 to a warp in order of decreasing length, and are summed
+// in registers.  Each warp or lane reads its item (first entry, end, output
+// row, partial slot) with one 16-byte load.  No atomics: the result is
+// bitwise reproducible.  The dense operands are gathered from row-major
+// copies padded to PB (QB) columns, built by a pack kernel, so one entry
+// costs one 8-64 byte gather per operand.
 #include <algorithm>
 
 #include "common.cuh"

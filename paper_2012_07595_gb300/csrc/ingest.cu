@@ -418,6 +418,12 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
     k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)Q.v.p, Q.v64.as<double>(), nseg); ::bks::note_launch();
   }
   BKS_CUDA_TRY(cudaGetLastError());
+  {
+    int tile = kTile, split = kSplit;
+    default_plan(nseg, &tile, &split);
+    T->m1.tile = T->m3.tile = tile;
+    T->m1.split = T->m3.split = split;
+  }
   BKS_TRY(build_tile_plan(T->m1, nseg, s));
   BKS_TRY(build_tile_plan(T->m3, nseg, s));
   Q.host_ptr.resize(n + 1);
