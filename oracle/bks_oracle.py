@@ -8,6 +8,8 @@ Pins (what fixes each function other than itself) live in
 
 * ``symmetrise``          -- dict model of the mirror/sum rule, bitwise.
 * ``mode1/mode3/core``    -- brute-force dense ``einsum`` on tiny tensors.
+* ``mode1_rows_from_input`` -- equals the rows of ``mode1`` of the stored
+                             tensor (duplicates, diagonal entries, mirrors).
 * ``orth_block``          -- orthonormality, reconstruction B = Q H + Qn R,
                              exact rank drops on planted dependent columns.
 * ``schedule_counts``     -- every k1/k3 printed in Tables 1-3 and in the
@@ -28,7 +30,7 @@ import numpy as np
 
 __all__ = [
     "SymTensor", "symmetrise", "mode1", "mode3", "core", "core_dense_check",
-    "orth_block", "schedule_counts", "expand", "gradient_prop2",
+    "orth_block", "schedule_counts", "expand", "gradient_prop2", "mode1_rows_from_input",
     "gradient_global", "inner_solve", "bks", "hooi", "sin_theta_max",
     "top_left_singular", "unfold1", "unfold3", "s_values", "tri_index",
     "BKSResult",
@@ -147,6 +149,37 @@ def mode1(A: SymTensor, X: np.ndarray, Y: np.ndarray) -> np.ndarray:
         vy = v * Y[A.k, b]
         for a in range(p):
             out[:, a + p * b] = np.bincount(A.i, weights=vy * X[A.j, a], minlength=A.m)
+    return out
+
+
+def mode1_rows_from_input(i, j, k, v, X: np.ndarray, Y: np.ndarray, rows) -> np.ndarray:
+    """Selected rows of unfold_1(A.(X,Y)_{2,3}) (Algorithm 3 step (i)) for
+    the tensor that `symmetrise(..., mirror=True)` stores from the one-sided
+    list (i, j, k, v), computed from the list itself: the stored tensor is
+    the input entries plus the mirror (j, i, k, v) of every entry with
+    i != j, with equal keys summed, and the contraction is linear in the
+    stored values, so
+        Out[r, a + p*b] = sum_{e: i_e = r} v_e X[j_e,a] Y[k_e,b]
+                        + sum_{e: j_e = r, i_e != j_e} v_e X[i_e,a] Y[k_e,b].
+    For checks at sizes where forming the stored tensor on the host is too
+    slow.  Returns len(rows) x (p*q)."""
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    k = np.asarray(k, dtype=np.int64)
+    v = np.asarray(v, dtype=np.float64)
+    rows = np.asarray(rows, dtype=np.int64)
+    p, q = X.shape[1], Y.shape[1]
+    order = np.argsort(rows)
+    srt = rows[order]
+    out = np.zeros((rows.size, p * q))
+    # the input entries (row i_e) and the mirrors (row j_e, i_e != j_e)
+    for r_idx, c_idx, keep in ((i, j, np.ones(i.shape, dtype=bool)), (j, i, i != j)):
+        sel = np.isin(r_idx, rows) & keep
+        if not sel.any():
+            continue
+        slot = order[np.searchsorted(srt, r_idx[sel])]
+        contrib = np.einsum("ea,eb->eba", v[sel][:, None] * X[c_idx[sel]], Y[k[sel]])
+        np.add.at(out, slot, contrib.reshape(slot.size, p * q))
     return out
 
 

@@ -112,3 +112,21 @@ def test_contractions_vs_einsum(shape, binary):
 def test_tri_index_layout():
     cols = [(a, b) for b in range(5) for a in range(b + 1)]
     assert [O.tri_index(a, b) for a, b in cols] == list(range(15))
+
+
+def test_mode1_rows_from_input_matches_stored_tensor():
+    """Row-sampled mode-1 values computed from the one-sided list equal the
+    rows of the contraction of the stored (mirrored, summed) tensor; the
+    input has duplicates and diagonal entries."""
+    g = np.random.default_rng(5)
+    m, n, N = 40, 6, 900
+    i = g.integers(0, m, N); j = g.integers(0, m, N); k = g.integers(0, n, N)
+    i[:50] = j[:50]                       # diagonal entries (not mirrored)
+    i[50:100] = i[100:150]; j[50:100] = j[100:150]; k[50:100] = k[100:150]  # duplicates
+    v = g.standard_normal(N)
+    A = O.symmetrise(m, n, i, j, k, v)
+    X = g.standard_normal((m, 3)); Y = g.standard_normal((n, 2))
+    rows = np.array([0, 3, 17, 39, 22])
+    got = O.mode1_rows_from_input(i, j, k, v, X, Y, rows)
+    ref = O.mode1(A, X, Y)[rows]
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
