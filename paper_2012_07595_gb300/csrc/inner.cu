@@ -277,13 +277,22 @@ __device__ void block_cholqr(double* Out, int n, int r, double* W, double* red) 
 // delta = 2 (||offdiag S|| + ||lambda|| ||R||), e_ij = (s_ij + lambda_j r_ij) /
 // (lambda_j - lambda_i); closer pairs get r_ij / 2 (they are a cluster and
 // only their joint span is determined).  Each step squares the relative
-// error; the steps stop after one whose largest correction is below 1e-8
-// (at most four), which takes the FP32 vectors to FP64 accuracy; only FP64
-// matrix products remain, which keeps the FP64 instruction count (a slow
-// pipe on this GPU) small.  On return S.V holds X (row-major,
+// error; the steps stop after one whose largest correction to the r
+// leading vectors (the r largest eigenvalues, ties to the lower index) is
+// below 1e-8 (at most four), which takes those FP32 vectors to FP64
+// accuracy.  The trailing vectors are not used: with (nearly) repeated
+// small eigenvalues they need not settle, and the test ignores them.  Only
+// FP64 matrix products remain, which keeps the FP64 instruction count (a
+// slow pipe on this GPU) small.  On return S.V holds X (row-major,
 // V[i*w + j] = component i of vector j) and S.lam the eigenvalues.
 // P, R, E: w x w FP64 scratch (global).  Every thread of the block calls.
-__device__ void block_eig_refined(int w, InnerShared& S, double* P, double* R, double* E) {
+__device__ __forceinline__ int desc_rank(const double* lam, int w, int j) {
+  int k = 0;
+  for (int l = 0; l < w; ++l) k += (lam[l] > lam[j]) || (lam[l] == lam[j] && l < j);
+  return k;
+}
+
+__device__ void block_eig_refined(int w, int r, InnerShared& S, double* P, double* R, double* E) {
   for (int x = threadIdx.x; x < w * w; x += blockDim.x) S.Gf[x] = (float)S.G[x];
   __syncthreads();
   // one warp: its steps synchronise with __syncwarp only
@@ -334,7 +343,7 @@ __device__ void block_eig_refined(int w, InnerShared& S, double* P, double* R, d
         e = fabs(gap) > delta ? (E[x] + S.lam[j] * R[x]) / gap : 0.5 * R[x];
       }
       E[x] = e;
-      emax = fmax(emax, fabs(e));
+      if (desc_rank(S.lam, w, j) < r) emax = fmax(emax, fabs(e));
     }
     double d1 = 0.0, d2 = 0.0;
     block_max3(emax, d1, d2);
@@ -367,7 +376,7 @@ __device__ void inner_topsvd(const double* T, int n, int w, int r, InnerShared& 
     S.G[i * w + j] = s;
   }
   __syncthreads();
-  block_eig_refined(w, S, P, R, E);
+  block_eig_refined(w, r, S, P, R, E);
   // the r largest eigenvalues (descending) on the diagonal of S.G
   for (int i = threadIdx.x; i < w; i += blockDim.x) S.G[i * w + i] = S.lam[i];
   __syncthreads();
@@ -541,6 +550,30 @@ __device__ void block_copy(const double* src, double* dst, int n) {
   for (int x = threadIdx.x; x < n; x += blockDim.x) dst[x] = src[x];
 }
 
+// T3 = unfold_3(C.(Uh,Uh)_{1,2}) (n x r1^2, column a + r1 b) has equal
+// columns (a, b) and (b, a), C being symmetric in its first two modes, so
+// T3 T3^T = T' T'^T with the r1(r1+1)/2 columns t_aa and (t_ab + t_ba)/sqrt(2),
+// a < b (column b(b+1)/2 + a): the same left singular vectors and values
+// from a smaller Gram without the r1(r1-1)/2 zero eigenvalues.  In place,
+// one row per thread.  Returns the new column count; when r exceeds
+// r1(r1+1)/2, T3 is left as it is and r1^2 is returned.
+__device__ int fold_sym_columns(double* T, int n, int r1, int r) {
+  const int wf = r1 * (r1 + 1) / 2;
+  if (wf < r) return r1 * r1;
+  constexpr double kInvSqrt2 = 0.70710678118654752440;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double row[kMaxW];
+    for (int j = 0; j < r1 * r1; ++j) row[j] = T[c + (int64_t)n * j];
+    int o = 0;
+    for (int b = 0; b < r1; ++b)
+      for (int a = 0; a <= b; ++a, ++o)
+        T[c + (int64_t)n * o] =
+            a == b ? row[a + r1 * b] : (row[a + r1 * b] + row[b + r1 * a]) * kInvSqrt2;
+  }
+  __syncthreads();
+  return wf;
+}
+
 // HOOI sweeps from (Ug, Wg); returns the number of sweeps; ctl[0..1] hold
 // the gradient and ||F|| at the returned point.
 __device__ int coop_sweeps(const CoopArgs& a, int max_sweeps, double tol, InnerShared& S,
@@ -580,7 +613,8 @@ __device__ int coop_sweeps(const CoopArgs& a, int max_sweeps, double tol, InnerS
     if (blockIdx.x == 0) {
       block_copy(a.T3, S.T3, a.k3 * a.r1 * a.r1);
       __syncthreads();
-      inner_topsvd(S.T3, a.k3, a.r1 * a.r1, a.r3, S, S.Wh, a.P, a.R, a.E2);
+      const int w3 = fold_sym_columns(S.T3, a.k3, a.r1, a.r3);
+      inner_topsvd(S.T3, a.k3, w3, a.r3, S, S.Wh, a.P, a.R, a.E2);
       block_copy(S.Wh, a.Wg, a.k3 * a.r3);
       __threadfence();
     }
