@@ -291,8 +291,9 @@ int bks_batch_solve(int njobs, bks_tensor* const* T, const bks_params* P,
  * arrive while others run join the GPU as slots and memory free up.  A
  * running job keeps its tensor, Krylov bases and inner-solve state on the
  * device until it completes; results are copied to host memory.
- * Predicted bytes of a job: 72 * nnz + 8 * (m + n) * 168 + 64 MiB (ingest
- * sort buffers, two sorted copies, bases and workspace).
+ * Predicted bytes of a job: 96 * nnz + 8 * (m + n) * 168 + 64 MiB (ingest
+ * sort buffers, two sorted copies, the interleaved copy of the short rows,
+ * bases and workspace).
  * flags: BKS_SERVE_AUTOTUNE tunes the work tiles per size class. */
 #define BKS_SERVE_AUTOTUNE 1
 typedef struct bks_server bks_server;

@@ -119,7 +119,17 @@ struct Part {
   DevBuf vrow;        // int32 [nv]     row of each virtual row
   DevBuf vslot;       // int32 [nv]     partial-sum slot, -1 if the row is not cut
   DevBuf vorder;      // int32 [nv]: the nvec warp rows, then the short rows by decreasing length
-  DevBuf vitems;      // int4 [nv]: per vorder position (first entry, end, row, slot)
+  DevBuf vitems;      // int4 [nv]: per vorder position (first entry, end, row, slot);
+                      // for the short rows, first and end in the interleaved copy below
+  // Lane-interleaved copy of the short virtual rows' entries: the short
+  // rows are taken 32 at a time in vorder order (group g, lane l), and
+  // entry t of a row sits at sell_base[g] + 32 t + l, so that the 32 lanes'
+  // loads of one step are consecutive.  Positions past a row's end are
+  // padding and never read.
+  int64_t nsell = 0;
+  DevBuf sc0, sc1;    // int32 [nsell]: c0, c1 of the entries
+  DevBuf sv32;        // float [nsell]
+  DevBuf sv64;        // double [nsell]
   DevBuf split_row;   // int32 [nsplit]   rows that were cut
   DevBuf split_first; // int32 [nsplit+1] their first slot (slots are consecutive)
   int32_t nempty = 0;
@@ -127,7 +137,7 @@ struct Part {
   std::vector<int32_t> host_ptr;  // host copy of ptr (kept for the mode-3 copy only)
   void persist() {
     for (DevBuf* b : {&ptr, &c0, &c1, &v, &v32, &v64, &vptr, &vrow, &vslot, &vorder, &vitems,
-                      &split_row, &split_first, &empty_rows})
+                      &sc0, &sc1, &sv32, &sv64, &split_row, &split_first, &empty_rows})
       b->persist();
   }
 };

@@ -95,16 +95,20 @@ struct TileArgs {
   int32_t nvec, nshortv;
   const int32_t* ia;   // index into operand A per entry
   const int32_t* ib;   // index into operand B per entry
+  const int32_t* sia;  // the same for the lane-interleaved copy of the short rows
+  const int32_t* sib;
 };
 
 // One entry's products into acc: v * A[ia,:]^T B[ib,:].
 template <typename T, int PB, int QB, bool TRI>
-__device__ __forceinline__ void one_entry(int e, const TileArgs& ta, const T* __restrict__ vals,
-                                          const T* __restrict__ Ap, const T* __restrict__ Bp,
+__device__ __forceinline__ void one_entry(int e, const int32_t* __restrict__ iap,
+                                          const int32_t* __restrict__ ibp,
+                                          const T* __restrict__ vals, const T* __restrict__ Ap,
+                                          const T* __restrict__ Bp,
                                           T (&acc)[Shape<PB, QB, TRI>::W]) {
   constexpr int NB = TRI ? PB : QB;
-  const int ia = __ldg(ta.ia + e);
-  const int ib = __ldg(ta.ib + e);
+  const int ia = __ldg(iap + e);
+  const int ib = __ldg(ibp + e);
   const T v = __ldg(vals + e);
   T xa[PB], xb[NB];
   load_row<T, PB>(Ap + (int64_t)ia * PB, xa);
@@ -234,10 +238,13 @@ __device__ __forceinline__ void warp_reduce_flush(int64_t row, int slot,
 // its entries 4 at a time (coalesced index and value loads) and the lane
 // sums combined by warp_reduce_flush; the following warps take 32 short
 // virtual rows each, one per lane, ordered by decreasing length, each lane
-// summing its row in registers.  No atomics: the sums have a fixed order.
+// summing its row in registers from the lane-interleaved copy (svals and
+// ta.sia / ta.sib), so that these loads are coalesced too.  No atomics:
+// the sums have a fixed order.
 template <typename T, typename OT, int PB, int QB, bool TRI>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
+k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ svals,
+           const T* __restrict__ Ap,
            const T* __restrict__ Bp, int p, int q, OT* __restrict__ out, int64_t ldo,
            T* __restrict__ partial) {
   constexpr int W = Shape<PB, QB, TRI>::W;
@@ -283,23 +290,25 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
 #pragma unroll
       for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, vc[u], xa[u], xb[u]);
     }
-    for (; x < e; x += 32) one_entry<T, PB, QB, TRI>(x, ta, vals, Ap, Bp, acc);
+    for (; x < e; x += 32) one_entry<T, PB, QB, TRI>(x, ta.ia, ta.ib, vals, Ap, Bp, acc);
     warp_reduce_flush<T, OT, PB, QB, TRI>(it.z, it.w, acc, p, q, out, ldo, partial, lane);
     return;
   }
   const int sidx = (gw - ta.nvec) * 32 + lane;
   if (sidx >= ta.nshortv) return;
+  // the row's entries in the lane-interleaved copy: it.x, it.x + 32, ... < it.y
+  // (the 32 lanes' loads of one step are consecutive)
   const int4 it = __ldg(ta.items + ta.nvec + sidx);
-  const int s = it.x, e = it.y;
-  int x = s;
-  for (; x + 4 <= e; x += 4) {
+  const int e = it.y;
+  int x = it.x;
+  for (; x + 96 < e; x += 128) {
     int iav[4], ibv[4];
     T v[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      iav[u] = __ldg(ta.ia + x + u);
-      ibv[u] = __ldg(ta.ib + x + u);
-      v[u] = __ldg(vals + x + u);
+      iav[u] = __ldg(ta.sia + x + 32 * u);
+      ibv[u] = __ldg(ta.sib + x + 32 * u);
+      v[u] = __ldg(svals + x + 32 * u);
     }
     T xa[4][PB], xb[4][NB];
 #pragma unroll
@@ -310,7 +319,7 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ Ap,
 #pragma unroll
     for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, v[u], xa[u], xb[u]);
   }
-  for (; x < e; ++x) one_entry<T, PB, QB, TRI>(x, ta, vals, Ap, Bp, acc);
+  for (; x < e; x += 32) one_entry<T, PB, QB, TRI>(x, ta.sia, ta.sib, svals, Ap, Bp, acc);
   flush_row<T, OT, PB, QB, TRI>(it.z, it.w, acc, p, q, out, ldo, partial);
 }
 
@@ -371,6 +380,13 @@ inline int grid_for(int64_t n) {
 inline int bucket(int x) { return x <= 2 ? 2 : (x <= 4 ? 4 : 8); }
 
 template <typename T> const T* values_of(const Part& P, int vdtype);
+template <typename T> const T* sell_values_of(const Part& P);
+template <> const float* sell_values_of<float>(const Part& P) { return P.sv32.as<float>(); }
+template <> const double* sell_values_of<double>(const Part& P) { return P.sv64.as<double>(); }
+// the interleaved copy of the index array `a` (c0 or c1 of P)
+inline const int32_t* sell_of(const Part& P, const int32_t* a) {
+  return a == P.c0.as<int32_t>() ? P.sc0.as<int32_t>() : P.sc1.as<int32_t>();
+}
 template <> const float* values_of<float>(const Part& P, int vdtype) {
   return vdtype == BKS_F32 ? P.v.as<float>() : P.v32.as<float>();
 }
@@ -385,13 +401,15 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
                     cudaStream_t s) {
   constexpr int W = Shape<PB, QB, TRI>::W;
   TileArgs ta{P.vitems.as<int4>(), P.vorder.as<int32_t>(), P.vptr.as<int32_t>(),
-              P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib};
+              P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib,
+              sell_of(P, ia), sell_of(P, ib)};
   DevBuf partial;
   if (P.nslots > 0) BKS_TRY(partial.alloc(sizeof(T) * (size_t)P.nslots * W, s));
   const int warps = kWarpsPerBlock;
   const int blocks = (plan_warps(P) + warps - 1) / warps;
   if (P.nv > 0) {
-    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,
+    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype),
+                                                                 sell_values_of<T>(P), Ap,
                                                                  Bp, p, q, out, ldo,
                                                                  partial.as<T>()); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
@@ -906,11 +924,13 @@ int launch_contract_fixed(const Part& P, int vdtype, const int32_t* ia, const in
                           const T* Ap, const T* Bp, int p, int q, OT* out,
                           int64_t ldo, T* partial, cudaStream_t s) {
   TileArgs ta{P.vitems.as<int4>(), P.vorder.as<int32_t>(), P.vptr.as<int32_t>(),
-              P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib};
+              P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib,
+              sell_of(P, ia), sell_of(P, ib)};
   const int warps = kWarpsPerBlock;
   const int blocks = (plan_warps(P) + warps - 1) / warps;
   if (P.nv > 0) {
-    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype), Ap,
+    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype),
+                                                                 sell_values_of<T>(P), Ap,
                                                                  Bp, p, q, out, ldo,
                                                                  partial); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());

@@ -255,6 +255,36 @@ __global__ void k_copy_u32(const uint32_t* in, int64_t n, int32_t* out) {
 
 // The kernel's per-item record in processing order: first entry, end,
 // output row, partial slot (one 16-byte load instead of two dependent ones)
+// 32 x the length of the first (longest) short row of each group of 32
+__global__ void k_sell_len(const int4* items, int32_t nshort, int32_t ngroups, int64_t* glen) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int4 it = items[g * 32];
+    glen[g] = 32 * (int64_t)(it.y - it.x);
+  }
+}
+// Copy the short rows' entries into the lane-interleaved layout and point
+// their work items at it (each thread rewrites only its own item).
+__global__ void k_sell_fill(int4* items, int32_t nshort, const int64_t* gbase,
+                            const int32_t* c0, const int32_t* c1, const float* vf,
+                            const double* vd, int32_t* sc0, int32_t* sc1, float* svf,
+                            double* svd) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nshort;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int4 it = items[x];
+    const int64_t base = gbase[x / 32] + (x % 32);
+    const int len = it.y - it.x;
+    for (int t = 0; t < len; ++t) {
+      const int64_t d = base + 32 * (int64_t)t;
+      sc0[d] = c0[it.x + t];
+      sc1[d] = c1[it.x + t];
+      svf[d] = vf[it.x + t];
+      svd[d] = vd[it.x + t];
+    }
+    items[x] = make_int4((int32_t)base, (int32_t)(base + 32 * (int64_t)len), it.z, it.w);
+  }
+}
+
 __global__ void k_vitems(const int32_t* vorder, int32_t nv, const int32_t* vptr,
                          const int32_t* vrow, const int32_t* vslot, int4* items) {
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nv;
@@ -439,6 +469,42 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
 
 }  // namespace
 
+namespace {
+
+// The lane-interleaved copy of the short rows (see Part).
+int build_sell(Part& P, cudaStream_t s) {
+  const int32_t ng = (P.nshortv + 31) / 32;
+  DevBuf glen, gbase, tot;
+  BKS_TRY(glen.alloc(sizeof(int64_t) * ng, s));
+  BKS_TRY(gbase.alloc(sizeof(int64_t) * ng, s));
+  BKS_TRY(tot.alloc(sizeof(int64_t), s));
+  int4* items = P.vitems.as<int4>() + P.nvec;
+  k_sell_len<<<grid_for(ng), 256, 0, s>>>(items, P.nshortv, ng, glen.as<int64_t>()); ::bks::note_launch();
+  BKS_CUDA_TRY(cudaGetLastError());
+  BKS_TRY(exclusive_scan_i64(glen.as<int64_t>(), gbase.as<int64_t>(), ng, tot.as<int64_t>(), s));
+  int64_t nsell = 0;
+  BKS_CUDA_TRY(cudaMemcpyAsync(&nsell, tot.p, sizeof(nsell), cudaMemcpyDeviceToHost, s));
+  BKS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (nsell >= ((int64_t)1 << 31))
+    return fail(BKS_EUNSUPPORTED, "interleaved short-row copy exceeds int32 positions");
+  P.nsell = nsell;
+  BKS_TRY(P.sc0.alloc(sizeof(int32_t) * std::max<int64_t>(nsell, 1), s));
+  BKS_TRY(P.sc1.alloc(sizeof(int32_t) * std::max<int64_t>(nsell, 1), s));
+  BKS_TRY(P.sv32.alloc(sizeof(float) * std::max<int64_t>(nsell, 1), s));
+  BKS_TRY(P.sv64.alloc(sizeof(double) * std::max<int64_t>(nsell, 1), s));
+  // values in both arithmetic types: the input dtype's array and its converted copy
+  const float* vf = P.v32.p ? P.v32.as<float>() : P.v.as<float>();
+  const double* vd = P.v64.p ? P.v64.as<double>() : P.v.as<double>();
+  k_sell_fill<<<grid_for(P.nshortv), 256, 0, s>>>(items, P.nshortv, gbase.as<int64_t>(),
+                                                  P.c0.as<int32_t>(), P.c1.as<int32_t>(), vf, vd,
+                                                  P.sc0.as<int32_t>(), P.sc1.as<int32_t>(),
+                                                  P.sv32.as<float>(), P.sv64.as<double>()); ::bks::note_launch();
+  BKS_CUDA_TRY(cudaGetLastError());
+  return BKS_OK;
+}
+
+}  // namespace
+
 int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
   const int64_t R = P.rows;
   DevBuf nvr, nslot, issplit, vbase, slotbase, splitpos, tot, isempty, emptypos;
@@ -525,6 +591,7 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
                                             P.vrow.as<int32_t>(), P.vslot.as<int32_t>(),
                                             P.vitems.as<int4>()); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
+    if (P.nshortv > 0) BKS_TRY(build_sell(P, s));
   } else {
     P.nvec = P.nshortv = 0;
   }

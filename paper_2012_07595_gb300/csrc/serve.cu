@@ -143,7 +143,7 @@ struct Job {
 };
 
 size_t predicted_bytes(int64_t m, int64_t n, int64_t nnz) {
-  return (size_t)72 * (size_t)nnz + (size_t)8 * (size_t)(m + n) * 168 + ((size_t)64 << 20);
+  return (size_t)96 * (size_t)nnz + (size_t)8 * (size_t)(m + n) * 168 + ((size_t)64 << 20);
 }
 
 }  // namespace
