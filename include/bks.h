@@ -131,7 +131,7 @@ int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
  *   rows) lives in a fixed 32 MiB device array inside the library, which
  *   every GPU that loads the library keeps until the process exits; a call
  *   needing more (about 4*8*m + 4*8*n + 8*32*(nnz/split) bytes in FP64,
- *   split = 512, or 1024 from 16M stored entries, unless
+ *   split = 512, 1024 from 8M and 2048 from 32M stored entries, unless
  *   bks_tensor_autotune / set_tiles chose another)
  *   returns BKS_EUNSUPPORTED before launching anything.  The call allocates
  *   nothing.  Its first call on a device looks up the array's device address
@@ -249,14 +249,16 @@ int hooi_solve(const bks_tensor* t, const hooi_params* prm, const double* U0,
  * entries are cut into pieces of at most `split` (their partial sums are
  * added in a fixed order by a second kernel); pieces and rows longer than
  * `tile` entries take one warp each, the others one lane each, 32 to a
- * warp in order of decreasing length.  The best sizes depend on how the
- * entries spread over rows.  The default is (tile, split) = (16, 512), and
- * (64, 1024) for tensors with at least 16M stored entries.
+ * warp in order of decreasing length (their entries are read from a
+ * lane-interleaved copy).  The best sizes depend on how the entries spread
+ * over rows.  The default (tile, split) is (32, 512) below 8M stored
+ * entries, (64, 1024) below 32M and (128, 2048) from 32M on.
  * bks_tensor_autotune times the mode-1 and triangle mode-3 contractions
  * (FP32, widths 4 x 4) under the plans (tile, split) in {(8,512),
- * (32,512), (16,1024), (16,512)} and keeps the fastest; tile and split
- * (host, nullable) receive the choice.  bks_tensor_set_tiles applies a
- * known choice (1 <= tile <= 64, 128 <= split <= 4096; else BKS_EINVAL).
+ * (16,512), (64,1024), (128,2048), (32,512)} and keeps the fastest; tile
+ * and split (host, nullable) receive the choice.  bks_tensor_set_tiles
+ * applies a known choice (1 <= tile <= 128, 128 <= split <= 4096; else
+ * BKS_EINVAL).
  * Both synchronise `stream`. */
 int bks_tensor_autotune(bks_tensor* t, int* tile, int* split, void* stream);
 int bks_tensor_set_tiles(bks_tensor* t, int tile, int split, void* stream);

@@ -89,16 +89,24 @@ struct DevBuf {
 // loops of nearly equal trip count; longer ones are processed one per warp
 // with the lanes striding over the entries.  The sizes are per tensor
 // (defaults below; bks_tensor_autotune picks them by timing).
-constexpr int kTile = 16;
+constexpr int kTile = 32;
 constexpr int kSplit = 512;
-// Default plan by size: (16, 512), and (64, 1024) from 16M stored entries on
-// (measured on GB300 Zipf tensors: best at 5M and at 48.5M stored entries)
+// Default plan by size (measured on GB300 Zipf tensors, FP32 mode-1 calls
+// at 5.0M, 11.8M and 48.5M stored entries): (32, 512) below 8M stored
+// entries, (64, 1024) below 32M, (128, 2048) from 32M on.
 inline void default_plan(int64_t nnz, int* tile, int* split) {
-  const bool big = nnz >= (int64_t)16 << 20;
-  *tile = big ? 64 : kTile;
-  *split = big ? 1024 : kSplit;
+  if (nnz >= ((int64_t)32 << 20)) {
+    *tile = 128;
+    *split = 2048;
+  } else if (nnz >= ((int64_t)8 << 20)) {
+    *tile = 64;
+    *split = 1024;
+  } else {
+    *tile = kTile;
+    *split = kSplit;
+  }
 }
-constexpr int kMaxTile = 64;
+constexpr int kMaxTile = 128;
 constexpr int kMinSplit = 128;
 constexpr int kMaxSplit = 4096;
 

@@ -24,7 +24,7 @@ int rebuild(bks_tensor* t, int tile, int split, cudaStream_t s) {
 }  // namespace
 
 int autotune_tensor(bks_tensor* t, cudaStream_t s, int* tile_out, int* split_out) {
-  static const int cand[][2] = {{8, 512}, {32, 512}, {16, 1024}, {16, 512}};
+  static const int cand[][2] = {{8, 512}, {16, 512}, {64, 1024}, {128, 2048}, {32, 512}};
   const int p = 4;
   DevBuf X, Y, out;
   BKS_TRY(X.alloc(sizeof(float) * (size_t)t->m * p, s));
@@ -69,7 +69,7 @@ int autotune_tensor(bks_tensor* t, cudaStream_t s, int* tile_out, int* split_out
 
 int set_tiles(bks_tensor* t, int tile, int split, cudaStream_t s) {
   if (tile < 1 || split < kMinSplit || tile > kMaxTile || split > kMaxSplit)
-    return fail(BKS_EINVAL, "tile must be in [1, 64] and split in [128, 4096]");
+    return fail(BKS_EINVAL, "tile must be in [1, 128] and split in [128, 4096]");
   if (t->m1.tile == tile && t->m1.split == split) return BKS_OK;
   BKS_TRY(rebuild(t, tile, split, s));
   BKS_CUDA_TRY(cudaStreamSynchronize(s));

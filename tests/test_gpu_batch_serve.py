@@ -60,12 +60,12 @@ def test_autotune_keeps_results():
     Y = torch.tensor(g.standard_normal((c.n, 3)), device="cuda")
     before = bk.bks_contract_mode1(T, X, Y).cpu().numpy()
     tile, split = bk.bks_tensor_autotune(T)
-    assert (tile, split) in {(8, 512), (32, 512), (16, 1024), (16, 512)}
+    assert (tile, split) in {(8, 512), (16, 512), (64, 1024), (128, 2048), (32, 512)}
     after = bk.bks_contract_mode1(T, X, Y).cpu().numpy()
     assert np.abs(after - before).max() <= 1e-12 * max(1.0, np.abs(before).max())
     # every row on a warp; long rows cut into many pieces; all but the
     # longest rows on single lanes
-    for tl, sp in [(1, 128), (16, 128), (64, 4096)]:
+    for tl, sp in [(1, 128), (16, 128), (64, 4096), (128, 2048)]:
         bk.bks_tensor_set_tiles(T, tl, sp)
         got = bk.bks_contract_mode1(T, X, Y).cpu().numpy()
         assert np.abs(got - before).max() <= 1e-12 * max(1.0, np.abs(before).max())
@@ -76,7 +76,7 @@ def test_autotune_keeps_results():
     with pytest.raises(bk.BksError):
         bk.bks_tensor_set_tiles(T, 8, 8)
     with pytest.raises(bk.BksError):
-        bk.bks_tensor_set_tiles(T, 65, 1024)
+        bk.bks_tensor_set_tiles(T, 129, 1024)
 
 
 def test_batch_matches_solo():

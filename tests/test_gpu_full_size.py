@@ -2,7 +2,7 @@
 `bench.py` times (GPU only).
 
 * The mode-1 contraction on the 1e6 x 1e6 x 200 Zipf(1.2) tensor (60M
-  one-sided draws, 48.5M stored, the (64, 1024) work plan): sampled output
+  one-sided draws, 48.5M stored, the (128, 2048) work plan): sampled output
   rows against the oracle's definition evaluated from the input list, FP64
   and FP32.
 * The mixed-precision solve on the 1e5 x 1e5 x 50 Zipf(1.1) tensor (5.0M
