@@ -178,7 +178,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # DRAM bytes (read + write) of k_contract<float,float,4,4,0> in one ncu
 # capture of the 500,000 x 500,000 x 200 case (`--ncu-case mode1 --size mid`)
-MID_TRAFFIC_BYTES = 200_094_720 + 34_200_064
+MID_TRAFFIC_BYTES = 186_827_264 + 30_340_352
 MID_NNZ = 11_777_770
 LARGE = {"m": 1_000_000, "n": 200, "draws": 60_000_000, "zipf_s": 1.2, "seed": 3, "r": 5}
 
@@ -189,7 +189,7 @@ def large_roofline(bk, torch, stream, flush, hbm, peak_kind):
     summed), with the 4 x 4 block shape of BK(2,4) (X and Y 4 columns,
     output 16).  `traffic`: DRAM bytes of k_contract measured by ncu on the
     500,000 x 500,000 x 200 case (11,777,770 stored, same kernel; that size
-    runs the (16, 512) plan, this one (64, 1024)), scaled to this launch by
+    runs the (64, 1024) plan, this one (128, 2048)), scaled to this launch by
     stored entries.  One timed call = pack of X and Y,
     the contraction kernel, the piece reduction of long rows and the zero
     rows; algorithmic bytes = index and value streams + row pointers + X and
