@@ -378,6 +378,9 @@ inline int grid_for(int64_t n) {
 }
 
 inline int bucket(int x) { return x <= 2 ? 2 : (x <= 4 ? 4 : 8); }
+// The FP64 kernels are bound by the FP64 pipe, so a 3-column operand (rank
+// 3) is not padded to 4 there: 9 products per entry instead of 16.
+template <typename T> int bucket_t(int x) { return (sizeof(T) == 8 && x == 3) ? 3 : bucket(x); }
 
 template <typename T> const T* values_of(const Part& P, int vdtype);
 template <typename T> const T* sell_values_of(const Part& P);
@@ -438,6 +441,12 @@ int dispatch(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib, co
     return launch_contract<T, OT, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, out, ldo, s);
   BKS_CASE(2, 2) BKS_CASE(2, 4) BKS_CASE(2, 8) BKS_CASE(4, 2) BKS_CASE(4, 4) BKS_CASE(4, 8)
   BKS_CASE(8, 2) BKS_CASE(8, 4)
+  if constexpr (sizeof(T) == 8) {
+    BKS_CASE(3, 2) BKS_CASE(3, 3) BKS_CASE(3, 4) BKS_CASE(3, 8) BKS_CASE(2, 3) BKS_CASE(4, 3)
+    BKS_CASE(8, 3)
+    if (tri && PB == 3)
+      return launch_contract<T, OT, 3, 3, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
+  }
 #undef BKS_CASE
   if (tri && PB == 2)
     return launch_contract<T, OT, 2, 2, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
@@ -459,14 +468,14 @@ int pack(const IT* X, int64_t ldx, int64_t rows, int p, int PB, DevBuf& buf, cud
 template <typename T, typename IT, typename OT>
 int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* Y, int64_t ldy,
                 int q, OT* out, int64_t ldo, cudaStream_t s) {
-  const int PB = bucket(p);
+  const int PB = bucket_t<T>(p);
   // keep PB*QB <= 32: split the Y columns into chunks of at most 4 when PB = 8
   const int qchunk = PB == 8 ? 4 : 8;
   DevBuf Xp;
   BKS_TRY((pack<T, IT>(X, ldx, t->m, p, PB, Xp, s)));
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
-    const int QB = bucket(qq);
+    const int QB = bucket_t<T>(qq);
     DevBuf Yp;
     BKS_TRY((pack<T, IT>(Y + ldy * q0, ldy, t->n, qq, QB, Yp, s)));
     // columns a + p*(q0 + b) of the full output start at column p*q0
@@ -480,7 +489,7 @@ int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
 template <typename T, typename IT, typename OT>
 int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* X2, int64_t ldx2,
                 int q, OT* out, int64_t ldo, cudaStream_t s) {
-  const int PB = bucket(p);
+  const int PB = bucket_t<T>(p);
   DevBuf Xp;
   BKS_TRY((pack<T, IT>(X, ldx, t->m, p, PB, Xp, s)));
   if (!X2)
@@ -489,7 +498,7 @@ int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
   const int qchunk = PB == 8 ? 4 : 8;
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
-    const int QB = bucket(qq);
+    const int QB = bucket_t<T>(qq);
     DevBuf X2p;
     BKS_TRY((pack<T, IT>(X2 + ldx2 * q0, ldx2, t->m, qq, QB, X2p, s)));
     BKS_TRY((dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),

@@ -36,7 +36,7 @@ def _setup(name, vdtype=np.float64):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("p,q", [(1, 1), (2, 3), (3, 4), (4, 4), (5, 2), (8, 4), (5, 5), (8, 8)])
+@pytest.mark.parametrize("p,q", [(1, 1), (2, 3), (3, 3), (3, 4), (4, 4), (5, 2), (8, 4), (5, 5), (8, 8)])
 def test_mode1_fp64(name, p, q):
     import torch
     bk, A, T = _setup(name)
@@ -49,7 +49,7 @@ def test_mode1_fp64(name, p, q):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("p,q", [(2, 2), (3, 4), (5, 5), (8, 3)])
+@pytest.mark.parametrize("p,q", [(2, 2), (3, 3), (3, 4), (5, 5), (8, 3)])
 def test_mode3_fp64(name, p, q):
     import torch
     bk, A, T = _setup(name)
