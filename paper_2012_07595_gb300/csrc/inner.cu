@@ -295,7 +295,7 @@ __device__ __forceinline__ int desc_rank(const double* lam, int w, int j) {
 __device__ void block_eig_refined(int w, int r, InnerShared& S, double* P, double* R, double* E) {
   for (int x = threadIdx.x; x < w * w; x += blockDim.x) S.Gf[x] = (float)S.G[x];
   __syncthreads();
-  // one warp: its steps synchronise with __syncwarp only
+  // FP32 cyclic Jacobi to its rounding floor (every thread of the block takes part)
   block_jacobi_eig<float>(S.Gf, S.Vf, w, 0.f, 40, reinterpret_cast<float*>(S.red),
                           reinterpret_cast<float*>(S.cs));
   for (int x = threadIdx.x; x < w * w; x += blockDim.x) S.V[x] = (double)S.Vf[x];
