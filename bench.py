@@ -110,6 +110,19 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def whole_job_rate(local_seconds, steps, dist=None, device="cpu"):
+    """Whole-job solves/s over the ranks: every rank times `steps` solves of
+    its own replica; the job's time is the slowest rank's (MAX all-reduce),
+    and the units are all ranks' solves.  Returns (rate, job seconds)."""
+    tot, world = float(local_seconds), 1
+    if dist is not None:
+        import torch
+        t = torch.tensor([tot], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot, world = float(t.item()), dist.get_world_size()
+    return world * steps / tot, tot
+
+
 def make_input():
     w = WORKLOAD
     return synth.zipf_tensor(w["seed"], w["m"], w["n"], w["draws"], w["zipf_s"],
@@ -432,12 +445,7 @@ def main():
     lat_mixed, inf_mixed, res_mixed = timed_solves(bk.BKS_PREC_MIXED, args.steps, args.warmup)
     launches = (bk.bks_launch_count() - launches0) * args.steps / (args.steps + args.warmup)
     clk = clocks.stop()
-    tot = sum(lat_mixed)
-    if dist:
-        t = torch.tensor([tot], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-    value = world * args.steps / tot
+    value, tot = whole_job_rate(sum(lat_mixed), args.steps, dist, "cuda")
     # ---- FP64 at the same tolerance ----
     lat64, inf64, res64 = timed_solves(bk.BKS_PREC_FP64, max(2, args.steps // 2), 1)
     fp64_rate = len(lat64) / sum(lat64)
