@@ -30,7 +30,10 @@ constexpr int kGramPerThread = (kMaxK + kMaxB) * kMaxB / kTSThreads;  // 24
 // CU is the arithmetic type of the update, CG that of the Gram (float for
 // the fast first round).  The tile is staged in shared memory in the
 // arithmetic type when both are the same (one conversion per element
-// loaded, none per multiply-add), else in double.
+// loaded, none per multiply-add).  CU = float with CG = double (the FP64
+// Gram of a block whose input carries FP32 rounding anyway) stages the
+// tile twice, in double for the Gram and in float for the update, and the
+// coefficients in float, so that no multiply-add converts.
 template <typename CU, typename CG>
 __global__ void __launch_bounds__(kTSThreads)
 k_ts_pass(const double* __restrict__ Q, int64_t ldq, int K, const double* __restrict__ B,
@@ -38,6 +41,7 @@ k_ts_pass(const double* __restrict__ Q, int64_t ldq, int K, const double* __rest
           int bo, int update, double* __restrict__ Out, int64_t ldo, int gram,
           double* __restrict__ gpart, int64_t m) {
   using ST = typename std::conditional<std::is_same<CU, CG>::value, CG, double>::type;
+  constexpr bool kDual = !std::is_same<CU, ST>::value;  // update staged apart, in CU
   extern __shared__ double sm_raw[];
   ST* sm = reinterpret_cast<ST*>(sm_raw);
   const int LD = kRT + 1;
@@ -45,11 +49,15 @@ k_ts_pass(const double* __restrict__ Q, int64_t ldq, int K, const double* __rest
   ST* Bs = Qs + (size_t)K * LD;            // [b][LD]
   ST* Os = Bs + (size_t)b * LD;            // [bo][LD]
   ST* Ms = Os + (size_t)kMaxB * LD;        // Mq [K][bo] then Mb [b][bo]
+  // the update's operands: the same arrays, or CU copies after Ms (dual)
+  CU* Qu = kDual ? reinterpret_cast<CU*>(Ms + (size_t)(K + b) * kMaxB) : reinterpret_cast<CU*>(Qs);
+  CU* Bu = kDual ? Qu + (size_t)K * LD : reinterpret_cast<CU*>(Bs);
+  CU* Mu = kDual ? Bu + (size_t)b * LD : reinterpret_cast<CU*>(Ms);
   const int tid = threadIdx.x;
   if (update) {
-    for (int x = tid; x < K * bo; x += blockDim.x) Ms[x] = (ST)Mq[(x / bo) + (int64_t)K * (x % bo)];
+    for (int x = tid; x < K * bo; x += blockDim.x) Mu[x] = (CU)Mq[(x / bo) + (int64_t)K * (x % bo)];
     for (int x = tid; x < b * bo; x += blockDim.x)
-      Ms[K * bo + x] = (ST)Mb[(x / bo) + (int64_t)b * (x % bo)];
+      Mu[K * bo + x] = (CU)Mb[(x / bo) + (int64_t)b * (x % bo)];
   }
   const int ocols = update ? bo : b;
   const int gw = K + ocols;  // Gram rows
@@ -66,6 +74,7 @@ k_ts_pass(const double* __restrict__ Q, int64_t ldq, int K, const double* __rest
       double val = 0.0;
       if (r < rows) val = c < K ? Q[r0 + r + ldq * c] : B[r0 + r + ldb * (c - K)];
       (c < K ? Qs + (size_t)c * LD : Bs + (size_t)(c - K) * LD)[r] = (ST)val;
+      if (kDual && update) (c < K ? Qu + (size_t)c * LD : Bu + (size_t)(c - K) * LD)[r] = (CU)val;
     }
     __syncthreads();
     const ST* O = Bs;
@@ -73,8 +82,8 @@ k_ts_pass(const double* __restrict__ Q, int64_t ldq, int K, const double* __rest
       for (int x = tid; x < bo * kRT; x += blockDim.x) {
         const int j = x / kRT, r = x % kRT;
         CU sacc = CU(0);
-        for (int d = 0; d < b; ++d) sacc += (CU)Bs[d * LD + r] * (CU)Ms[K * bo + d * bo + j];
-        for (int e = 0; e < K; ++e) sacc -= (CU)Qs[e * LD + r] * (CU)Ms[e * bo + j];
+        for (int d = 0; d < b; ++d) sacc += Bu[d * LD + r] * Mu[K * bo + d * bo + j];
+        for (int e = 0; e < K; ++e) sacc -= Qu[e * LD + r] * Mu[e * bo + j];
         Os[j * LD + r] = (ST)sacc;
       }
       __syncthreads();
@@ -430,21 +439,26 @@ __global__ void k_copy_small(const double* __restrict__ src, double* __restrict_
     dst[x] = src[x];
 }
 
+template <typename CU, typename CG>
 size_t ts_smem(int K, int b) {
+  using ST = typename std::conditional<std::is_same<CU, CG>::value, CG, double>::type;
   const int LD = kRT + 1;
-  return sizeof(double) * ((size_t)(K + b + kMaxB) * LD + (size_t)(K + b) * kMaxB);
+  size_t bytes = sizeof(ST) * ((size_t)(K + b + kMaxB) * LD + (size_t)(K + b) * kMaxB);
+  if (!std::is_same<CU, ST>::value)
+    bytes += sizeof(CU) * ((size_t)(K + b) * LD + (size_t)(K + b) * kMaxB);
+  return bytes;
 }
 
 template <typename CU, typename CG>
 int launch_ts(const double* Q, int64_t ldq, int K, const double* B, int64_t ldb, int b,
               const double* Mq, const double* Mb, int bo, int update, double* Out, int64_t ldo,
               int gram, double* gpart, int64_t m, int grid, cudaStream_t s) {
-  const size_t smem = ts_smem(K, b);
+  const size_t smem = ts_smem<CU, CG>(K, b);
   static bool attr_set = false;
   if (!attr_set) {
     BKS_CUDA_TRY(cudaFuncSetAttribute(k_ts_pass<CU, CG>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)ts_smem(kMaxK, kMaxB)));
+                                      (int)ts_smem<CU, CG>(kMaxK, kMaxB)));
     attr_set = true;
   }
   k_ts_pass<CU, CG><<<grid, kTSThreads, smem, s>>>(Q, ldq, K, B, ldb, b, Mq, Mb, bo, update, Out,
@@ -554,10 +568,16 @@ int orth_block(const double* Q, int64_t ldq, int K, double* B, int64_t ldb, int 
     }
     return BKS_OK;
   }
-  // P3: [Bn | D] = B1 Mb - Q Mq (no columns, in place) and its Gram
+  // P3: [Bn | D] = B1 Mb - Q Mq (no columns, in place) and its Gram in
+  // FP64 (with fast_first the update in FP32: B1 carries FP32 rounding
+  // already, and P4 takes Bn to FP64 orthogonality from this FP64 Gram)
   const int gw3 = K + no;
-  BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, sm + L.Mq, sm + L.Mb, no, 1, B, ldb, 1,
-                                    ws.gpart.as<double>(), m, grid, s)));
+  if (o.fast_first)
+    BKS_TRY((launch_ts<float, double>(Q, ldq, K, B, ldb, b, sm + L.Mq, sm + L.Mb, no, 1, B, ldb, 1,
+                                      ws.gpart.as<double>(), m, grid, s)));
+  else
+    BKS_TRY((launch_ts<double, double>(Q, ldq, K, B, ldb, b, sm + L.Mq, sm + L.Mb, no, 1, B, ldb, 1,
+                                      ws.gpart.as<double>(), m, grid, s)));
   reduce(gw3 * no);
   k_orth_r3<<<1, 256, 0, s>>>(ws.gram.as<double>(), K, b, sm, st, H, R, st + 1); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
