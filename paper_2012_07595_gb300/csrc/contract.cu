@@ -749,8 +749,18 @@ int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* 
   const size_t smem = std::max(sizeof(T) * 2 * (size_t)batch * KP,
                                sizeof(T) * (size_t)ngroups * ntiles * 16);
   auto kern = big ? k_core_chunks<T, 3> : k_core_chunks<T, 1>;
-  if (smem > 48 * 1024)
-    BKS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // The shared-memory limit is raised once per kernel to the largest size
+  // any call asks for (k1 <= 128: 64 KB of staged rows, or 528 tiles of 16
+  // accumulators), so that calls from several host threads never lower it
+  // under one another (a thread-safe static initialisation).
+  constexpr size_t kSmemMax = std::max<size_t>(64 * 1024, sizeof(T) * 16 * (32 * 33 / 2));
+  static const cudaError_t attr1 = cudaFuncSetAttribute(
+      k_core_chunks<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+  static const cudaError_t attr3 = cudaFuncSetAttribute(
+      k_core_chunks<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+  if (attr1 != cudaSuccess || attr3 != cudaSuccess)
+    return fail(BKS_ECUDA, "k_core_chunks shared-memory limit not accepted");
+  if (smem > kSmemMax) return fail(BKS_EUNSUPPORTED, "core: shared-memory tile above its limit");
   kern<<<nch, kCoreThreads, smem, s>>>(cp.lo.as<int32_t>(), cp.hi.as<int32_t>(), P.c0.as<int32_t>(),
                                        P.c1.as<int32_t>(), values_of<T>(P, t->vdtype), Xp.as<T>(),
                                        r1, KP, batch, ngroups, Mp.as<T>()); ::bks::note_launch();

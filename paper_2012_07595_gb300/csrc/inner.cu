@@ -713,12 +713,12 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   const int nmax = std::max(k1, k3);
   // A, V (nmax^2 each), red (64), cs (the one-warp Jacobi needs 128)
   const size_t hs = sizeof(float) * (2 * (size_t)nmax * nmax + 64 + std::max<size_t>(128, 4 * (size_t)nmax));
-  static bool attr = false;
-  if (!attr) {
-    BKS_CUDA_TRY(cudaFuncSetAttribute(k_hosvd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(float) * (2 * 128 * 128 + 64 + 4 * 128))));
-    attr = true;
-  }
+  // raised once, to the size at k1 = 128 (a thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_hosvd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(sizeof(float) * (2 * 128 * 128 + 64 + 4 * 128)));
+  if (attr != cudaSuccess)
+    return fail(BKS_ECUDA, std::string("k_hosvd shared-memory limit: ") + cudaGetErrorString(attr));
   k_hosvd<<<2, kInnerThreads, hs, s>>>(w.part1.as<float>(), w.part3.as<float>(), nparts, k1, k3,
                                        r1, r3, w.Uh0.as<double>(), w.Wh0.as<double>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
