@@ -189,14 +189,15 @@ __device__ __forceinline__ bool same_bits(double a, double b) {
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+// SM count of the device current at the first call (a thread-safe static
+// initialisation; the library drives one device)
 inline int num_sms() {
-  static int s = -1;
-  if (s < 0) {
-    int dev = 0;
+  static const int s = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-    if (s <= 0) s = 1;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
   return s;
 }
 
