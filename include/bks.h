@@ -331,7 +331,8 @@ int bks_server_cancel(bks_server* srv, uint64_t ticket);
 int bks_server_stats(bks_server* srv, int* queued, int* running, int* finished,
                      size_t* resident_bytes);
 
-/* Cancel what is still queued or running, wait for the workers, free. */
+/* Cancel what is still queued or running, wait for the workers, free.
+ * No other call on the same server may overlap with or follow it. */
 void bks_server_destroy(bks_server* srv);
 
 /* Last error message of the calling thread ("" if none). */

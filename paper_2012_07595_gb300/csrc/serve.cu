@@ -367,10 +367,16 @@ extern "C" void bks_server_destroy(bks_server* S) {
   {
     std::lock_guard<std::mutex> lock(S->mu);
     for (auto& kv : S->jobs) kv.second->cancel.store(1);
+    for (auto& J : S->queue) {
+      J->status = BKS_ECANCELED;
+      J->err = "server destroyed before the job started";
+      J->done = true;
+    }
     S->queue.clear();
     S->stop = true;
   }
   S->cv_work.notify_all();
+  S->cv_done.notify_all();
   for (auto& w : S->workers) w.join();
   delete S;
 }
