@@ -28,7 +28,8 @@
  *     buffer of the call that the comment calls "dtype-typed".
  *
  * Limits: 2*ceil(log2 m) + ceil(log2 n) <= 64 bits (the ingest sort key),
- * stored nonzeros < 2^31, contraction widths p, q <= 8 per call for the
+ * at most 2^31 - 1024 entries after mirroring (input plus mirrors, before
+ * duplicates are summed), contraction widths p, q <= 8 per call for the
  * mode-1 and mode-3 contractions.
  */
 #ifndef BKS_GB300_H

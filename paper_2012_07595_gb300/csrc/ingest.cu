@@ -338,7 +338,9 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
     BKS_TRY(read_i32(tot.as<int32_t>(), &noff, s));
   }
   const int64_t N = nnz + noff;
-  if (N >= (1ll << 31)) return fail(BKS_EUNSUPPORTED, "more than 2^31-1 stored entries");
+  // int32 entry positions, with room for the kernels' look-ahead past a row's end
+  if (N > (1ll << 31) - 1024)
+    return fail(BKS_EUNSUPPORTED, "more than 2^31 - 1024 expanded entries");
   DevBuf keys, pay;
   BKS_TRY(keys.alloc(sizeof(uint64_t) * std::max<int64_t>(N, 1), s));
   BKS_TRY(pay.alloc(sizeof(uint32_t) * std::max<int64_t>(N, 1), s));
@@ -485,7 +487,7 @@ int build_sell(Part& P, cudaStream_t s) {
   int64_t nsell = 0;
   BKS_CUDA_TRY(cudaMemcpyAsync(&nsell, tot.p, sizeof(nsell), cudaMemcpyDeviceToHost, s));
   BKS_CUDA_TRY(cudaStreamSynchronize(s));
-  if (nsell >= ((int64_t)1 << 31))
+  if (nsell > ((int64_t)1 << 31) - 1024)
     return fail(BKS_EUNSUPPORTED, "interleaved short-row copy exceeds int32 positions");
   P.nsell = nsell;
   BKS_TRY(P.sc0.alloc(sizeof(int32_t) * std::max<int64_t>(nsell, 1), s));
