@@ -19,10 +19,13 @@
 // loaded while the current one's gathers are in flight) and the lane sums
 // are combined by a recursive-halving shuffle reduction.  Shorter rows take
 // one lane each, 32 to a warp in order of decreasing length, and are summed
-// in registers.  Each warp or lane reads its item (first entry, end, output
-// row, partial slot) with one 16-byte load.  No atomics: the result is
-// bitwise reproducible.  The dense operands are gathered from row-major
-// copies padded to PB (QB) columns, built by a pack kernel, so one entry
+// in registers; their entries are read from a lane-interleaved copy (entry
+// t of lane l at base + 32 t + l), so that the warp's loads of one step are
+// coalesced as well.  Each warp or lane reads its item (first entry, end,
+// output row, partial slot) with one 16-byte load.  No atomics: the result
+// is bitwise reproducible.  The dense operands are gathered from row-major
+// copies padded to PB (QB) columns (2, 4 or 8; 3 stays 3 in FP64, whose
+// kernels are bound by the FP64 pipe), built by a pack kernel, so one entry
 // costs one 8-64 byte gather per operand.
 #include <algorithm>
 
