@@ -16,6 +16,9 @@ Pins (what fixes each function other than itself) live in
                              figure captions of Section 6.2 (three printed
                              values disagree with the rule; see the tests).
 * ``gradient_prop2``      -- equals ``gradient_global`` (two derivations).
+* ``hosvd_truncated``     -- returns the exact factor subspaces of a core of
+                             exact multilinear rank (U,U,W).F0.
+* ``sin_theta_max``       -- sin of a known planted principal angle.
 * ``inner_solve``/``bks``/``hooi`` -- closed forms n=1 (Eckart-Young) and
                              rank-one slices, exact recovery of a planted
                              multilinear-rank tensor, monotone ||F||, and
@@ -33,7 +36,7 @@ __all__ = [
     "orth_block", "schedule_counts", "expand", "gradient_prop2", "mode1_rows_from_input",
     "gradient_global", "inner_solve", "bks", "hooi", "sin_theta_max",
     "top_left_singular", "unfold1", "unfold3", "s_values", "tri_index",
-    "BKSResult",
+    "BKSResult", "hosvd_truncated", "INNER_INIT_SWEEPS",
 ]
 
 
@@ -508,9 +511,15 @@ def top_left_singular(M: np.ndarray, r: int) -> np.ndarray:
     return u[:, :r].copy()
 
 
-def _top_eig(G: np.ndarray, r: int) -> np.ndarray:
-    w, V = np.linalg.eigh(G)
-    return V[:, ::-1][:, :r].copy()
+def hosvd_truncated(C: np.ndarray, r1: int, r3: int):
+    """Truncated HOSVD of the (1,2)-symmetric core C (k1 x k1 x k3)
+    (Section 2.3, multilinear rank via the SVDs of the unfoldings): Uh holds
+    the r1 leading left singular vectors of unfold_1(C) (which equal those of
+    unfold_2(C) by the symmetry) and Wh the r3 leading left singular vectors
+    of unfold_3(C)."""
+    k1, _, k3 = C.shape
+    return (top_left_singular(C.reshape(k1, -1, order="F"), r1),
+            top_left_singular(unfold3(C), r3))
 
 
 def sin_theta_max(Ua: np.ndarray, Ub: np.ndarray) -> float:
@@ -566,32 +575,37 @@ def _hooi_sweeps(C, Uh, Wh, sweeps, tol):
         done += 1
 
 
+# Section 6.2: the inner problem starts from the truncated HOSVD of C
+# followed by 5 HOOI iterations
+INNER_INIT_SWEEPS = 5
+
+
 def inner_solve(C: np.ndarray, r1: int, r3: int, tol: float, max_inner: int = 1000,
-                init_sweeps: int = 0):
+                init_sweeps: int = INNER_INIT_SWEEPS):
     """Best rank-(r1,r1,r3) approximation of the dense (1,2)-symmetric core
     C (k1 x k1 x k3), Algorithm 5 step (i).
 
     Section 6.2 starts from the truncated HOSVD of C followed by 5 HOOI
-    sweeps and then runs Newton-Grassmann.  This library's reading: the
-    truncated HOSVD start (after ``init_sweeps`` HOOI sweeps, none by
-    default) is compared with the current point (Uh = [I;0], Wh = [I;0],
-    which is (U0, W0) in the bases) by ||F||; the better one continues with
-    HOOI sweeps until its G-gradient is below ``tol`` relative to ||F|| or
-    ``max_inner`` sweeps.  Keeping the current point as a candidate makes
-    ||F|| non-decreasing over the outer iterations (eq. (Fnon-decr)).
+    iterations and then runs Newton-Grassmann (not given in the paper) with
+    the outer stopping criterion.  This library's reading: after the HOSVD
+    start and its ``init_sweeps`` HOOI sweeps the HOOI sweeps continue until
+    the G-gradient is below ``tol`` relative to ||F|| or ``max_inner``
+    sweeps are done.  Monotone safeguard (this library's reading): the
+    current point (Uh = [I;0], Wh = [I;0], which is (U0, W0) in the bases)
+    is kept as a second candidate, and the continuation starts from
+    whichever of the two has the larger ||F||; so ||F|| never decreases
+    over the outer iterations (eq. (Fnon-decr)).
     Returns (Uh, Wh, info)."""
     k1, _, k3 = C.shape
-    C1 = C.reshape(k1, -1, order="F")
-    C3 = unfold3(C)
-    Uh_a = _top_eig(C1 @ C1.T, r1)
-    Wh_a = _top_eig(C3 @ C3.T, r3)
+    Uh_a, Wh_a = hosvd_truncated(C, r1, r3)
     Uh_b = np.eye(k1, r1)
     Wh_b = np.eye(k3, r3)
     A_ = _hooi_sweeps(C, Uh_a, Wh_a, init_sweeps, 0.0)
     B_ = _hooi_sweeps(C, Uh_b, Wh_b, 0, 0.0)
     start = A_ if A_[3] >= B_[3] else B_
     Uh, Wh, g, nf, done = _hooi_sweeps(C, start[0], start[1], max_inner, tol)
-    return Uh, Wh, {"grad": g, "normF": nf, "sweeps": done + init_sweeps,
+    return Uh, Wh, {"grad": g, "normF": nf,
+                    "sweeps": done + (A_[4] if start is A_ else 0),
                     "hosvd_won": start is A_}
 
 
@@ -613,36 +627,35 @@ class BKSResult:
 def bks(A: SymTensor, U0: np.ndarray, W0: np.ndarray, s: int = 2, p: int = 4,
         tol: float = 1e-10, max_outer: int = 500, variant: str = "bk",
         drop_tol: float = 1e-14, inner_tol: float | None = None,
-        max_inner: int = 1000) -> BKSResult:
+        max_inner: int = 1000, scale_free: bool = False) -> BKSResult:
     """Tensor Krylov-Schur for a (1,2)-symmetric tensor (Algorithm 5 with
     U = V, X = Y, Section 5).  Each outer iteration: one BK stage from
     (U0, W0) gives the G-gradient by Proposition 2 (steps (iii)-(iv)); stop
-    if ||grad||/||F|| <= tol; else finish the s-stage expansion (step (v)),
-    form C = A.(X,X,Z) (eq. (tkd)), solve the inner problem (step (i)) and
-    restart from U0 = X Uh, W0 = Z Wh (eq. (tks1), step (ii))."""
+    if ||grad||/||F|| <= tol (Section 6.2); else finish the s-stage
+    expansion (step (v)), form C = A.(X,X,Z) (eq. (tkd)), solve the inner
+    problem (step (i)) to the same criterion, ||grad_C||/||F_C|| <= tol
+    (Section 6.2), and restart from U0 = X Uh, W0 = Z Wh (eq. (tks1), step
+    (ii)).  ``inner_tol`` replaces the inner tolerance when given.
+    ``scale_free`` (this library's option) stops on ||grad||/||F||^2 <= tol
+    instead, a test that does not change when A is scaled; the inner
+    tolerance is then carried over through ||F|| (tol * ||F||)."""
     r1, r3 = U0.shape[1], W0.shape[1]
     U, W = U0.copy(), W0.copy()
     hist = []
-    # the inner problem is solved to a tenth of the outer tolerance so that
-    # its residual gradient does not hold the outer test just above tol
-    itol_fixed = inner_tol
     F = None
     for it in range(max_outer + 1):
         X, Z, info = expand(A, U, W, 1, p, variant, drop_tol)
         g, nf, F = gradient_prop2(info["H1"], info["P1"], info["P3"], r1, r3)
-        hist.append({"grad_rel": g / nf if nf > 0 else math.inf, "normF": nf})
-        if nf > 0 and g <= tol * nf:
-            return BKSResult(U, W, F, True, it, g / nf, nf, hist)
+        rel = (g / (nf * nf) if scale_free else g / nf) if nf > 0 else math.inf
+        hist.append({"grad_rel": rel, "normF": nf})
+        if nf > 0 and rel <= tol:
+            return BKSResult(U, W, F, True, it, rel, nf, hist)
         if it == max_outer:
             break
         X, Z, _ = expand(A, U, W, s, p, variant, drop_tol)
         hist[-1]["k1"], hist[-1]["k3"] = X.shape[1], Z.shape[1]
         Cc = core(A, X, Z)
-        # inexact inner solves: the projected problem is solved a hundred
-        # times more accurately than the current outer gradient, and at
-        # least to a tenth of the outer tolerance (this library's reading;
-        # Section 6.2 uses the outer tolerance throughout)
-        itol = itol_fixed if itol_fixed is not None else max(0.1 * tol, 0.01 * g / nf)
+        itol = inner_tol if inner_tol is not None else (tol * nf if scale_free else tol)
         Uh, Wh, iinfo = inner_solve(Cc, r1, r3, itol, max_inner)
         hist[-1]["inner_sweeps"] = iinfo["sweeps"]
         U = X @ Uh

@@ -204,3 +204,85 @@ def test_example1_noise_level_scaling():
         out[rho] = np.linalg.norm(R, 2)
     ratio = out[1e-2] / out[1e-4]
     assert 30 < ratio < 300
+
+
+def _planted_core(seed, k1, k3, r1, r3):
+    """C = (Uh, Uh, Wh).F0 with orthonormal Uh (k1 x r1), Wh (k3 x r3) and a
+    generic F0 symmetric in its first two modes: a dense core of exact
+    multilinear rank (r1, r1, r3)."""
+    g = synth.rng(seed)
+    Uh = synth.orthonormal(g, k1, r1)
+    Wh = synth.orthonormal(g, k3, r3)
+    F0 = g.standard_normal((r1, r1, r3))
+    F0 = 0.5 * (F0 + F0.transpose(1, 0, 2))
+    C = np.einsum("ia,jb,kc,abc->ijk", Uh, Uh, Wh, F0, optimize=True)
+    return 0.5 * (C + C.transpose(1, 0, 2)), Uh, Wh
+
+
+@pytest.mark.parametrize("k1,k3,r1,r3", [(12, 7, 3, 2), (20, 9, 2, 3), (36, 21, 3, 3)])
+def test_hosvd_recovers_planted_factor_subspaces(k1, k3, r1, r3):
+    """Section 2.3: the HOSVD of a tensor of exact multilinear rank
+    (r1, r1, r3) returns the column spaces of its unfoldings, i.e. span(Uh)
+    and span(Wh), whatever the order of the trailing (zero) singular
+    values.  Taking the trailing instead of the leading vectors, or the
+    wrong unfolding, returns an orthogonal or unrelated subspace."""
+    C, Uh, Wh = _planted_core(70 + k1, k1, k3, r1, r3)
+    Ua, Wa = O.hosvd_truncated(C, r1, r3)
+    assert Ua.shape == (k1, r1) and Wa.shape == (k3, r3)
+    assert O.sin_theta_max(Uh, Ua) < 1e-12
+    assert O.sin_theta_max(Wh, Wa) < 1e-12
+    # with the exact factors the core has all of C's norm
+    F = np.einsum("abc,ai,bj,ck->ijk", C, Ua, Ua, Wa)
+    assert abs(np.linalg.norm(F) - np.linalg.norm(C)) < 1e-12 * np.linalg.norm(C)
+
+
+def test_inner_solve_paper_schedule_counts_hosvd_sweeps():
+    """Section 6.2: the inner solve starts from the truncated HOSVD and runs
+    5 HOOI iterations before its stopping test; on a random core where the
+    HOSVD start beats the warm start [I;0] the sweep count includes them."""
+    g = synth.rng(81)
+    C = g.standard_normal((14, 14, 9)); C = C + C.transpose(1, 0, 2)
+    Uh, Wh, info = O.inner_solve(C, 2, 2, 1e-10)
+    assert info["hosvd_won"]
+    assert info["sweeps"] >= O.INNER_INIT_SWEEPS == 5
+    assert info["grad"] <= 1e-10 * info["normF"]
+    # an exact-rank core is solved by the start itself: the gradient is
+    # zero there, and the 5 start sweeps keep the subspaces
+    Cp, Up, Wp = _planted_core(82, 14, 9, 2, 2)
+    Uq, Wq, iq = O.inner_solve(Cp, 2, 2, 1e-12)
+    assert O.sin_theta_max(Up, Uq) < 1e-12 and O.sin_theta_max(Wp, Wq) < 1e-12
+
+
+@pytest.mark.parametrize("theta", [1e-6, 1e-3, 0.3, 1.2])
+def test_sin_theta_max_known_angle(theta):
+    """Principal angles (the accuracy measure of Section 6.2.1): rotate one
+    basis vector of an orthonormal pair by a known angle theta into the
+    orthogonal complement; the largest principal angle is theta, and the
+    sine form is accurate to rounding at small angles."""
+    g = synth.rng(90)
+    Q = synth.orthonormal(g, 30, 5)
+    Ua = Q[:, :3]
+    Ub = Ua.copy()
+    Ub[:, 1] = np.cos(theta) * Q[:, 1] + np.sin(theta) * Q[:, 4]
+    got = O.sin_theta_max(Ua, Ub)
+    assert abs(got - np.sin(theta)) <= 1e-12 * np.sin(theta) + 4e-16
+    # a rotation inside either subspace changes no principal angle
+    R = synth.orthonormal(g, 3, 3)
+    assert abs(O.sin_theta_max(Ua @ R, Ub) - got) <= 1e-12 * got + 4e-16
+    assert abs(O.sin_theta_max(Ua, Ub @ R) - got) <= 1e-12 * got + 4e-16
+    # symmetric for subspaces of equal dimension
+    assert abs(O.sin_theta_max(Ub, Ua) - got) <= 1e-12 * got + 4e-16
+
+
+def test_sin_theta_max_picks_the_largest_of_several_angles():
+    g = synth.rng(91)
+    Q = synth.orthonormal(g, 40, 6)
+    Ua = Q[:, :3]
+    Ub = Ua.copy()
+    angles = [0.05, 0.0, 0.4]
+    for c, th in enumerate(angles):
+        Ub[:, c] = np.cos(th) * Q[:, c] + np.sin(th) * Q[:, 3 + c]
+    assert abs(O.sin_theta_max(Ua, Ub) - np.sin(0.4)) < 1e-14
+    assert O.sin_theta_max(Ua, Ua) < 1e-15
+    # orthogonal subspaces: the angle is pi/2
+    assert abs(O.sin_theta_max(Q[:, :2], Q[:, 2:4]) - 1.0) < 1e-14
