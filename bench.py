@@ -406,11 +406,12 @@ def main():
     W0 = torch.tensor(W0h, device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def params(prec):
+    def params(prec, inner=None):
         return bk.BksParams(r1=w["r"], r3=w["r"], stages=w["stages"], block_p=w["block_p"],
                             tol=w["tol"], precision=prec, mixed_tol=w["mixed_tol"],
                             tol_scale_free=w["tol_scale_free"], refine_sweeps=50,
-                            max_outer=500)
+                            max_outer=500,
+                            inner_schedule=bk.BKS_INNER_FAST if inner is None else inner)
 
     def timed_solves(prec, steps, warm):
         lat = []

@@ -71,6 +71,10 @@ extern "C" {
 #define BKS_VARIANT_MIN 1  /* min-BK, Algorithm 4 / Table 1 */
 #define BKS_VARIANT_MAX 2  /* max-BK, Table 2 */
 
+#define BKS_INNER_PAPER 0  /* inner solve as Section 6.2: truncated HOSVD + 5 HOOI sweeps,
+                              then sweeps to the outer stopping criterion */
+#define BKS_INNER_FAST  1  /* truncated HOSVD without start sweeps, inexact inner tolerance */
+
 typedef struct bks_tensor bks_tensor;
 
 /* ---- tensor storage (Definition 2.1; Section 4.3 storage reading) -------
@@ -123,24 +127,30 @@ int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
                        int64_t ldo, int dtype, void* stream);
 
 /* bks_contract_mode1_noalloc: the same result as bks_contract_mode1 (same
- *   arguments, same kernels, bitwise the same output) for callers that
- *   cannot allocate device memory -- for example a host framework that has
- *   reserved the whole device for its own memory pool, or code that must
- *   not let a library call cudaMalloc, which can synchronise the device and
- *   fail under memory pressure.  The paper has no counterpart of this call.
+ *   arguments, the same code path with the same kernels and summation
+ *   order, bitwise the same output) for callers that cannot allocate device
+ *   memory -- for example a host framework that has reserved the whole
+ *   device for its own memory pool, or code that must not let a library
+ *   call cudaMalloc, which can synchronise the device and fail under memory
+ *   pressure.  The paper has no counterpart of this call.
  *   Scratch (the packed copies of X and Y and the partial sums of long
  *   rows) lives in a fixed 32 MiB device array inside the library, which
- *   every GPU that loads the library keeps until the process exits; a call
- *   needing more (about 4*8*m + 4*8*n + 8*32*(nnz/split) bytes in FP64,
- *   split = 512, 1024 from 8M and 2048 from 32M stored entries, unless
- *   bks_tensor_autotune / set_tiles chose another)
- *   returns BKS_EUNSUPPORTED before launching anything.  The call allocates
- *   nothing.  Its first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.  All calls share the one array and every call
- *   overwrites what it uses (nothing has to start at zero), so calls that
- *   overlap on the GPU -- on different streams, or from several host
- *   threads -- race; order them on one stream. */
+ *   every GPU that loads the library keeps until the process exits.  A call
+ *   needs s*(PB*m + QB*n + PB*QB*nslots) bytes, each of the three pieces
+ *   rounded up to 256 bytes, with s = 8 (BKS_F64) or 4 (BKS_F32); PB is p
+ *   padded to 2, 4 or 8 (3 stays 3 in FP64), QB likewise for min(q, 8), or
+ *   for min(q, 4) when PB = 8; nslots is the number of pieces into which
+ *   rows longer than the work plan's split (512 below 8M stored entries,
+ *   1024 below 32M, 2048 from 32M, unless bks_tensor_autotune / set_tiles
+ *   chose another) are cut, about nnz / split on power-law tensors.  The
+ *   worst case is 64*m + 64*n + 256*nslots bytes in FP64.  A call needing
+ *   more than 32 MiB returns BKS_EUNSUPPORTED before launching anything.
+ *   The call allocates nothing.  Its first call on a device looks up the
+ *   array's device address (cudaGetSymbolAddress) with that device current;
+ *   make that first call before any stream capture.  All calls share the
+ *   one array and every call overwrites what it uses (nothing has to start
+ *   at zero), so calls that overlap on the GPU -- on different streams, or
+ *   from several host threads -- race; order them on one stream. */
 int bks_contract_mode1_noalloc(const bks_tensor* t, const void* X, int64_t ldx,
                                int p, const void* Y, int64_t ldy, int q,
                                void* out, int64_t ldo, int dtype, void* stream);
@@ -178,9 +188,9 @@ typedef struct {
                           form after the FP32 phase */
   uint64_t seed;       /* random start when U0/W0 are NULL */
   double drop_tol;     /* rank-drop threshold of the block QR (relative) */
-  double inner_tol;    /* inner stopping tolerance on ||grad_C|| / ||F_C|| (<= 0: inexact
-                          inner solves, max(tol / 10, ||grad|| / ||F|| / 100) at the
-                          current outer point) */
+  double inner_tol;    /* inner stopping tolerance on ||grad_C|| / ||F_C||; <= 0: set by
+                          inner_schedule (PAPER: the outer tolerance; FAST: max(tol / 10,
+                          ||grad|| / ||F|| / 100) at the current outer point) */
   int tol_scale_free;  /* 0: stop when ||grad|| / ||F|| <= tol (Section 6.2, depends on the
                           scale of A); 1: stop when ||grad|| / ||F||^2 <= tol (invariant
                           under A -> c A) */
@@ -190,6 +200,12 @@ typedef struct {
                           tol (FP64 stage-1 contractions, gradient and stopping test; FP32
                           later Krylov blocks and core C with its first-order blocks
                           replaced by FP64 projections of the stage-1 results) */
+  int inner_schedule;  /* BKS_INNER_PAPER (default) or BKS_INNER_FAST: the inner solve of
+                          Algorithm 5 step (i).  Both start from the better (larger ||F||) of
+                          the truncated HOSVD of C and the current point and continue with
+                          HOOI sweeps; PAPER gives the HOSVD start 5 sweeps first and solves
+                          to the outer tolerance (Section 6.2), FAST gives it none and stops
+                          at the inexact tolerance above (fewer sweeps, same optimum) */
 } bks_params;
 
 typedef struct {
@@ -209,7 +225,8 @@ typedef struct {
 } bks_info;
 
 /* Default parameters: r1 = r3 = 2, s = 2, p = 4, tol 1e-10, max_outer 500,
- * max_inner 1000, BK, FP64, refine 1, seed 1, mixed_tol 1e-4, drop_tol 1e-14 (a rank-drop threshold
+ * max_inner 1000, BK, FP64, refine 1, seed 1, mixed_tol 1e-4, inner schedule
+ * BKS_INNER_PAPER, drop_tol 1e-14 (a rank-drop threshold
  * well below the gradient accuracy: near convergence the stage-1 residual
  * columns that carry the gradient are small relative to their raw norms). */
 void bks_params_default(bks_params* p);
@@ -231,8 +248,12 @@ typedef struct {
   double tol;
   int max_iter;
   int grad_every;      /* gradient test cadence (Section 6.1: every 10) */
-  int precision;       /* BKS_PREC_FP64 or BKS_PREC_MIXED */
+  int precision;       /* BKS_PREC_FP64 or BKS_PREC_MIXED: FP32 contractions until the
+                          gradient, evaluated from them, has ||grad|| / ||F||^2 <= mixed_tol
+                          or stops halving for two evaluations; then FP64 contractions (the
+                          gradient is evaluated at the next iteration again) until tol */
   uint64_t seed;
+  double mixed_tol;    /* MIXED only (<= 0: 1e-4) */
 } hooi_params;
 
 void hooi_params_default(hooi_params* p);

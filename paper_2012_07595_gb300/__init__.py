@@ -26,7 +26,7 @@ __all__ = [
     "bks_contract_mode3", "bks_core", "bks_solve", "hooi_solve", "BksParams", "HooiParams",
     "col_major", "library_path", "bks_launch_count", "bks_tensor_autotune",
     "bks_tensor_set_tiles", "bks_batch_solve", "Server", "BKS_ECANCELED", "BKS_EPENDING",
-    "BKS_EBUDGET",
+    "BKS_EBUDGET", "BKS_INNER_PAPER", "BKS_INNER_FAST", "bks_contract_mode1_noalloc",
 ]
 
 BKS_OK = 0
@@ -39,6 +39,7 @@ BKS_F32, BKS_F64 = 1, 2
 BKS_MIRROR, BKS_VALIDATE_SYMMETRIC, BKS_INPUT_ON_DEVICE = 1, 2, 4
 BKS_PREC_FP64, BKS_PREC_MIXED = 0, 1
 BKS_VARIANT_BK, BKS_VARIANT_MIN, BKS_VARIANT_MAX = 0, 1, 2
+BKS_INNER_PAPER, BKS_INNER_FAST = 0, 1
 
 _ERRNAMES = {BKS_EINVAL: "BKS_EINVAL", BKS_ENOMEM: "BKS_ENOMEM", BKS_ECUDA: "BKS_ECUDA",
              BKS_EASYM: "BKS_EASYM", BKS_ENOTCONV: "BKS_ENOTCONV",
@@ -60,7 +61,8 @@ class _Params(ctypes.Structure):
                 ("variant", ctypes.c_int), ("precision", ctypes.c_int),
                 ("refine_sweeps", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("drop_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("tol_scale_free", ctypes.c_int), ("mixed_tol", ctypes.c_double)]
+                ("tol_scale_free", ctypes.c_int), ("mixed_tol", ctypes.c_double),
+                ("inner_schedule", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -76,7 +78,8 @@ class _Info(ctypes.Structure):
 class _HooiParams(ctypes.Structure):
     _fields_ = [("r1", ctypes.c_int), ("r3", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("grad_every", ctypes.c_int),
-                ("precision", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("mixed_tol", ctypes.c_double)]
 
 
 _lib = None
@@ -302,11 +305,27 @@ def bks_contract_mode1(t: Tensor, X, Y, out=None, stream=None):
 
 
 def bks_contract_mode1_noalloc(t: Tensor, X, Y, out, stream=None):
-    """bks_contract_mode1 for callers that cannot allocate device memory:
-    the library uses its fixed 32 MiB device scratch array instead of
-    allocating.  `out` (m x p q, column-major) must be given."""
-    X, Y = col_major(X), col_major(Y)
+    """bks_contract_mode1 for callers that cannot allocate device memory: the
+    library uses its fixed 32 MiB device scratch array instead of
+    allocating, and this wrapper allocates nothing either.  X (m x p), Y
+    (n x q) and `out` (m x p q) must be column-major CUDA tensors (stride
+    (1, ld), ld >= rows) of one dtype (float32 or float64) on one device;
+    anything else raises instead of being copied."""
+    import torch
+    for name, x, rows in (("X", X, t.m), ("Y", Y, t.n), ("out", out, t.m)):
+        if not isinstance(x, torch.Tensor) or x.dim() != 2 or not x.is_cuda:
+            raise ValueError(f"{name} must be a 2-D CUDA tensor")
+        if x.shape[0] != rows or x.stride(0) != 1 or (x.shape[1] > 1 and x.stride(1) < rows):
+            raise ValueError(f"{name} must be column-major with {rows} rows (stride (1, ld), "
+                             f"ld >= {rows}); got shape {tuple(x.shape)}, "
+                             f"stride {tuple(x.stride())}")
+    if not (X.dtype == Y.dtype == out.dtype) or X.dtype not in (torch.float32, torch.float64):
+        raise ValueError("X, Y and out must share one dtype, float32 or float64")
+    if not (X.device == Y.device == out.device):
+        raise ValueError("X, Y and out must be on one device")
     p, q = X.shape[1], Y.shape[1]
+    if out.shape[1] != p * q:
+        raise ValueError(f"out must have p*q = {p * q} columns, not {out.shape[1]}")
     _check(lib().bks_contract_mode1_noalloc(t.handle, ctypes.c_void_p(X.data_ptr()), _ld(X), p,
                                             ctypes.c_void_p(Y.data_ptr()), _ld(Y), q,
                                             ctypes.c_void_p(out.data_ptr()), _ld(out),
@@ -363,6 +382,7 @@ class BksParams:
     inner_tol: float = 0.0
     tol_scale_free: int = 0
     mixed_tol: float = 1e-4
+    inner_schedule: int = BKS_INNER_PAPER
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -380,6 +400,7 @@ class HooiParams:
     grad_every: int = 10
     precision: int = BKS_PREC_FP64
     seed: int = 1
+    mixed_tol: float = 1e-4
 
     def to_c(self) -> _HooiParams:
         p = _HooiParams()

@@ -5,7 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -189,17 +192,55 @@ __device__ __forceinline__ bool same_bits(double a, double b) {
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
-// SM count of the device current at the first call (a thread-safe static
-// initialisation; the library drives one device)
-inline int num_sms() {
-  static const int s = [] {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 1;
-  }();
-  return s;
+// ---- per-device state -------------------------------------------------------
+// Calls may come from any host thread with any current device; what is
+// cached per process (SM counts, raised shared-memory limits, workspaces)
+// is therefore kept per device index.
+constexpr int kMaxDevices = 64;
+
+// The calling thread's current device, or -1 when it cannot be used as an
+// index into the per-device caches.
+inline int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+  return dev;
 }
+
+// SM count of the current device (queried once per device).
+inline int num_sms() {
+  static std::atomic<int> cache[kMaxDevices];
+  const int dev = current_device();
+  int n = dev >= 0 ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (n > 0) return n;
+  int d = 0;
+  cudaGetDevice(&d);
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0) n = 1;
+  if (dev >= 0) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
+// Runs an initialisation (a cudaFuncSetAttribute, say) once per device, the
+// first time a thread with that device current asks, and returns its
+// result on every later call for that device.  Thread-safe.
+class PerDeviceOnce {
+ public:
+  template <typename F>
+  cudaError_t run(F&& init) {
+    const int dev = current_device();
+    if (dev < 0) return init();
+    std::lock_guard<std::mutex> lock(mu_);
+    if (!done_[dev]) {
+      err_[dev] = init();
+      done_[dev] = true;
+    }
+    return err_[dev];
+  }
+
+ private:
+  std::mutex mu_;
+  bool done_[kMaxDevices] = {};
+  cudaError_t err_[kMaxDevices] = {};
+};
 
 // ---- scans (scan.cu) ------------------------------------------------------
 // out[i] = sum_{t<i} in[i]; out may alias in; total (device) optional.
@@ -234,7 +275,7 @@ int contract_core_x(const bks_tensor* t, const double* U, int64_t ldu, int r1, c
                     int64_t ldw, int r3, double* F, bool fp32, cudaStream_t s);
 // inner solve (inner.cu)
 int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int max_inner,
-                double* Uh, double* Wh, double* negU, double* negW, double* info,
+                int init_sweeps, double* Uh, double* Wh, double* negU, double* negW, double* info,
                 cudaStream_t s);
 
 }  // namespace bks

@@ -400,29 +400,34 @@ template <> const double* values_of<double>(const Part& P, int vdtype) {
   return vdtype == BKS_F64 ? P.v.as<double>() : P.v64.as<double>();
 }
 
-// One launch pair (tile kernel + piece reduction) for fixed buckets.
+// One launch pair (tile kernel + piece reduction) for fixed buckets.  The
+// partial sums of cut rows go to `part` (nslots x W values) when the caller
+// provides it, else to a stream-ordered allocation.
 template <typename T, typename OT, int PB, int QB, bool TRI>
 int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib,
                     const T* Ap, const T* Bp, int p, int q, OT* out, int64_t ldo,
-                    cudaStream_t s) {
+                    T* part, cudaStream_t s) {
   constexpr int W = Shape<PB, QB, TRI>::W;
   TileArgs ta{P.vitems.as<int4>(), P.vorder.as<int32_t>(), P.vptr.as<int32_t>(),
               P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib,
               sell_of(P, ia), sell_of(P, ib)};
   DevBuf partial;
-  if (P.nslots > 0) BKS_TRY(partial.alloc(sizeof(T) * (size_t)P.nslots * W, s));
+  if (P.nslots > 0 && !part) {
+    BKS_TRY(partial.alloc(sizeof(T) * (size_t)P.nslots * W, s));
+    part = partial.as<T>();
+  }
   const int warps = kWarpsPerBlock;
   const int blocks = (plan_warps(P) + warps - 1) / warps;
   if (P.nv > 0) {
     k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype),
                                                                  sell_values_of<T>(P), Ap,
                                                                  Bp, p, q, out, ldo,
-                                                                 partial.as<T>()); ::bks::note_launch();
+                                                                 part); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (P.nsplit > 0) {
     k_split_reduce<T, OT, PB, QB, TRI><<<P.nsplit, 256, 0, s>>>(
-        P.split_row.as<int32_t>(), P.split_first.as<int32_t>(), P.nsplit, partial.as<T>(), p, q,
+        P.split_row.as<int32_t>(), P.split_first.as<int32_t>(), P.nsplit, part, p, q,
         out, ldo); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
@@ -438,55 +443,108 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
 template <typename T, typename OT>
 int dispatch(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib, const T* Ap,
              int PB, const T* Bp, int QB, bool tri, int p, int q, OT* out,
-             int64_t ldo, cudaStream_t s) {
+             int64_t ldo, cudaStream_t s, T* part = nullptr) {
 #define BKS_CASE(pb, qb)                                                                      \
   if (!tri && PB == pb && QB == qb)                                                           \
-    return launch_contract<T, OT, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, out, ldo, s);
+    return launch_contract<T, OT, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, out, ldo,   \
+                                                 part, s);
   BKS_CASE(2, 2) BKS_CASE(2, 4) BKS_CASE(2, 8) BKS_CASE(4, 2) BKS_CASE(4, 4) BKS_CASE(4, 8)
   BKS_CASE(8, 2) BKS_CASE(8, 4)
   if constexpr (sizeof(T) == 8) {
     BKS_CASE(3, 2) BKS_CASE(3, 3) BKS_CASE(3, 4) BKS_CASE(3, 8) BKS_CASE(2, 3) BKS_CASE(4, 3)
     BKS_CASE(8, 3)
     if (tri && PB == 3)
-      return launch_contract<T, OT, 3, 3, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
+      return launch_contract<T, OT, 3, 3, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, part,
+                                                    s);
   }
 #undef BKS_CASE
   if (tri && PB == 2)
-    return launch_contract<T, OT, 2, 2, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
+    return launch_contract<T, OT, 2, 2, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, part,
+                                                  s);
   if (tri && PB == 4)
-    return launch_contract<T, OT, 4, 4, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
+    return launch_contract<T, OT, 4, 4, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, part,
+                                                  s);
   if (tri && PB == 8)
-    return launch_contract<T, OT, 8, 8, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, s);
+    return launch_contract<T, OT, 8, 8, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, part,
+                                                  s);
   return fail(BKS_EUNSUPPORTED, "contraction bucket not instantiated");
+}
+
+template <typename T, typename IT>
+int pack_into(const IT* X, int64_t ldx, int64_t rows, int p, int PB, T* dst, cudaStream_t s) {
+  k_pack<IT, T><<<grid_for(rows), 256, 0, s>>>(X, ldx, rows, p, PB, dst); ::bks::note_launch();
+  BKS_CUDA_TRY(cudaGetLastError());
+  return BKS_OK;
 }
 
 template <typename T, typename IT>
 int pack(const IT* X, int64_t ldx, int64_t rows, int p, int PB, DevBuf& buf, cudaStream_t s) {
   BKS_TRY(buf.alloc(sizeof(T) * (size_t)rows * PB, s));
-  k_pack<IT, T><<<grid_for(rows), 256, 0, s>>>(X, ldx, rows, p, PB, buf.as<T>()); ::bks::note_launch();
-  BKS_CUDA_TRY(cudaGetLastError());
-  return BKS_OK;
+  return pack_into<T, IT>(X, ldx, rows, p, PB, buf.as<T>(), s);
 }
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Temporaries of one mode-1 contraction: the packed operands and the
+// partial sums of cut rows.  Taken from a fixed region when `fixed` is
+// given (the allocation-free entry point), else allocated on the stream.
+struct Mode1Scratch {
+  unsigned char* fixed = nullptr;
+  size_t fixed_bytes = 0;
+};
+
+// Bytes of the temporaries of a mode-1 contraction with widths p x q in
+// arithmetic type T (each piece 256-byte aligned): packed X (m x PB),
+// packed Y (n x QB, reused by every chunk of Y columns) and the partial
+// sums (nslots x PB*QB).
+template <typename T>
+size_t mode1_scratch_bytes(const bks_tensor* t, int p, int q);
 
 template <typename T, typename IT, typename OT>
 int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* Y, int64_t ldy,
-                int q, OT* out, int64_t ldo, cudaStream_t s) {
+                int q, OT* out, int64_t ldo, cudaStream_t s, const Mode1Scratch* fx = nullptr) {
   const int PB = bucket_t<T>(p);
   // keep PB*QB <= 32: split the Y columns into chunks of at most 4 when PB = 8
   const int qchunk = PB == 8 ? 4 : 8;
-  DevBuf Xp;
-  BKS_TRY((pack<T, IT>(X, ldx, t->m, p, PB, Xp, s)));
+  const int QBmax = bucket_t<T>(std::min(qchunk, q));
+  const size_t xb = align256(sizeof(T) * (size_t)t->m * PB);
+  const size_t yb = align256(sizeof(T) * (size_t)t->n * QBmax);
+  const size_t pb = align256(sizeof(T) * (size_t)t->m1.nslots * PB * QBmax);
+  DevBuf own;
+  unsigned char* base = nullptr;
+  if (fx) {
+    if (xb + yb + pb > fx->fixed_bytes)
+      return fail(BKS_EUNSUPPORTED, "mode-1 contraction needs " + std::to_string(xb + yb + pb) +
+                                        " bytes of scratch, above the fixed " +
+                                        std::to_string(fx->fixed_bytes) + " bytes");
+    base = fx->fixed;
+  } else {
+    BKS_TRY(own.alloc(xb + yb + pb, s));
+    base = static_cast<unsigned char*>(own.p);
+  }
+  T* Xp = reinterpret_cast<T*>(base);
+  T* Yp = reinterpret_cast<T*>(base + xb);
+  T* part = t->m1.nslots > 0 ? reinterpret_cast<T*>(base + xb + yb) : nullptr;
+  BKS_TRY((pack_into<T, IT>(X, ldx, t->m, p, PB, Xp, s)));
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
     const int QB = bucket_t<T>(qq);
-    DevBuf Yp;
-    BKS_TRY((pack<T, IT>(Y + ldy * q0, ldy, t->n, qq, QB, Yp, s)));
+    // stream order: the previous chunk's kernels have read Yp and the
+    // partial sums before this pack overwrites them
+    BKS_TRY((pack_into<T, IT>(Y + ldy * q0, ldy, t->n, qq, QB, Yp, s)));
     // columns a + p*(q0 + b) of the full output start at column p*q0
     BKS_TRY((dispatch<T, OT>(t->m1, t->vdtype, t->m1.c1.as<int32_t>(), t->m1.c0.as<int32_t>(),
-                        Xp.as<T>(), PB, Yp.as<T>(), QB, false, p, qq,
-                        out + ldo * (p * q0), ldo, s)));
+                             Xp, PB, Yp, QB, false, p, qq, out + ldo * (p * q0), ldo, s, part)));
   }
   return BKS_OK;
+}
+
+template <typename T>
+size_t mode1_scratch_bytes(const bks_tensor* t, int p, int q) {
+  const int PB = bucket_t<T>(p);
+  const int QBmax = bucket_t<T>(std::min(PB == 8 ? 4 : 8, q));
+  return align256(sizeof(T) * (size_t)t->m * PB) + align256(sizeof(T) * (size_t)t->n * QBmax) +
+         align256(sizeof(T) * (size_t)t->m1.nslots * PB * QBmax);
 }
 
 template <typename T, typename IT, typename OT>
@@ -752,16 +810,20 @@ int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* 
   const size_t smem = std::max(sizeof(T) * 2 * (size_t)batch * KP,
                                sizeof(T) * (size_t)ngroups * ntiles * 16);
   auto kern = big ? k_core_chunks<T, 3> : k_core_chunks<T, 1>;
-  // The shared-memory limit is raised once per kernel to the largest size
-  // any call asks for (k1 <= 128: 64 KB of staged rows, or 528 tiles of 16
-  // accumulators), so that calls from several host threads never lower it
-  // under one another (a thread-safe static initialisation).
+  // The shared-memory limit is raised once per kernel and device to the
+  // largest size any call asks for (k1 <= 128: 64 KB of staged rows, or 528
+  // tiles of 16 accumulators), so that calls from several host threads
+  // never lower it under one another.
   constexpr size_t kSmemMax = std::max<size_t>(64 * 1024, sizeof(T) * 16 * (32 * 33 / 2));
-  static const cudaError_t attr1 = cudaFuncSetAttribute(
-      k_core_chunks<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-  static const cudaError_t attr3 = cudaFuncSetAttribute(
-      k_core_chunks<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-  if (attr1 != cudaSuccess || attr3 != cudaSuccess)
+  static PerDeviceOnce once;
+  const cudaError_t attr = once.run([] {
+    cudaError_t e = cudaFuncSetAttribute(k_core_chunks<T, 1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_core_chunks<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemMax);
+  });
+  if (attr != cudaSuccess)
     return fail(BKS_ECUDA, "k_core_chunks shared-memory limit not accepted");
   if (smem > kSmemMax) return fail(BKS_EUNSUPPORTED, "core: shared-memory tile above its limit");
   kern<<<nch, kCoreThreads, smem, s>>>(cp.lo.as<int32_t>(), cp.hi.as<int32_t>(), P.c0.as<int32_t>(),
@@ -911,24 +973,21 @@ extern "C" int bks_core(const bks_tensor* t, const void* U, int64_t ldu, int r1,
 // the packed row-major copies of X and Y and the partial sums of long rows --
 // in one file-scope device array of fixed size instead of allocating it.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace bks {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (host code only sees a stand-in symbol, not a device address).
+// per device with that device current (host code only sees a stand-in
+// symbol, not a device address).
 int noalloc_scratch(unsigned char** out) {
-  int dev = 0;
-  BKS_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return fail(BKS_EUNSUPPORTED, "device index too large");
+  const int dev = current_device();
+  if (dev < 0) return fail(BKS_EUNSUPPORTED, "no current device, or a device index above 63");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
@@ -939,88 +998,21 @@ int noalloc_scratch(unsigned char** out) {
   return BKS_OK;
 }
 
-inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-template <typename T, typename OT, int PB, int QB, bool TRI>
-int launch_contract_fixed(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib,
-                          const T* Ap, const T* Bp, int p, int q, OT* out,
-                          int64_t ldo, T* partial, cudaStream_t s) {
-  TileArgs ta{P.vitems.as<int4>(), P.vorder.as<int32_t>(), P.vptr.as<int32_t>(),
-              P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib,
-              sell_of(P, ia), sell_of(P, ib)};
-  const int warps = kWarpsPerBlock;
-  const int blocks = (plan_warps(P) + warps - 1) / warps;
-  if (P.nv > 0) {
-    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype),
-                                                                 sell_values_of<T>(P), Ap,
-                                                                 Bp, p, q, out, ldo,
-                                                                 partial); ::bks::note_launch();
-    BKS_CUDA_TRY(cudaGetLastError());
-  }
-  if (P.nsplit > 0) {
-    k_split_reduce<T, OT, PB, QB, TRI><<<P.nsplit, 256, 0, s>>>(
-        P.split_row.as<int32_t>(), P.split_first.as<int32_t>(), P.nsplit, partial, p, q, out,
-        ldo); ::bks::note_launch();
-    BKS_CUDA_TRY(cudaGetLastError());
-  }
-  if (P.nempty > 0) {
-    const int w = p * q;
-    k_zero_rows<OT><<<grid_for((int64_t)P.nempty * w), 256, 0, s>>>(P.empty_rows.as<int32_t>(),
-                                                                    P.nempty, w, out, ldo); ::bks::note_launch();
-    BKS_CUDA_TRY(cudaGetLastError());
-  }
-  return BKS_OK;
-}
-
-template <typename T>
-int dispatch_fixed(const Part& P, int vdtype, const T* Ap, int PB, const T* Bp, int QB,
-                   int p, int q, T* out, int64_t ldo, T* partial, cudaStream_t s) {
-  const int32_t* ia = P.c1.as<int32_t>();
-  const int32_t* ib = P.c0.as<int32_t>();
-#define BKS_FIXED_CASE(pb, qb)                                                               \
-  if (PB == pb && QB == qb)                                                                  \
-    return launch_contract_fixed<T, T, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, \
-                                                      out, ldo, partial, s);
-  BKS_FIXED_CASE(2, 2) BKS_FIXED_CASE(2, 4) BKS_FIXED_CASE(2, 8) BKS_FIXED_CASE(4, 2)
-  BKS_FIXED_CASE(4, 4) BKS_FIXED_CASE(4, 8) BKS_FIXED_CASE(8, 2) BKS_FIXED_CASE(8, 4)
-#undef BKS_FIXED_CASE
-  return fail(BKS_EUNSUPPORTED, "contraction bucket not instantiated");
-}
-
+// The allocating path's own code with its temporaries in the fixed array:
+// the same buckets, kernels and summation order, hence the same bits.
 template <typename T>
 int mode1_noalloc_typed(const bks_tensor* t, const T* X, int64_t ldx, int p, const T* Y,
                         int64_t ldy, int q, T* out, int64_t ldo, cudaStream_t s) {
-  const int PB = bucket(p);
-  const int qchunk = PB == 8 ? 4 : 8;
-  const int QBmax = bucket(std::min(qchunk, q));
-  const Part& P = t->m1;
-  // scratch layout: [Xp: m x PB][Yp: n x QB][piece partials: nslots x PB*QB]
-  const size_t xb = align256(sizeof(T) * (size_t)t->m * PB);
-  const size_t yb = align256(sizeof(T) * (size_t)t->n * QBmax);
-  const size_t pbytes = align256(sizeof(T) * (size_t)P.nslots * PB * QBmax);
-  const size_t need = xb + yb + pbytes;
+  const size_t need = mode1_scratch_bytes<T>(t, p, q);
   if (need > kNoAllocScratchBytes)
     return fail(BKS_EUNSUPPORTED,
                 "bks_contract_mode1_noalloc: needs " + std::to_string(need) +
                     " bytes of scratch, above the fixed " +
                     std::to_string(kNoAllocScratchBytes) + " bytes");
-  unsigned char* base = nullptr;
-  BKS_TRY(noalloc_scratch(&base));
-  T* Xp = reinterpret_cast<T*>(base);
-  T* Yp = reinterpret_cast<T*>(base + xb);
-  T* partial = reinterpret_cast<T*>(base + xb + yb);
-  k_pack<T, T><<<grid_for(t->m), 256, 0, s>>>(X, ldx, t->m, p, PB, Xp); ::bks::note_launch();
-  BKS_CUDA_TRY(cudaGetLastError());
-  for (int q0 = 0; q0 < q; q0 += qchunk) {
-    const int qq = std::min(qchunk, q - q0);
-    const int QB = bucket(qq);
-    // stream order: the previous chunk's kernels finish reading Yp first
-    k_pack<T, T><<<grid_for(t->n), 256, 0, s>>>(Y + ldy * q0, ldy, t->n, qq, QB, Yp); ::bks::note_launch();
-    BKS_CUDA_TRY(cudaGetLastError());
-    BKS_TRY(dispatch_fixed<T>(P, t->vdtype, Xp, PB, Yp, QB, p, qq, out + ldo * (p * q0),
-                              ldo, partial, s));
-  }
-  return BKS_OK;
+  Mode1Scratch fx;
+  BKS_TRY(noalloc_scratch(&fx.fixed));
+  fx.fixed_bytes = kNoAllocScratchBytes;
+  return mode1_typed<T, T, T>(t, X, ldx, p, Y, ldy, q, out, ldo, s, &fx);
 }
 
 }  // namespace

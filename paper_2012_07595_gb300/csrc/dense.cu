@@ -454,12 +454,14 @@ int launch_ts(const double* Q, int64_t ldq, int K, const double* B, int64_t ldb,
               const double* Mq, const double* Mb, int bo, int update, double* Out, int64_t ldo,
               int gram, double* gpart, int64_t m, int grid, cudaStream_t s) {
   const size_t smem = ts_smem<CU, CG>(K, b);
-  // the shared-memory limit is raised once per kernel, to the largest tile
-  // any call stages (a thread-safe static initialisation: the batch and
-  // serving workers launch these kernels from several host threads)
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      k_ts_pass<CU, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)ts_smem<CU, CG>(kMaxK, kMaxB));
+  // the shared-memory limit is raised once per kernel and device, to the
+  // largest tile any call stages (the batch and serving workers launch
+  // these kernels from several host threads)
+  static PerDeviceOnce once;
+  const cudaError_t attr = once.run([] {
+    return cudaFuncSetAttribute(k_ts_pass<CU, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ts_smem<CU, CG>(kMaxK, kMaxB));
+  });
   if (attr != cudaSuccess)
     return fail(BKS_ECUDA, std::string("k_ts_pass shared-memory limit: ") + cudaGetErrorString(attr));
   k_ts_pass<CU, CG><<<grid, kTSThreads, smem, s>>>(Q, ldq, K, B, ldb, b, Mq, Mb, bo, update, Out,

@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_coop(CoopArgs a) {
     if (threadIdx.x == 0) {
       a.info[0] = a.ctl[0];
       a.info[1] = a.ctl[1];
-      a.info[2] = done + a.init_sweeps;
+      a.info[2] = done + (hosvd_won ? a.init_sweeps : 0);
       a.info[3] = hosvd_won ? 1.0 : 0.0;
     }
   }
@@ -692,11 +692,15 @@ struct InnerWork {
 // their negatives (for the restart combine) and info[4] = {grad, ||F||,
 // sweeps, hosvd_won} on the device.
 int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int max_inner,
-                double* Uh, double* Wh, double* negU, double* negW, double* info,
+                int init_sweeps, double* Uh, double* Wh, double* negU, double* negW, double* info,
                 cudaStream_t s) {
   if (k1 > 128 || k3 > 128) return fail(BKS_EUNSUPPORTED, "inner solve: k1, k3 must be <= 128");
   if (r1 > kMaxR || r3 > kMaxR) return fail(BKS_EUNSUPPORTED, "inner solve: r1, r3 must be <= 8");
-  static thread_local InnerWork w;
+  // workspace of the calling thread on the current device
+  static thread_local InnerWork ws_by_dev[kMaxDevices];
+  const int dev = current_device();
+  if (dev < 0) return fail(BKS_EUNSUPPORTED, "inner solve: device index above 63");
+  InnerWork& w = ws_by_dev[dev];
   const int nparts = std::min(64, std::max(k1, k3));
   const size_t p1 = sizeof(float) * (size_t)nparts * k1 * k1, p3 = sizeof(float) * (size_t)nparts * k3 * k3;
   if (w.part1.bytes < p1) BKS_TRY(w.part1.alloc(p1, s));
@@ -713,10 +717,12 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   const int nmax = std::max(k1, k3);
   // A, V (nmax^2 each), red (64), cs (the one-warp Jacobi needs 128)
   const size_t hs = sizeof(float) * (2 * (size_t)nmax * nmax + 64 + std::max<size_t>(128, 4 * (size_t)nmax));
-  // raised once, to the size at k1 = 128 (a thread-safe static initialisation)
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      k_hosvd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)(sizeof(float) * (2 * 128 * 128 + 64 + 4 * 128)));
+  // raised once per device, to the size at k1 = 128
+  static PerDeviceOnce once;
+  const cudaError_t attr = once.run([] {
+    return cudaFuncSetAttribute(k_hosvd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(float) * (2 * 128 * 128 + 64 + 4 * 128)));
+  });
   if (attr != cudaSuccess)
     return fail(BKS_ECUDA, std::string("k_hosvd shared-memory limit: ") + cudaGetErrorString(attr));
   k_hosvd<<<2, kInnerThreads, hs, s>>>(w.part1.as<float>(), w.part3.as<float>(), nparts, k1, k3,
@@ -748,7 +754,7 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(w.coop_grid, (work + 511) / 512));
   CoopArgs a;
   a.C = C; a.k1 = k1; a.k3 = k3; a.r1 = r1; a.r3 = r3; a.tol = tol; a.max_inner = max_inner;
-  a.init_sweeps = 0; a.Uh0 = w.Uh0.as<double>(); a.Wh0 = w.Wh0.as<double>();
+  a.init_sweeps = std::max(0, init_sweeps); a.Uh0 = w.Uh0.as<double>(); a.Wh0 = w.Wh0.as<double>();
   a.Ug = w.Ug.as<double>(); a.Wg = w.Wg.as<double>(); a.Ub = w.Ub.as<double>();
   a.Wb = w.Wb.as<double>(); a.D = w.D.as<double>(); a.E = w.E.as<double>();
   a.T1 = w.T1.as<double>(); a.T3 = w.T3.as<double>(); a.ctl = w.ctl.as<double>();

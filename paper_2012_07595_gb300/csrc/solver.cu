@@ -16,6 +16,7 @@ namespace {
 
 constexpr int kBasisCap = 128;   // k1, k3 <= 128 (inner solve limit)
 constexpr int kBlockMax = 32;    // columns of one contraction result
+constexpr int kInnerStartSweeps = 5;  // HOOI sweeps after the HOSVD start (Section 6.2)
 
 __global__ void k_f3w(const double* __restrict__ H1, int r1, int r3, double* __restrict__ F3wT) {
   // F3wT (w3 x r3, ld w3): row tri(a,b), column c = w_ab F[a,b,c], F[a,b,c] = H1[a + r1(b + r1 c)]
@@ -350,18 +351,20 @@ struct BksState {
     last_k3 = k3;
     BKS_TRY(core());
     BKS_CUDA_TRY(cudaEventRecord(ev[0], s));
-    // inner tolerance: a tenth of the outer one unless given, so that the
-    // inner residual gradient does not hold the outer test just above tol
-    // (the inner test is ||grad_C|| / ||F_C||; with the scale-free outer
-    // test the tolerance is carried over through ||F||)
+    // inner tolerance (the inner test is ||grad_C|| / ||F_C||; with the
+    // scale-free outer test the tolerance is carried over through ||F||).
+    // BKS_INNER_PAPER (Section 6.2): the truncated HOSVD start gets 5 HOOI
+    // sweeps and the inner problem is solved to the outer criterion.
+    // BKS_INNER_FAST: no start sweeps and an inexact inner solve, a hundred
+    // times below the current outer gradient and at least a tenth of the
+    // outer tolerance.  inner_tol > 0 replaces either tolerance.
     const double otol = P.tol_scale_free ? cur_tol * last_nf : cur_tol;
-    // inexact inner solves: a hundred times below the current outer
-    // gradient, and at least a tenth of the outer tolerance (this library's
-    // reading; Section 6.2 uses the outer tolerance throughout)
-    const double itol = P.inner_tol > 0 ? P.inner_tol : std::max(0.1 * otol, 0.01 * last_grad_rel);
-    BKS_TRY(inner_solve(C.as<double>(), k1, k3, r1, r3, itol, P.max_inner, Uh.as<double>(),
-                        Wh.as<double>(), negU.as<double>(), negW.as<double>(),
-                        inner_info.as<double>(), s));
+    const bool fast = P.inner_schedule == BKS_INNER_FAST;
+    const double itol = P.inner_tol > 0 ? P.inner_tol
+                        : fast ? std::max(0.1 * otol, 0.01 * last_grad_rel) : otol;
+    BKS_TRY(inner_solve(C.as<double>(), k1, k3, r1, r3, itol, P.max_inner,
+                        fast ? 0 : kInnerStartSweeps, Uh.as<double>(), Wh.as<double>(),
+                        negU.as<double>(), negW.as<double>(), inner_info.as<double>(), s));
     BKS_CUDA_TRY(cudaEventRecord(ev[1], s));
     // U0 <- X Uh, W0 <- Z Wh (eq. (tks1)), in place in the first columns
     BKS_TRY(ts_combine(Xp(), m, k1, nullptr, m, 0, negU.as<double>(), nullptr, r1, Xp(), m, m,
@@ -389,6 +392,8 @@ int check_params(const bks_tensor* t, const bks_params* p) {
     return fail(BKS_EINVAL, "unknown variant");
   if (p->precision != BKS_PREC_FP64 && p->precision != BKS_PREC_MIXED)
     return fail(BKS_EINVAL, "unknown precision");
+  if (p->inner_schedule != BKS_INNER_PAPER && p->inner_schedule != BKS_INNER_FAST)
+    return fail(BKS_EINVAL, "unknown inner schedule");
   return BKS_OK;
 }
 
@@ -415,6 +420,7 @@ extern "C" void bks_params_default(bks_params* p) {
   p->drop_tol = 1e-14;
   p->inner_tol = 0.0;
   p->mixed_tol = 1e-4;
+  p->inner_schedule = BKS_INNER_PAPER;
 }
 
 extern "C" void hooi_params_default(hooi_params* p) {
@@ -427,6 +433,7 @@ extern "C" void hooi_params_default(hooi_params* p) {
   p->grad_every = 10;
   p->precision = BKS_PREC_FP64;
   p->seed = 1;
+  p->mixed_tol = 1e-4;
 }
 
 namespace bks {
@@ -617,7 +624,15 @@ extern "C" int hooi_solve(const bks_tensor* t, const hooi_params* prm, const dou
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t m = t->m, n = t->n;
-  const bool fp32 = prm->precision == BKS_PREC_MIXED;
+  if (prm->precision != BKS_PREC_FP64 && prm->precision != BKS_PREC_MIXED)
+    return fail(BKS_EINVAL, "unknown precision");
+  // mixed precision: FP32 contractions until the FP32-evaluated gradient is
+  // below mixed_tol (scale-free) or stops halving, then FP64 to the end
+  bool fp32 = prm->precision == BKS_PREC_MIXED;
+  const double mtol = prm->mixed_tol > 0 ? prm->mixed_tol : 1e-4;
+  double best_sf = INFINITY;
+  int stall = 0, fp32_iters = 0;
+  bool force_check = false;
   const int w1 = r1 * r3, w3 = r1 * (r1 + 1) / 2;
   DenseWork ws;
   DevBuf Ub, Wb, T1, T3, T3c, G, FT, FF, FT3, FF3, sc, gout, gout3;
@@ -654,7 +669,9 @@ extern "C" int hooi_solve(const bks_tensor* t, const hooi_params* prm, const dou
   int hist_len = 0;
   for (;; ++it) {
     BKS_TRY(contract_mode1_x(t, Up, m, r1, Wp, n, r3, T1.as<double>(), m, fp32, s));
-    if (it % every == 0 || it >= prm->max_iter) {
+    if (fp32) ++fp32_iters;
+    if (it % every == 0 || it >= prm->max_iter || force_check) {
+      force_check = false;
       // mode 1: F1 = U^T T1, gradient T1 F1^T - U (F1 F1^T)
       BKS_TRY(ts_gram(Up, m, r1, T1.as<double>(), m, w1, m, G.as<double>(), ws, s));
       k_hooi_small<<<1, 128, 0, s>>>(G.as<double>(), r1, w1, FT.as<double>(), FF.as<double>(),
@@ -683,7 +700,21 @@ extern "C" int hooi_solve(const bks_tensor* t, const hooi_params* prm, const dou
         ++hist_len;
       }
       if (!std::isfinite(grad)) return fail(BKS_ENUMERIC, "NaN or Inf in the gradient");
-      if (rel <= prm->tol) { converged = true; break; }
+      if (fp32) {
+        const double sf = nf > 0 ? grad / (nf * nf) : INFINITY;
+        if (sf < 0.5 * best_sf) { best_sf = sf; stall = 0; } else ++stall;
+        if (sf <= mtol || stall >= 2 || rel <= prm->tol) {
+          // FP64 from here on: the contractions at the current point again,
+          // and the gradient test on them at the next iteration
+          fp32 = false;
+          force_check = true;
+          BKS_TRY(make_t3());
+          --fp32_iters;
+          continue;
+        }
+      } else {
+        if (rel <= prm->tol) { converged = true; break; }
+      }
       if (it >= prm->max_iter) break;
     }
     // U <- r1 leading left singular vectors of T1; W from the new U
@@ -707,7 +738,7 @@ extern "C" int hooi_solve(const bks_tensor* t, const hooi_params* prm, const dou
     info->k1 = r1;
     info->k3 = r3;
     info->inner_sweeps = 0;
-    info->fp32_iters = fp32 ? it : 0;
+    info->fp32_iters = fp32_iters;
     for (int q = 0; q < 5; ++q) info->phase_ms[q] = 0.0;
     info->history_len = hist_len;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

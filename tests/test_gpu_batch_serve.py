@@ -42,6 +42,25 @@ def _determined(F, mode):
     return sv[-1] > 1e-6 * sv[0]
 
 
+def _oracle_check(c, U, W, F, normF, tol):
+    """Properties the oracle evaluates at a returned point (Algorithm 5's
+    result): orthonormal U and W, F = A.(U,U,W) (eq. (Rayleigh)) and
+    ||F|| as reported, F symmetric in its first two modes, ||F|| <= ||A||,
+    and the scale-free G-gradient (Section 2.5) within twice the
+    tolerance."""
+    A = O.symmetrise(c.m, c.n, c.i, c.j, c.k, c.v)
+    U, W, F = np.asarray(U), np.asarray(W), np.asarray(F)
+    r1, r3 = U.shape[1], W.shape[1]
+    assert np.abs(U.T @ U - np.eye(r1)).max() < 1e-12
+    assert np.abs(W.T @ W - np.eye(r3)).max() < 1e-12
+    gg, nf, Fo = O.gradient_global(A, U, W)
+    assert abs(nf - normF) <= 1e-10 * nf
+    assert np.allclose(F, Fo, rtol=0, atol=1e-10 * nf)
+    assert np.allclose(Fo, Fo.transpose(1, 0, 2), rtol=0, atol=1e-12 * nf)
+    assert nf ** 2 <= A.fro2() * (1 + 1e-12)
+    assert gg / nf ** 2 <= 2 * tol, (gg / nf ** 2, tol)
+
+
 def _same_solution(a, b, Fa):
     assert abs(a["normF"] - b["normF"]) <= 1e-9 * a["normF"]
     if _determined(Fa, 0):
@@ -90,6 +109,8 @@ def test_batch_matches_solo():
     for q, (T, p) in enumerate(zip(tens, params)):
         U, W, F, info, st = res[q]
         assert st in (bk.BKS_OK,), (q, st)
+        _oracle_check(jobs[q][1], U.cpu().numpy(), W.cpu().numpy(), F.cpu().numpy(),
+                      info["normF"], p.tol)
         Us, Ws, Fs, infos = bk.bks_solve(T, p)
         _same_solution({"U": Us.cpu().numpy(), "W": Ws.cpu().numpy(), "normF": infos["normF"]},
                        {"U": U.cpu().numpy(), "W": W.cpu().numpy(), "normF": info["normF"]},
@@ -120,9 +141,10 @@ def test_server_alone_equals_in_mix_and_failure_paths():
         out = [srv.poll(t, wait=True) for t in tickets]
         rb = srv.poll(bad, wait=True)
         assert rb["status"] == bk.BKS_EINVAL
-        for r in out:
+        for (j, c), r in zip(jobs, out):
             assert r["status"] == bk.BKS_OK, r["error"]
             assert r["latency_s"] > 0
+            _oracle_check(c, r["U"], r["W"], r["F"], r["normF"], 1e-9)
         for a, b in zip(alone, out[:4]):
             _same_solution(a, b, a["F"])
         assert srv.stats()["running"] == 0

@@ -129,12 +129,34 @@ def test_core_fp32_within_summation_bound(r1, r3):
 
 
 def test_ragged_widths_and_leading_dimensions():
+    """Operands and outputs with a leading dimension above their row count
+    (column-major views into larger buffers) go through the C ABI as they
+    are: the binding passes the view's stride as ld, without a copy."""
     import torch
     bk, A, T = _setup("uniform_small")
     g = synth.rng(16)
-    Xbig = torch.tensor(g.standard_normal((A.m + 5, 7)), device="cuda")
-    X = Xbig[: A.m, 1:4]              # ld = m + 5... column-major requires a copy
-    Y = torch.tensor(g.standard_normal((A.n, 3)), device="cuda")
-    got = bk.bks_contract_mode1(T, X, Y)
-    ref = O.mode1(A, X.cpu().numpy(), Y.cpu().numpy())
-    assert rel_err(got.cpu().numpy(), ref) < 1e-13
+    Xbig = torch.tensor(g.standard_normal((7, A.m + 5)), device="cuda").t()   # ld = m + 5
+    X = Xbig[: A.m, 1:4]
+    Ybig = torch.tensor(g.standard_normal((5, A.n + 3)), device="cuda").t()   # ld = n + 3
+    Y = Ybig[: A.n, :3]
+    assert X.stride() == (1, A.m + 5) and Y.stride() == (1, A.n + 3)
+    assert bk.col_major(X).data_ptr() == X.data_ptr()
+    Obig = torch.full((12, A.m + 9), float("nan"), device="cuda", dtype=torch.float64).t()
+    out = Obig[: A.m, 1:10]
+    bk.bks_contract_mode1(T, X, Y, out=out)
+    Xh, Yh = X.cpu().numpy(), Y.cpu().numpy()
+    ref = O.mode1(A, Xh, Yh)
+    assert rel_err(out.cpu().numpy(), ref) < 1e-13
+    # the padding rows and columns of the output buffer are untouched
+    ob = Obig.cpu().numpy()
+    assert np.all(np.isnan(ob[A.m:, :])) and np.all(np.isnan(ob[:, 0])) and np.all(np.isnan(ob[:, 10:]))
+    O3big = torch.full((8, A.n + 4), float("nan"), device="cuda", dtype=torch.float64).t()
+    out3 = O3big[: A.n, :6]
+    bk.bks_contract_mode3(T, X, out=out3)
+    assert rel_err(out3.cpu().numpy(), O.mode3(A, Xh)) < 1e-13
+    out3f = O3big[: A.n, 2:8]                    # p = 2, q = 3: six columns
+    X2 = Xbig[: A.m, 4:7]
+    bk.bks_contract_mode3(T, X[:, :2], X2, out=out3f)
+    assert rel_err(out3f.cpu().numpy(), O.mode3(A, Xh[:, :2], X2.cpu().numpy())) < 1e-13
+    F = bk.bks_core(T, X, Y).cpu().numpy()
+    assert rel_err(F, O.core(A, Xh, Yh)) < 1e-12
