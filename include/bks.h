@@ -136,10 +136,12 @@ int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
  *   Scratch (the packed copies of X and Y and the partial sums of long
  *   rows) lives in a fixed 32 MiB device array inside the library, which
  *   every GPU that loads the library keeps until the process exits.  A call
- *   needs s*(PB*m + QB*n + PB*QB*nslots) bytes, each of the three pieces
- *   rounded up to 256 bytes, with s = 8 (BKS_F64) or 4 (BKS_F32); PB is p
- *   padded to 2, 4 or 8 (3 stays 3 in FP64), QB likewise for min(q, 8), or
- *   for min(q, 4) when PB = 8; nslots is the number of pieces into which
+ *   needs s*(SP*m + SQ*n + PB*QB*nslots) bytes, each of the three pieces
+ *   rounded up to 256 bytes, with s = 8 (BKS_F64) or 4 (BKS_F32); PB is the
+ *   width bucket of p (1 -> 2; 2, 3, 4, 5 as they are; 6..8 -> 8), QB that
+ *   of min(q, 8), or of min(q, 5) when PB = 5 and min(q, 4) when PB = 8; SP,
+ *   SQ are the packed row strides (FP32: 2 for width 2, 4 for 3 and 4, 8
+ *   for 5 and 8; FP64: the width itself); nslots is the number of pieces into which
  *   rows longer than the work plan's split (512 below 8M stored entries,
  *   1024 below 32M, 2048 from 32M, unless bks_tensor_autotune / set_tiles
  *   chose another) are cut, about nnz / split on power-law tensors.  The

@@ -47,16 +47,57 @@ __global__ void k_pack(const IT* __restrict__ X, int64_t ldx, int64_t rows, int 
   }
 }
 
+// Row stride of a packed operand of (bucket) width N: FP32 rows are padded
+// to 2, 4 or 8 values so that a row is one or two aligned vector loads (a
+// 3-wide row is one float4, a 5-wide row one float4 and one float); FP64
+// rows keep 3 and 5 values (those kernels are bound by the FP64 pipe, not
+// by loads).
+template <typename T, int N>
+struct RowStride {
+  static constexpr int v = sizeof(T) == 4 ? (N <= 2 ? 2 : N <= 4 ? 4 : 8) : N;
+};
+template <typename T> inline int row_stride(int N) {
+  return sizeof(T) == 4 ? (N <= 2 ? 2 : N <= 4 ? 4 : 8) : N;
+}
+
+// The first N values of a packed row (stride RowStride<T, N>): one 32-byte
+// load for 8-float rows, 16-byte vector loads when rows are 16-byte aligned
+// (the unused tail of the last vector is padding of the row), else 8-byte
+// loads for FP32, else scalar.
+// One 32-byte row (8 floats, 32-byte aligned) by a single 256-bit load
+// (sm_100 and later): one request per gathered row instead of two.
+__device__ __forceinline__ void ldg_v8(const float* __restrict__ p, float (&v)[8]) {
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                 "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+
 template <typename T, int N>
 __device__ __forceinline__ void load_row(const T* __restrict__ base, T (&x)[N]) {
-  // 8/16-byte vector loads of a padded row
-  if constexpr (sizeof(T) * N % 16 == 0) {
+  constexpr int S = RowStride<T, N>::v;
+  if constexpr (sizeof(T) == 4 && S == 8) {
+    float v[8];
+    ldg_v8(reinterpret_cast<const float*>(base), v);
 #pragma unroll
-    for (int t = 0; t < (int)(sizeof(T) * N / 16); ++t) {
-      float4 q = __ldg(reinterpret_cast<const float4*>(base) + t);
+    for (int u = 0; u < N; ++u) x[u] = v[u];
+  } else if constexpr ((sizeof(T) * S) % 16 == 0) {
+    constexpr int V = (int)(16 / sizeof(T));
+    constexpr int NV = (N + V - 1) / V;  // NV V <= S: S is a multiple of V and S >= N
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(base) + t);
       const T* qq = reinterpret_cast<const T*>(&q);
 #pragma unroll
-      for (int u = 0; u < (int)(16 / sizeof(T)); ++u) x[t * (16 / sizeof(T)) + u] = qq[u];
+      for (int u = 0; u < V; ++u)
+        if (t * V + u < N) x[t * V + u] = qq[u];
+    }
+  } else if constexpr (sizeof(T) == 4 && S % 2 == 0) {
+#pragma unroll
+    for (int t = 0; t < N / 2; ++t) {
+      const float2 q = __ldg(reinterpret_cast<const float2*>(base) + t);
+      x[2 * t] = q.x;
+      x[2 * t + 1] = q.y;
     }
   } else {
 #pragma unroll
@@ -114,8 +155,8 @@ __device__ __forceinline__ void one_entry(int e, const int32_t* __restrict__ iap
   const int ib = __ldg(ibp + e);
   const T v = __ldg(vals + e);
   T xa[PB], xb[NB];
-  load_row<T, PB>(Ap + (int64_t)ia * PB, xa);
-  load_row<T, NB>(Bp + (int64_t)ib * NB, xb);
+  load_row<T, PB>(Ap + (int64_t)ia * RowStride<T, PB>::v, xa);
+  load_row<T, NB>(Bp + (int64_t)ib * RowStride<T, NB>::v, xb);
   accumulate<T, PB, QB, TRI>(acc, v, xa, xb);
 }
 
@@ -277,8 +318,8 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ svals,
       T xa[4][PB], xb[4][NB];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        load_row<T, PB>(Ap + (int64_t)iav[u] * PB, xa[u]);
-        load_row<T, NB>(Bp + (int64_t)ibv[u] * NB, xb[u]);
+        load_row<T, PB>(Ap + (int64_t)iav[u] * RowStride<T, PB>::v, xa[u]);
+        load_row<T, NB>(Bp + (int64_t)ibv[u] * RowStride<T, NB>::v, xb[u]);
       }
       T vc[4] = {v[0], v[1], v[2], v[3]};
       x += 128;
@@ -316,8 +357,8 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ svals,
     T xa[4][PB], xb[4][NB];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      load_row<T, PB>(Ap + (int64_t)iav[u] * PB, xa[u]);
-      load_row<T, NB>(Bp + (int64_t)ibv[u] * NB, xb[u]);
+      load_row<T, PB>(Ap + (int64_t)iav[u] * RowStride<T, PB>::v, xa[u]);
+      load_row<T, NB>(Bp + (int64_t)ibv[u] * RowStride<T, NB>::v, xb[u]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, v[u], xa[u], xb[u]);
@@ -330,27 +371,45 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ svals,
 inline int plan_warps(const Part& P) { return P.nvec + (P.nshortv + 31) / 32; }
 
 
-// Rows cut into pieces: add the pieces' partial sums in a fixed order.
+// s + y into the unevaluated sum s + c, the rounding error of s + y going
+// to c (TwoSum, Knuth's error-free transformation: exact in IEEE
+// arithmetic, no FMA contraction involved).
+template <typename T>
+__device__ __forceinline__ void two_sum_acc(T& s, T& c, T y) {
+  const T t = s + y;
+  const T bp = t - s;
+  c += (s - (t - bp)) + (y - bp);
+  s = t;
+}
+
+// Rows cut into pieces: add the pieces' partial sums in a fixed order, with
+// TwoSum compensation at both levels (pieces into 256 / W group sums, the
+// group sums into one), so that the error of a cut row does not grow with
+// its number of pieces.
 template <typename T, typename OT, int PB, int QB, bool TRI>
 __global__ void k_split_reduce(const int32_t* __restrict__ split_row,
                                const int32_t* __restrict__ split_first, int nsplit,
                                const T* __restrict__ partial, int p, int q, OT* __restrict__ out,
                                int64_t ldo) {
   constexpr int W = Shape<PB, QB, TRI>::W;
-  __shared__ T sh[256];
+  __shared__ T sh[256], shc[256];
   const int s = blockIdx.x;
   if (s >= nsplit) return;
   const int f0 = split_first[s], f1 = split_first[s + 1];
   const int groups = 256 / W;
   const int c = threadIdx.x % W, g = threadIdx.x / W;
-  T acc = T(0);
+  T acc = T(0), cmp = T(0);
   if (g < groups)
-    for (int f = f0 + g; f < f1; f += groups) acc += partial[(int64_t)f * W + c];
+    for (int f = f0 + g; f < f1; f += groups) two_sum_acc(acc, cmp, partial[(int64_t)f * W + c]);
   sh[threadIdx.x] = acc;
+  shc[threadIdx.x] = cmp;
   __syncthreads();
   if (threadIdx.x < W) {
-    T tot = T(0);
-    for (int t = 0; t < groups; ++t) tot += sh[t * W + threadIdx.x];
+    T tot = T(0), tc = T(0);
+    for (int t = 0; t < groups; ++t) {
+      tc += shc[t * W + threadIdx.x];
+      two_sum_acc(tot, tc, sh[t * W + threadIdx.x]);
+    }
     const int64_t row = split_row[s];
     int col = -1;
     if constexpr (TRI) {
@@ -361,7 +420,7 @@ __global__ void k_split_reduce(const int32_t* __restrict__ split_row,
       int a = c % PB, b = c / PB;
       if (a < p && b < q) col = a + p * b;
     }
-    if (col >= 0) out[row + ldo * col] = (OT)tot;
+    if (col >= 0) out[row + ldo * col] = (OT)(tot + tc);
   }
 }
 
@@ -380,10 +439,14 @@ inline int grid_for(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 32));
 }
 
-inline int bucket(int x) { return x <= 2 ? 2 : (x <= 4 ? 4 : 8); }
-// The FP64 kernels are bound by the FP64 pipe, so a 3-column operand (rank
-// 3) is not padded to 4 there: 9 products per entry instead of 16.
-template <typename T> int bucket_t(int x) { return (sizeof(T) == 8 && x == 3) ? 3 : bucket(x); }
+// Width buckets of the kernels: 1 -> 2, 2..5 as they are, 6..8 -> 8.  The
+// kernels multiply only the bucket width (3 x 4 is 12 products per entry,
+// 5 x 5 is 25), whatever the row stride.
+inline int bucket(int x) { return x <= 2 ? 2 : (x <= 5 ? x : 8); }
+template <typename T> int bucket_t(int x) { return bucket(x); }
+// Columns of the second operand per kernel call: the accumulators of one
+// output row (PB x QB) stay at most 32.
+inline int qchunk_of(int PB) { return PB <= 4 ? 8 : (PB == 5 ? 5 : 4); }
 
 template <typename T> const T* values_of(const Part& P, int vdtype);
 template <typename T> const T* sell_values_of(const Part& P);
@@ -448,25 +511,17 @@ int dispatch(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib, co
   if (!tri && PB == pb && QB == qb)                                                           \
     return launch_contract<T, OT, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, out, ldo,   \
                                                  part, s);
-  BKS_CASE(2, 2) BKS_CASE(2, 4) BKS_CASE(2, 8) BKS_CASE(4, 2) BKS_CASE(4, 4) BKS_CASE(4, 8)
-  BKS_CASE(8, 2) BKS_CASE(8, 4)
-  if constexpr (sizeof(T) == 8) {
-    BKS_CASE(3, 2) BKS_CASE(3, 3) BKS_CASE(3, 4) BKS_CASE(3, 8) BKS_CASE(2, 3) BKS_CASE(4, 3)
-    BKS_CASE(8, 3)
-    if (tri && PB == 3)
-      return launch_contract<T, OT, 3, 3, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, part,
-                                                    s);
-  }
+  BKS_CASE(2, 2) BKS_CASE(2, 3) BKS_CASE(2, 4) BKS_CASE(2, 5) BKS_CASE(2, 8)
+  BKS_CASE(3, 2) BKS_CASE(3, 3) BKS_CASE(3, 4) BKS_CASE(3, 5) BKS_CASE(3, 8)
+  BKS_CASE(4, 2) BKS_CASE(4, 3) BKS_CASE(4, 4) BKS_CASE(4, 5) BKS_CASE(4, 8)
+  BKS_CASE(5, 2) BKS_CASE(5, 3) BKS_CASE(5, 4) BKS_CASE(5, 5)
+  BKS_CASE(8, 2) BKS_CASE(8, 3) BKS_CASE(8, 4)
 #undef BKS_CASE
-  if (tri && PB == 2)
-    return launch_contract<T, OT, 2, 2, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, part,
-                                                  s);
-  if (tri && PB == 4)
-    return launch_contract<T, OT, 4, 4, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, part,
-                                                  s);
-  if (tri && PB == 8)
-    return launch_contract<T, OT, 8, 8, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, part,
-                                                  s);
+#define BKS_TRI(pb)                                                                           \
+  if (tri && PB == pb)                                                                        \
+    return launch_contract<T, OT, pb, pb, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, part, s);
+  BKS_TRI(2) BKS_TRI(3) BKS_TRI(4) BKS_TRI(5) BKS_TRI(8)
+#undef BKS_TRI
   return fail(BKS_EUNSUPPORTED, "contraction bucket not instantiated");
 }
 
@@ -504,11 +559,11 @@ template <typename T, typename IT, typename OT>
 int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* Y, int64_t ldy,
                 int q, OT* out, int64_t ldo, cudaStream_t s, const Mode1Scratch* fx = nullptr) {
   const int PB = bucket_t<T>(p);
-  // keep PB*QB <= 32: split the Y columns into chunks of at most 4 when PB = 8
-  const int qchunk = PB == 8 ? 4 : 8;
+  // keep PB*QB <= 32: the Y columns in chunks of at most qchunk_of(PB)
+  const int qchunk = qchunk_of(PB);
   const int QBmax = bucket_t<T>(std::min(qchunk, q));
-  const size_t xb = align256(sizeof(T) * (size_t)t->m * PB);
-  const size_t yb = align256(sizeof(T) * (size_t)t->n * QBmax);
+  const size_t xb = align256(sizeof(T) * (size_t)t->m * row_stride<T>(PB));
+  const size_t yb = align256(sizeof(T) * (size_t)t->n * row_stride<T>(QBmax));
   const size_t pb = align256(sizeof(T) * (size_t)t->m1.nslots * PB * QBmax);
   DevBuf own;
   unsigned char* base = nullptr;
@@ -525,13 +580,13 @@ int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
   T* Xp = reinterpret_cast<T*>(base);
   T* Yp = reinterpret_cast<T*>(base + xb);
   T* part = t->m1.nslots > 0 ? reinterpret_cast<T*>(base + xb + yb) : nullptr;
-  BKS_TRY((pack_into<T, IT>(X, ldx, t->m, p, PB, Xp, s)));
+  BKS_TRY((pack_into<T, IT>(X, ldx, t->m, p, row_stride<T>(PB), Xp, s)));
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
     const int QB = bucket_t<T>(qq);
     // stream order: the previous chunk's kernels have read Yp and the
     // partial sums before this pack overwrites them
-    BKS_TRY((pack_into<T, IT>(Y + ldy * q0, ldy, t->n, qq, QB, Yp, s)));
+    BKS_TRY((pack_into<T, IT>(Y + ldy * q0, ldy, t->n, qq, row_stride<T>(QB), Yp, s)));
     // columns a + p*(q0 + b) of the full output start at column p*q0
     BKS_TRY((dispatch<T, OT>(t->m1, t->vdtype, t->m1.c1.as<int32_t>(), t->m1.c0.as<int32_t>(),
                              Xp, PB, Yp, QB, false, p, qq, out + ldo * (p * q0), ldo, s, part)));
@@ -542,8 +597,9 @@ int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
 template <typename T>
 size_t mode1_scratch_bytes(const bks_tensor* t, int p, int q) {
   const int PB = bucket_t<T>(p);
-  const int QBmax = bucket_t<T>(std::min(PB == 8 ? 4 : 8, q));
-  return align256(sizeof(T) * (size_t)t->m * PB) + align256(sizeof(T) * (size_t)t->n * QBmax) +
+  const int QBmax = bucket_t<T>(std::min(qchunk_of(PB), q));
+  return align256(sizeof(T) * (size_t)t->m * row_stride<T>(PB)) +
+         align256(sizeof(T) * (size_t)t->n * row_stride<T>(QBmax)) +
          align256(sizeof(T) * (size_t)t->m1.nslots * PB * QBmax);
 }
 
@@ -552,19 +608,19 @@ int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
                 int q, OT* out, int64_t ldo, cudaStream_t s) {
   const int PB = bucket_t<T>(p);
   DevBuf Xp;
-  BKS_TRY((pack<T, IT>(X, ldx, t->m, p, PB, Xp, s)));
+  BKS_TRY((pack<T, IT>(X, ldx, t->m, p, row_stride<T>(PB), Xp, s)));
   if (!X2)
     return dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
-                       Xp.as<T>(), PB, Xp.as<T>(), PB, true, p, p, out, ldo, s);
-  const int qchunk = PB == 8 ? 4 : 8;
+                           Xp.as<T>(), PB, Xp.as<T>(), PB, true, p, p, out, ldo, s);
+  const int qchunk = qchunk_of(PB);
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
     const int QB = bucket_t<T>(qq);
     DevBuf X2p;
-    BKS_TRY((pack<T, IT>(X2 + ldx2 * q0, ldx2, t->m, qq, QB, X2p, s)));
+    BKS_TRY((pack<T, IT>(X2 + ldx2 * q0, ldx2, t->m, qq, row_stride<T>(QB), X2p, s)));
     BKS_TRY((dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
-                        Xp.as<T>(), PB, X2p.as<T>(), QB, false, p, qq,
-                        out + ldo * (p * q0), ldo, s)));
+                             Xp.as<T>(), PB, X2p.as<T>(), QB, false, p, qq,
+                             out + ldo * (p * q0), ldo, s)));
   }
   return BKS_OK;
 }
