@@ -135,57 +135,162 @@ def start_matrices(m, n, r, seed=20):
 
 
 # ---------------------------------------------------------------------------
-def cpu_oracle_sample(coo, budget_s=20.0):
-    """The oracle as it stands on the host cores: one outer iteration of
-    Algorithm 5 (stage 1 + expansion + core + inner solve) on a row-sample of
-    the workload, scaled to solves/s by the GPU run's outer-iteration count.
-    The sample keeps the draws whose i and j fall in the first `frac` of the
-    permuted index range, so it has the same generator and value law."""
+def cpu_info():
+    """Host cores and CPU model (for the CPU-baseline records)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def count_stored(coo):
+    """Stored entries of the mirrored tensor (distinct (i, j, k) after adding
+    (j, i, k) for every i != j), counted from the input list."""
+    off = coo.i != coo.j
+    i = np.concatenate([coo.i, coo.j[off]]).astype(np.int64)
+    j = np.concatenate([coo.j, coo.i[off]]).astype(np.int64)
+    k = np.concatenate([coo.k, coo.k[off]]).astype(np.int64)
+    return int(np.unique((i * coo.m + j) * coo.n + k).size)
+
+
+SAMPLE_FRAC = 0.25
+
+
+def oracle_sample(coo, frac=SAMPLE_FRAC):
+    """The index sample of the workload: the draws whose i and j fall in the
+    first `frac` of the (uniformly permuted) index range, stored by the
+    oracle; same generator, same value law.  Returns (A, U0, W0)."""
     import oracle as O
     w = WORKLOAD
-    frac = 0.5
     mm = int(w["m"] * frac)
-    # rows of the sample: relabel indices < mm (the permutation is uniform)
     sel = (coo.i < mm) & (coo.j < mm)
-    sub = (coo.i[sel], coo.j[sel], coo.k[sel], coo.v[sel])
-    t0 = time.perf_counter()
-    A = O.symmetrise(mm, w["n"], *sub)
+    A = O.symmetrise(mm, w["n"], coo.i[sel], coo.j[sel], coo.k[sel], coo.v[sel])
     U0, W0 = start_matrices(mm, w["n"], w["r"])
-    t1 = time.perf_counter()
-    res = O.bks(A, U0, W0, s=w["stages"], p=w["block_p"], tol=0.0, max_outer=1)
-    t2 = time.perf_counter()
-    return {"seconds_per_outer_iter": t2 - t1, "ingest_s": t1 - t0, "nnz_sample": A.nnz,
-            "m_sample": mm, "threads": 1}
+    return A, U0, W0
+
+
+def oracle_outer_iteration(A, U0, W0):
+    """Seconds of one FP64 outer iteration of the oracle's Algorithm 5 (stage
+    1 with the gradient, the rest of the expansion, the core, the inner
+    solve on the Section 6.2 schedule, the restart) at the workload's
+    parameters."""
+    import oracle as O
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    O.bks(A, U0, W0, s=w["stages"], p=w["block_p"], tol=0.0, max_outer=1)
+    return time.perf_counter() - t0
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle on the host cores, same config and
-    metric (BKS solves/s), each step a bounded sample (one outer iteration
-    on a half-index row sample) extrapolated to a full solve."""
+    """--impl reference: the oracle on the host cores, same config and
+    metric (BKS solves/s).  A full oracle solve of the workload takes
+    minutes, so a step is one FP64 outer iteration on the index sample; the
+    rate is scaled by the stored-entry ratio (full workload counted from
+    its input list) and by the oracle's own outer-iteration count, measured
+    once by a full solve of the sample before the timed steps."""
+    import oracle as O
+    w = WORKLOAD
     coo = make_input()
-    outer_iters = 6  # outer iterations of an FP64 solve at this tolerance (the GPU FP64 solve's count)
+    nnz_full = count_stored(coo)
+    A, U0, W0 = oracle_sample(coo)
+    t0 = time.perf_counter()
+    res = O.bks(A, U0, W0, s=w["stages"], p=w["block_p"], tol=w["tol"],
+                scale_free=bool(w["tol_scale_free"]))
+    sample_solve_s = time.perf_counter() - t0
+    iters = max(1, res.iters)
     times = []
     for s in range(args.warmup + args.steps):
-        d = cpu_oracle_sample(coo)
+        t = oracle_outer_iteration(A, U0, W0)
         if s >= args.warmup:
-            times.append(d["seconds_per_outer_iter"])
+            times.append(t)
     t_iter = statistics.median(times)
-    nnz_full = 5_000_000  # stored entries of the full workload (measured by the GPU arm)
-    scale = nnz_full / max(1, d["nnz_sample"])
-    solve_s = t_iter * scale * outer_iters
-    value = 1.0 / solve_s
+    scale = nnz_full / max(1, A.nnz)
+    value = 1.0 / (t_iter * scale * iters)
+    info = cpu_info()
     line = {"metric": "BKS solves/s", "value": value, "unit": "solves/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": solve_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": t_iter * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD["workload"]},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one outer iteration on a {d['m_sample']}-row sample "
-                                       f"({d['nnz_sample']} stored), scaled by stored entries "
-                                       f"x {outer_iters} outer iterations"},
+                             "nproc": info["nproc"], "cpu_model": info["model"],
+                             "sample": f"step = one FP64 outer iteration of the oracle on the "
+                                       f"{int(SAMPLE_FRAC * 100)}%-index sample ({A.nnz} of "
+                                       f"{nnz_full} stored entries), single-threaded; rate "
+                                       f"scaled by stored entries and by the oracle's "
+                                       f"{iters} outer iterations to solve that sample "
+                                       f"({sample_solve_s:.1f} s, measured before the steps)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def cpu_baseline_leg(coo, nnz_full, gpu_fp64_iters):
+    """The oracle on the host cores beside the GPU numbers (rank 0, N = 1):
+    (1) one FP64 outer iteration on the index sample, scaled to a solve by
+    stored entries and the outer-iteration count of this run's FP64 GPU
+    solve on the Section 6.2 inner schedule (the oracle's schedule);
+    (2) full oracle BKS and HOOI solves of the 300 x 300 x 100 workload;
+    (3) the oracle's mode-1 loop in C with OpenMP on all host cores, on the
+    full workload (FP64, widths 3 x 4)."""
+    import oracle as O
+    w = WORKLOAD
+    info = cpu_info()
+    A, U0, W0 = oracle_sample(coo)
+    t_iter = oracle_outer_iteration(A, U0, W0)
+    scale = nnz_full / max(1, A.nnz)
+    solve_s = t_iter * scale * max(1, gpu_fp64_iters)
+    out = {"value": 1.0 / solve_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+           "nproc": info["nproc"], "cpu_model": info["model"],
+           "sample": f"one FP64 outer iteration of the oracle on the {int(SAMPLE_FRAC * 100)}%-"
+                     f"index sample ({A.nnz} of {nnz_full} stored), {t_iter:.2f} s single-"
+                     f"threaded, scaled by stored entries x {gpu_fp64_iters} outer iterations "
+                     f"(this run's FP64 GPU solve on the same inner schedule)"}
+    # (2) the small planted workload, solved in full
+    coo1, _ = synth.small_planted(1)
+    A1 = O.symmetrise(coo1.m, coo1.n, coo1.i, coo1.j, coo1.k, coo1.v)
+    g = synth.rng(101)
+    U1, W1 = synth.orthonormal(g, A1.m, 2), synth.orthonormal(g, A1.n, 2)
+    t0 = time.perf_counter()
+    rb = O.bks(A1, U1, W1, s=2, p=2, tol=1e-10)
+    t_bks = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rh = O.hooi(A1, U1, W1, tol=1e-10)
+    t_hooi = time.perf_counter() - t0
+    out["small_planted"] = {"workload": "300x300x100, 10,000 draws mirrored + planted (2,2,2), "
+                                        "rank (2,2,2), BK(2,2), tol 1e-10, FP64",
+                            "oracle_bks_s": t_bks, "oracle_bks_iters": rb.iters,
+                            "oracle_hooi_s": t_hooi, "oracle_hooi_iters": rh.iters,
+                            "cores": 1}
+    # (3) the all-cores column
+    try:
+        from oracle import omp
+        t0 = time.perf_counter()
+        Af = O.symmetrise(coo.m, coo.n, coo.i, coo.j, coo.k, coo.v)
+        t_sym = time.perf_counter() - t0
+        g = synth.rng(5)
+        X = g.standard_normal((Af.m, 3)); Y = g.standard_normal((Af.n, 4))
+        rp = omp.csr_rowptr(Af)
+        omp.mode1_omp(Af, X, Y, rp)
+        ts = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            omp.mode1_omp(Af, X, Y, rp)
+            ts.append(time.perf_counter() - t0)
+        t_omp = statistics.median(ts)
+        alg = Af.nnz * (4 + 4 + 8) + (Af.m + 1) * 8 + Af.m * 3 * 8 + Af.n * 4 * 8 + Af.m * 12 * 8
+        out["openmp_mode1"] = {"seconds": t_omp, "GB_per_s": alg / t_omp / 1e9,
+                               "threads": omp.threads(), "width": "3 x 4", "dtype": "f64",
+                               "nnz_stored": Af.nnz, "symmetrise_s": t_sym}
+    except Exception as e:  # gcc or OpenMP missing on the host
+        out["openmp_mode1"] = {"unavailable": str(e)[:200]}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -196,54 +301,142 @@ MID_NNZ = 11_777_770
 LARGE = {"m": 1_000_000, "n": 200, "draws": 60_000_000, "zipf_s": 1.2, "seed": 3, "r": 5}
 
 
-def large_roofline(bk, torch, stream, flush, hbm, peak_kind):
-    """The contraction roofline case: the mode-1 contraction on the
-    1e6 x 1e6 x 200 Zipf(1.2) tensor (FP32 values, mirrored, duplicates
-    summed), with the 4 x 4 block shape of BK(2,4) (X and Y 4 columns,
-    output 16).  `traffic`: DRAM bytes of k_contract measured by ncu on the
-    500,000 x 500,000 x 200 case (11,777,770 stored, same kernel; that size
-    runs the (64, 1024) plan, this one (128, 2048)), scaled to this launch by
-    stored entries.  One timed call = pack of X and Y,
-    the contraction kernel, the piece reduction of long rows and the zero
-    rows; algorithmic bytes = index and value streams + row pointers + X and
-    Y read once + output written once (gathers served by L2 not counted)."""
+def _timed(torch, stream, flush, fn, reps=15):
+    """Median CUDA-event time of fn() on `stream`, the L2 flushed before each."""
+    for _ in range(3):
+        fn()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(2.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.median(ts)
+
+
+def fp32_alu_peak_tflops(torch):
+    """FP32 FMA peak from the unit counts and the measured maximum SM clock:
+    SMs x 128 FP32 lanes x 2 flops x clock."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def large_workload(bk, torch, stream, flush, hbm, peak_kind):
+    """The 1e6 x 1e6 x 200 Zipf(1.2) tensor (60M one-sided draws, FP32
+    |N(0,1)| values, mirrored, duplicates summed -> 48.5M stored), rank
+    (5,5,5), BK(2,4) -> (k1, k3) = (70, 40):
+      * `roofline`: the FP32 mode-1 contraction with 4 x 4 blocks, the
+        BK(2,4) block shape;
+      * `kernels`: the contraction widths a rank-5 BK(2,4) solve issues
+        (mode 1: 5 x 5 stage 1, 5 x 4 and 4 x 5 stage 2; mode 3: the
+        15-column triangle of stage 1 and the 5 x 4 block of stage 2), the
+        core C = A.(X,X,Z) at (70, 40) against the FP32 ALU peak, and the
+        core F = A.(U,U,W) at (5, 5, 5);
+      * `solve`: a full mixed-precision solve with its FP64 refinement.
+    One timed contraction call = pack of the operands, the contraction
+    kernel, the piece reduction of long rows and the zero rows; algorithmic
+    bytes = index and value streams + row pointers + operands read once +
+    output written once (gathers served by L2 not counted).  `traffic`: DRAM
+    bytes of k_contract from an ncu capture of the 500,000 x 500,000 x 200
+    case (same kernel), scaled to this launch by stored entries."""
     L = LARGE
     coo = synth.zipf_tensor(L["seed"], L["m"], L["n"], L["draws"], L["zipf_s"],
                             values="absnormal", vdtype=np.float32)
     T = bk.bks_tensor_create_coo(coo.m, coo.n, coo.i, coo.j, coo.k, coo.v)
     del coo
-    m, n, p, q = L["m"], L["n"], 4, 4
+    m, n, nnz = L["m"], L["n"], T.nnz
     g = synth.rng(11)
-    X = torch.tensor(g.standard_normal((m, p)), device="cuda", dtype=torch.float32)
-    Y = torch.tensor(g.standard_normal((n, q)), device="cuda", dtype=torch.float32)
-    out = torch.empty((p * q, m), device="cuda", dtype=torch.float32).t()
-    for _ in range(3):
-        bk.bks_contract_mode1(T, X, Y, out=out, stream=stream)
-    ts = []
-    for _ in range(20):
-        flush.fill_(2.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        bk.bks_contract_mode1(T, X, Y, out=out, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1) / 1e3)
-    kt = statistics.median(ts)
-    nnz = T.nnz
-    alg = nnz * (4 + 4 + 4) + (m + 1) * 4 + m * p * 4 + n * q * 4 + m * p * q * 4
-    ach = alg / kt / 1e9
+
+    def cm(rows, cols, dt=torch.float32):
+        return torch.tensor(g.standard_normal((rows, cols)), device="cuda", dtype=dt)
+
+    def mode1(p, q):
+        X, Y = cm(m, p), cm(n, q)
+        out = torch.empty((p * q, m), device="cuda", dtype=torch.float32).t()
+        t = _timed(torch, stream, flush, lambda: bk.bks_contract_mode1(T, X, Y, out=out, stream=stream))
+        alg = nnz * 12 + (m + 1) * 4 + m * p * 4 + n * q * 4 + m * p * q * 4
+        return {"call": f"mode1 {p}x{q}", "us": t * 1e6, "alg_bytes": alg, "GB_per_s": alg / t / 1e9,
+                "frac": alg / t / 1e9 / hbm}
+
+    def mode3(p, q):
+        X = cm(m, p)
+        if q is None:
+            w = p * (p + 1) // 2
+            out = torch.empty((w, n), device="cuda", dtype=torch.float32).t()
+            t = _timed(torch, stream, flush, lambda: bk.bks_contract_mode3(T, X, out=out, stream=stream))
+            alg = nnz * 12 + (n + 1) * 4 + m * p * 4 + n * w * 4
+            name = f"mode3 triangle {p} ({w} columns)"
+        else:
+            X2 = cm(m, q)
+            out = torch.empty((p * q, n), device="cuda", dtype=torch.float32).t()
+            t = _timed(torch, stream, flush,
+                       lambda: bk.bks_contract_mode3(T, X, X2, out=out, stream=stream))
+            alg = nnz * 12 + (n + 1) * 4 + m * (p + q) * 4 + n * p * q * 4
+            name = f"mode3 {p}x{q}"
+        return {"call": name, "us": t * 1e6, "alg_bytes": alg, "GB_per_s": alg / t / 1e9,
+                "frac": alg / t / 1e9 / hbm}
+
+    r44 = mode1(4, 4)
+    roofline = {"kernel": "bks_contract_mode1 FP32 (pack + k_contract<float,float,4,4> + piece "
+                          "reduction + zero rows)",
+                "workload": f"zipf1.2 (1,2)-symmetric 1e6 x 1e6 x 200, {nnz} stored "
+                            f"({L['draws']} draws mirrored, duplicates summed), X 4 cols, Y 4 cols",
+                "bound": "hbm", "achieved": r44["GB_per_s"], "peak": hbm, "unit": "GB/s",
+                "frac": r44["frac"], "peak_kind": peak_kind,
+                "traffic": int(MID_TRAFFIC_BYTES * nnz / MID_NNZ),
+                "traffic_note": "ncu dram bytes of k_contract<float,float,4,4> on the 11.8M-entry "
+                                "case, scaled by stored entries",
+                "alg_bytes_per_launch": r44["alg_bytes"], "median_launch_s": r44["us"] * 1e-6,
+                "nnz_stored": nnz}
+    kernels = [mode1(5, 5), mode1(5, 4), mode1(4, 5), mode3(5, None), mode3(5, 4)]
+    # K3: C = A.(X,X,Z) at (k1, k3) = (70, 40), FP32
+    k1, k3 = 70, 40
+    Xc, Zc = cm(m, k1), cm(n, k3)
+    t = _timed(torch, stream, flush, lambda: bk.bks_core(T, Xc, Zc, stream=stream), reps=5)
+    flops = 2.0 * (nnz * (k1 * (k1 + 1) / 2 + k1) + n * k3 * k1 * (k1 + 1) / 2)
+    peak32 = fp32_alu_peak_tflops(torch)
+    kernels.append({"call": "core C = A.(X,X,Z) FP32, (k1,k3) = (70,40)", "us": t * 1e6,
+                    "flops": flops, "TFLOP_per_s": flops / t / 1e12, "bound": "alu",
+                    "peak_TFLOP_per_s": peak32, "frac": flops / t / 1e12 / peak32,
+                    "peak_kind": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"})
+    del Xc, Zc
+    # K4: F = A.(U,U,W) at (5,5,5), FP32 and FP64
+    for dt, name in ((torch.float32, "FP32"), (torch.float64, "FP64")):
+        U, Wm = cm(m, 5, dt), cm(n, 5, dt)
+        t = _timed(torch, stream, flush, lambda: bk.bks_core(T, U, Wm, stream=stream))
+        alg = nnz * 12 + (n + 1) * 4 + m * 5 * U.element_size() + n * 15 * 4
+        kernels.append({"call": f"core F = A.(U,U,W) {name}, r = (5,5,5)", "us": t * 1e6,
+                        "alg_bytes": alg, "GB_per_s": alg / t / 1e9, "frac": alg / t / 1e9 / hbm})
+    # the full solve: mixed precision, then the FP64 refinement form
+    U0h, W0h = start_matrices(m, n, L["r"], seed=21)
+    prm = bk.BksParams(r1=L["r"], r3=L["r"], stages=2, block_p=4, tol=1e-9, tol_scale_free=1,
+                       precision=bk.BKS_PREC_MIXED, mixed_tol=1e-4, refine_sweeps=50,
+                       max_outer=200, inner_schedule=bk.BKS_INNER_FAST)
+    U0, W0 = torch.tensor(U0h, device="cuda"), torch.tensor(W0h, device="cuda")
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    U, W, F, info = bk.bks_solve(T, prm, U0, W0, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve = {"seconds": e0.elapsed_time(e1) / 1e3, "converged": info["converged"],
+             "iters": info["iters"], "fp32_iters": info["fp32_iters"], "k1": info["k1"],
+             "k3": info["k3"], "grad_rel": info["grad_rel"], "normF": info["normF"],
+             "phase_ms": info["phase_ms"],
+             "params": "rank (5,5,5), BK(2,4), ||grad||/||F||^2 <= 1e-9, mixed then FP64 "
+                       "refinement, fast inner schedule"}
     T.close()
-    traffic = int(MID_TRAFFIC_BYTES * nnz / MID_NNZ)
-    return {"kernel": "bks_contract_mode1 FP32 (pack + k_contract<float,float,4,4> + piece "
-                      "reduction + zero rows)",
-            "workload": f"zipf1.2 (1,2)-symmetric 1e6 x 1e6 x 200, {nnz} stored "
-                        f"({L['draws']} draws mirrored, duplicates summed), X 4 cols, Y 4 cols",
-            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "peak_kind": peak_kind, "traffic": traffic,
-            "traffic_note": "ncu dram bytes of k_contract on the 11.8M-entry case, scaled by "
-                            "stored entries", "alg_bytes_per_launch": alg,
-            "median_launch_s": kt, "nnz_stored": nnz}
+    return roofline, kernels, solve
 
 
 def ncu_case(args):
@@ -296,20 +489,36 @@ def ncu_case(args):
     print(f"ncu case {args.ncu_case} ({args.size}) done: nnz {T.nnz}")
 
 
+def _sin_max(A, B):
+    D = B - A @ (A.T @ B)
+    return float(np.linalg.norm(D, 2)) if D.size else 0.0
+
+
+def _determined(F, mode, rel=1e-6):
+    """A mode's subspace is unique when its last S-value (Section 2.6) is
+    clearly above zero."""
+    Fk = np.moveaxis(np.asarray(F), mode, 0).reshape(F.shape[mode], -1)
+    sv = np.sqrt(np.maximum(np.linalg.eigvalsh(Fk @ Fk.T), 0.0))
+    return sv[0] > 0 and sv[0] > rel * sv[-1]
+
+
 def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
-    """The batched form (many small solves on concurrent streams, work tiles
-    autotuned per size class) and the serving loop (Poisson arrivals,
-    admission by a 150 GB budget, continuous batching), both on jobs drawn
-    as the batched workload (sizes scaled by `scale`), mixed precision at
-    the scale-free tolerance 1e-9, against the same jobs solved one at a
-    time in FP64."""
+    """The batched form (independent solves on concurrent streams, work
+    tiles autotuned per size class) on the job-size law of the batched
+    workload at `scale`, mixed precision at the scale-free tolerance 1e-9,
+    against the same jobs solved one at a time in FP64; every job's result
+    compared with its FP64 solution (sin of the largest principal angle,
+    modes whose last S-value is zero skipped).  Then the serving loop on a
+    Poisson stream of jobs drawn the same way: an offered-rate sweep below
+    the measured service rate (latency = service time plus the queueing of
+    a stable system) and the nominal 200 requests/s."""
     jobs = synth.batch_jobs(seed=4, count=n_batch, scale=scale)
     coos = [synth.job_tensor(j) for j in jobs]
 
     def prm(r, prec):
         return bk.BksParams(r1=r, r3=r, stages=2, block_p=4, tol=1e-9, tol_scale_free=1,
                             precision=prec, mixed_tol=1e-4, refine_sweeps=50, max_outer=200,
-                            max_inner=100)
+                            max_inner=200, inner_schedule=bk.BKS_INNER_FAST)
 
     tens = [bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v) for c in coos]
     for T in tens[:4]:
@@ -320,40 +529,78 @@ def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
                              nstreams=8, autotune=True, stream=stream)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
-    ok = sum(1 for r in res if r[4] == 0)
+    seq, seq_lat = [], []
     t0 = time.perf_counter()
     for T, j in zip(tens, jobs):
+        t1 = time.perf_counter()
         try:
-            bk.bks_solve(T, prm(j["r"], bk.BKS_PREC_FP64), stream=stream)
-        except bk.BksError:
-            pass
-    torch.cuda.synchronize()
+            seq.append(bk.bks_solve(T, prm(j["r"], bk.BKS_PREC_FP64), stream=stream))
+        except bk.BksError as e:
+            seq.append(None)
+        torch.cuda.synchronize()
+        seq_lat.append(time.perf_counter() - t1)
     t_seq = time.perf_counter() - t0
+    errs, failed = [], []
+    for q, (r, sq, j) in enumerate(zip(res, seq, jobs)):
+        U, W, F, info, st = r
+        if st != 0:
+            failed.append({"job": q, "status": st, "m": j["m"], "n": j["n"], "r": j["r"],
+                           "nnz_stored": tens[q].nnz, "iters": info["iters"],
+                           "grad_rel": info["grad_rel"]})
+            continue
+        if sq is None or not sq[3]["converged"]:
+            continue
+        F64 = sq[2].cpu().numpy()
+        e = 0.0
+        if _determined(F64, 0):
+            e = max(e, _sin_max(sq[0].cpu().numpy(), U.cpu().numpy()))
+        if _determined(F64, 2):
+            e = max(e, _sin_max(sq[1].cpu().numpy(), W.cpu().numpy()))
+        errs.append(e)
+    ok = n_batch - len(failed)
     batched = {"jobs": n_batch, "ok": ok, "solves_per_s": n_batch / t_batch,
+               "ok_solves_per_s": ok / t_batch,
                "sequential_fp64_solves_per_s": n_batch / t_seq,
-               "speedup_vs_sequential_fp64": t_seq / t_batch, "streams": 8,
-               "scale": scale, "nnz_stored_total": int(sum(T.nnz for T in tens))}
+               "speedup_vs_sequential_fp64": t_seq / t_batch, "streams": 8, "scale": scale,
+               "nnz_stored_total": int(sum(T.nnz for T in tens)),
+               "subspace_sin_vs_fp64": {"max": max(errs) if errs else None,
+                                        "median": float(np.median(errs)) if errs else None,
+                                        "jobs_compared": len(errs)},
+               "failed": failed[:20]}
     del tens
-    # serving: Poisson arrivals, mean gap 5 ms
-    arrivals, sjobs = synth.serving_stream(seed=5, requests=n_serve, scale=scale)
-    scoos = [synth.job_tensor(j) for j in sjobs]
-    with bk.Server(150 << 30, max_slots=8, autotune=True) as srv:
-        start = time.perf_counter()
-        tickets = []
-        for a, j, c in zip(arrivals, sjobs, scoos):
-            now = time.perf_counter() - start
-            if a > now:
-                time.sleep(a - now)
-            tickets.append(srv.submit(c.m, c.n, c.i, c.j, c.k, c.v,
-                                      prm(j["r"], bk.BKS_PREC_MIXED)))
-        outs = [srv.poll(t, wait=True) for t in tickets]
-        wall = time.perf_counter() - start
-    lat = sorted(o["latency_s"] for o in outs)
-    serving = {"requests": n_serve, "ok": sum(1 for o in outs if o["status"] == 0),
-               "solves_per_s": n_serve / wall, "offered_per_s": n_serve / float(arrivals[-1]),
-               "latency_p50_s": lat[len(lat) // 2],
-               "latency_p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-               "slots": 8, "budget_bytes": 150 << 30, "scale": scale}
+    seq_sorted = sorted(seq_lat)
+    one_at_a_time = {"p50_s": seq_sorted[len(seq_sorted) // 2],
+                     "p99_s": seq_sorted[min(len(seq_sorted) - 1, int(0.99 * len(seq_sorted)))],
+                     "note": "the batched jobs solved one at a time in FP64, solve time per job"}
+    # ---- serving ----
+    service_rate = n_batch / t_batch
+
+    def serve(rate, nreq, seed):
+        arrivals, sjobs = synth.serving_stream(seed=seed, requests=nreq, scale=scale,
+                                               mean_gap_s=1.0 / rate)
+        scoos = [synth.job_tensor(j) for j in sjobs]
+        with bk.Server(150 << 30, max_slots=8, autotune=True) as srv:
+            start = time.perf_counter()
+            tickets = []
+            for a, j, c in zip(arrivals, sjobs, scoos):
+                now = time.perf_counter() - start
+                if a > now:
+                    time.sleep(a - now)
+                tickets.append(srv.submit(c.m, c.n, c.i, c.j, c.k, c.v,
+                                          prm(j["r"], bk.BKS_PREC_MIXED)))
+            outs = [srv.poll(t, wait=True) for t in tickets]
+            wall = time.perf_counter() - start
+        lat = sorted(o["latency_s"] for o in outs)
+        return {"requests": nreq, "offered_per_s": nreq / float(arrivals[-1]),
+                "ok": sum(1 for o in outs if o["status"] == 0), "solves_per_s": nreq / wall,
+                "latency_p50_s": lat[len(lat) // 2],
+                "latency_p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+
+    sweep = [serve(f * service_rate, n_serve, 50 + i) for i, f in enumerate((0.3, 0.6))]
+    nominal = serve(200.0, n_serve, 5)
+    serving = {"slots": 8, "budget_bytes": 150 << 30, "scale": scale,
+               "service_rate_batched_per_s": service_rate, "sweep": sweep,
+               "nominal_200_per_s": nominal, "one_at_a_time_fp64": one_at_a_time}
     return batched, serving
 
 
@@ -364,11 +611,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch-scale", type=float, default=0.1,
+    ap.add_argument("--batch-scale", type=float, default=0.25,
                     help="size scale of the batched/serving jobs (1.0 = m up to 2e5 and "
                          "up to 5M stored entries per job); 0 skips them")
     ap.add_argument("--batch-jobs", type=int, default=256)
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--ncu-case", default=None,
                     help="profiling entry: build the workload, run a few launches of one "
                          "kernel family (mode1, mode3, core, solve) and exit without a JSON line")
@@ -413,7 +660,7 @@ def main():
                             max_outer=500,
                             inner_schedule=bk.BKS_INNER_FAST if inner is None else inner)
 
-    def timed_solves(prec, steps, warm):
+    def timed_solves(prec, steps, warm, inner=None):
         lat = []
         infos = []
         for s in range(warm + steps):
@@ -424,7 +671,7 @@ def main():
             if dist:
                 dist.barrier()
             e0.record(stream)
-            U, W, F, info = bk.bks_solve(T, params(prec), U0, W0, stream=stream)
+            U, W, F, info = bk.bks_solve(T, params(prec, inner), U0, W0, stream=stream)
             e1.record(stream)
             torch.cuda.synchronize()
             if s >= warm:
@@ -450,6 +697,18 @@ def main():
     # ---- FP64 at the same tolerance ----
     lat64, inf64, res64 = timed_solves(bk.BKS_PREC_FP64, max(2, args.steps // 2), 1)
     fp64_rate = len(lat64) / sum(lat64)
+    # ---- the Section 6.2 inner schedule (HOSVD + 5 HOOI sweeps, inner
+    # tolerance = outer tolerance), both precisions ----
+    paper = {}
+    for nm, prec in (("mixed", bk.BKS_PREC_MIXED), ("fp64", bk.BKS_PREC_FP64)):
+        lp, ip, rp_ = timed_solves(prec, 2, 1, inner=bk.BKS_INNER_PAPER)
+        paper[nm] = {"solves_per_s": len(lp) / sum(lp), "iters": ip[-1]["iters"],
+                     "inner_sweeps": ip[-1]["inner_sweeps"], "grad_rel": ip[-1]["grad_rel"],
+                     "subspace_sin_vs_ref": None}
+        Up, Wp = rp_[0].cpu().numpy(), rp_[1].cpu().numpy()
+        paper[nm]["subspace_sin_vs_ref"] = max(
+            float(np.linalg.norm(Up - Uref @ (Uref.T @ Up), 2)),
+            float(np.linalg.norm(Wp - Wref @ (Wref.T @ Wp), 2)))
     # subspace agreement mixed vs FP64: sin of the largest principal angle
     def sin_max(A, B):
         D = B - A @ (A.T @ B)
@@ -493,7 +752,7 @@ def main():
                          "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
                          "alg_bytes_per_launch": alg_bytes, "median_launch_s": kt}
     del T32
-    roofline = large_roofline(bk, torch, stream, flush, hbm, peak_kind)
+    roofline, large_kernels, large_solve = large_workload(bk, torch, stream, flush, hbm, peak_kind)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e_steps = max(1, min(3, args.steps))
@@ -520,18 +779,10 @@ def main():
         batched, serving = batch_and_serve(bk, torch, args.batch_scale, args.batch_jobs,
                                            args.serve_requests, stream)
 
-    # ---- CPU oracle baseline (bounded sample) ----
+    # ---- CPU oracle baseline (bounded sample; rank 0, N = 1) ----
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        d = cpu_oracle_sample(coo)
-        outer = statistics.median([i["iters"] for i in inf64])
-        scale = T.nnz / max(1, d["nnz_sample"])
-        solve_s = d["seconds_per_outer_iter"] * scale * max(1, outer)
-        cpu = {"value": 1.0 / solve_s, "unit": "solves/s", "cores": d["threads"],
-               "kind": "oracle",
-               "sample": f"one FP64 outer iteration on a {d['m_sample']}-row sample "
-                         f"({d['nnz_sample']} stored), {d['seconds_per_outer_iter']:.1f} s, scaled "
-                         f"by stored entries x {outer} outer iterations (FP64 GPU solve count)"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_leg(coo, T.nnz, paper["fp64"]["iters"])
 
     lat_sorted = sorted(lat_mixed)
     line = {
@@ -545,6 +796,9 @@ def main():
                    "1e-6 (sin of largest principal angle) of an FP64 solution converged to "
                    "||grad||/||F||^2 <= 1e-11",
                    "l2": "512 MB buffer written between timed steps",
+                   "inner_schedule": "fast (HOSVD start without sweeps, inexact inner "
+                                     "tolerance); the Section 6.2 schedule is reported in "
+                                     "paper_inner_schedule",
                    "parallelism": f"replicas x{world}"},
         "fp64_solves_per_s": fp64_rate, "mixed_over_fp64": value / world / fp64_rate,
         "subspace_sin": ang,
@@ -555,8 +809,11 @@ def main():
                         "fp64": [i["iters"] for i in inf64]},
         "grad_rel": {"mixed": inf_mixed[-1]["grad_rel"], "fp64": inf64[-1]["grad_rel"]},
         "phase_ms": {"mixed": inf_mixed[-1]["phase_ms"], "fp64": inf64[-1]["phase_ms"]},
+        "paper_inner_schedule": paper,
         "roofline": roofline,
         "roofline_workload": roofline_workload,
+        "large_workload": {"workload": roofline["workload"], "kernels": large_kernels,
+                           "solve": large_solve},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -130,3 +130,21 @@ def test_mode1_rows_from_input_matches_stored_tensor():
     got = O.mode1_rows_from_input(i, j, k, v, X, Y, rows)
     ref = O.mode1(A, X, Y)[rows]
     assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_openmp_contraction_loop_equals_the_oracle():
+    """The benchmark's all-cores CPU column (the oracle's mode-1 loop in C
+    with OpenMP) computes unfold_1 of A.(X,Y)_{2,3} like the numpy oracle."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from oracle import omp
+    c = synth.zipf_tensor(12, 700, 9, 20_000, 1.1)
+    A = O.symmetrise(c.m, c.n, c.i, c.j, c.k, c.v)
+    g = synth.rng(13)
+    for p, q in [(3, 4), (5, 5), (1, 1), (8, 8)]:
+        X = g.standard_normal((A.m, p)); Y = g.standard_normal((A.n, q))
+        got = omp.mode1_omp(A, X, Y)
+        ref = O.mode1(A, X, Y)
+        assert np.allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    assert omp.threads() >= 1
