@@ -19,6 +19,9 @@ Pins (what fixes each function other than itself) live in
 * ``hosvd_truncated``     -- returns the exact factor subspaces of a core of
                              exact multilinear rank (U,U,W).F0.
 * ``sin_theta_max``       -- sin of a known planted principal angle.
+* ``ng_model``/``ng_step`` -- finite differences of the pulled-back
+                             objective; quadratic convergence; the same
+                             optimum as HOOI.
 * ``inner_solve``/``bks``/``hooi`` -- closed forms n=1 (Eckart-Young) and
                              rank-one slices, exact recovery of a planted
                              multilinear-rank tensor, monotone ||F||, and
@@ -36,7 +39,7 @@ __all__ = [
     "orth_block", "schedule_counts", "expand", "gradient_prop2", "mode1_rows_from_input",
     "gradient_global", "inner_solve", "bks", "hooi", "sin_theta_max",
     "top_left_singular", "unfold1", "unfold3", "s_values", "tri_index",
-    "BKSResult", "hosvd_truncated", "INNER_INIT_SWEEPS",
+    "BKSResult", "hosvd_truncated", "INNER_INIT_SWEEPS", "ng_model", "ng_step",
 ]
 
 
@@ -575,27 +578,107 @@ def _hooi_sweeps(C, Uh, Wh, sweeps, tol):
         done += 1
 
 
+# ----------------------------------------------------------------------------
+# Newton-Grassmann on the dense core (Section 6.2 names the method; the
+# step below is this library's derivation for the symmetric problem)
+# ----------------------------------------------------------------------------
+def _complement(Q: np.ndarray) -> np.ndarray:
+    """An orthonormal basis of the orthogonal complement of span(Q)."""
+    k, r = Q.shape
+    full = np.linalg.qr(np.concatenate([Q, np.eye(k)], axis=1))[0]
+    # Householder QR of [Q I]: the first r columns span Q; the next k - r
+    # complete the orthogonal basis
+    return full[:, r:k].copy()
+
+
+def ng_model(C: np.ndarray, Uh: np.ndarray, Wh: np.ndarray):
+    """Gradient and Hessian of g(X, Y) = 1/2 ||C.(U(X), U(X), W(Y))||^2 at
+    X = 0, Y = 0, where U(X) = (Uh + Up X)(I + X^T X)^{-1/2} and W(Y) =
+    (Wh + Wp Y)(I + Y^T Y)^{-1/2} with [Uh Up], [Wh Wp] orthogonal: local
+    coordinates of the product of Grassmann manifolds around (Uh, Wh), U
+    used in modes 1 and 2 (the (1,2)-symmetric problem).  With B1 =
+    C.(Up,Uh,Wh), B11 = C.(Up,Up,Wh), B3 = C.(Uh,Uh,Wp), B13 = C.(Up,Uh,Wp)
+    and F0 = C.(Uh,Uh,Wh), the second-order expansion of the core gives
+      grad_X = 2 unfold_1(B1) unfold_1(F0)^T,  grad_Y = unfold_3(B3) unfold_3(F0)^T,
+      H = J^T J + [[2K - 2 (M1 (x) I), 2L], [2L^T, -(M3 (x) I)]],
+    J the Jacobian of the first-order core term, K[(s,a),(p,b)] =
+    sum_c F0[a,b,c] B11[s,p,c], L[(s,a),(t,c)] = sum_b F0[a,b,c] B13[s,b,t],
+    M1 = unfold_1(F0) unfold_1(F0)^T, M3 = unfold_3(F0) unfold_3(F0)^T.
+    Coordinates are ordered x = vec(X) (column-major), then y = vec(Y).
+    Returns (grad, H, Up, Wp)."""
+    r1, r3 = Uh.shape[1], Wh.shape[1]
+    Up, Wp = _complement(Uh), _complement(Wh)
+    d1, d3 = Up.shape[1], Wp.shape[1]
+    c3 = lambda A, B, Cm: np.einsum("ijk,ia,jb,kc->abc", C, A, B, Cm, optimize=True)
+    F0 = c3(Uh, Uh, Wh)
+    B1 = c3(Up, Uh, Wh)
+    B11 = c3(Up, Up, Wh)
+    B3 = c3(Uh, Uh, Wp)
+    B13 = c3(Up, Uh, Wp)
+    gX = 2.0 * np.einsum("abc,sbc->sa", F0, B1)
+    gY = np.einsum("abc,abt->tc", F0, B3)
+    I1, I3 = np.eye(r1), np.eye(r3)
+    Jx = (np.einsum("aA,sbc->abcsA", I1, B1) + np.einsum("bA,sac->abcsA", I1, B1))
+    Jx = Jx.reshape(r1 * r1 * r3, d1 * r1, order="F")
+    Jy = np.einsum("cC,abt->abctC", I3, B3).reshape(r1 * r1 * r3, d3 * r3, order="F")
+    J = np.concatenate([Jx, Jy], axis=1)
+    K = np.einsum("abc,spc->sapb", F0, B11).reshape(d1 * r1, d1 * r1, order="F")
+    L = np.einsum("abc,sbt->satc", F0, B13).reshape(d1 * r1, d3 * r3, order="F")
+    M1 = unfold1(F0) @ unfold1(F0).T
+    M3 = unfold3(F0) @ unfold3(F0).T
+    H = J.T @ J
+    H[: d1 * r1, : d1 * r1] += 2.0 * K - 2.0 * np.kron(M1, np.eye(d1))
+    H[: d1 * r1, d1 * r1:] += 2.0 * L
+    H[d1 * r1:, : d1 * r1] += 2.0 * L.T
+    H[d1 * r1:, d1 * r1:] -= np.kron(M3, np.eye(d3))
+    grad = np.concatenate([gX.ravel(order="F"), gY.ravel(order="F")])
+    return grad, H, Up, Wp
+
+
+def ng_step(C: np.ndarray, Uh: np.ndarray, Wh: np.ndarray):
+    """One Newton step for max ||C.(U,U,W)|| on the Grassmann product:
+    solve H z = -grad in the local coordinates of ``ng_model`` and move to
+    the orthonormalised (Uh + Up X, Wh + Wp Y).  Returns (Uh, Wh, ok) with
+    ok False, and the point unchanged, when -H is not positive definite
+    (the point is not near a nondegenerate maximum)."""
+    r1, r3 = Uh.shape[1], Wh.shape[1]
+    grad, H, Up, Wp = ng_model(C, Uh, Wh)
+    try:
+        Lc = np.linalg.cholesky(-H)
+    except np.linalg.LinAlgError:
+        return Uh, Wh, False
+    z = np.linalg.solve(Lc.T, np.linalg.solve(Lc, grad))    # z = (-H)^{-1} grad
+    d1 = Up.shape[1]
+    X = z[: d1 * r1].reshape(d1, r1, order="F")
+    Y = z[d1 * r1:].reshape(-1, r3, order="F")
+    Un = np.linalg.qr(Uh + Up @ X)[0]
+    Wn = np.linalg.qr(Wh + Wp @ Y)[0]
+    return Un, Wn, True
+
+
 # Section 6.2: the inner problem starts from the truncated HOSVD of C
 # followed by 5 HOOI iterations
 INNER_INIT_SWEEPS = 5
 
 
 def inner_solve(C: np.ndarray, r1: int, r3: int, tol: float, max_inner: int = 1000,
-                init_sweeps: int = INNER_INIT_SWEEPS):
+                init_sweeps: int = INNER_INIT_SWEEPS, method: str = "ng"):
     """Best rank-(r1,r1,r3) approximation of the dense (1,2)-symmetric core
     C (k1 x k1 x k3), Algorithm 5 step (i).
 
-    Section 6.2 starts from the truncated HOSVD of C followed by 5 HOOI
-    iterations and then runs Newton-Grassmann (not given in the paper) with
-    the outer stopping criterion.  This library's reading: after the HOSVD
-    start and its ``init_sweeps`` HOOI sweeps the HOOI sweeps continue until
-    the G-gradient is below ``tol`` relative to ||F|| or ``max_inner``
-    sweeps are done.  Monotone safeguard (this library's reading): the
-    current point (Uh = [I;0], Wh = [I;0], which is (U0, W0) in the bases)
-    is kept as a second candidate, and the continuation starts from
-    whichever of the two has the larger ||F||; so ||F|| never decreases
-    over the outer iterations (eq. (Fnon-decr)).
-    Returns (Uh, Wh, info)."""
+    Section 6.2: start from the truncated HOSVD of C followed by 5 HOOI
+    iterations, then Newton-Grassmann with the outer stopping criterion.
+    Here: after the HOSVD start and its ``init_sweeps`` HOOI sweeps,
+    ``method`` "ng" takes Newton steps (``ng_step``) until the G-gradient
+    is below ``tol`` relative to ||F|| or ``max_inner`` steps are done; a
+    step is refused where -H is not positive definite or ||F|| would drop,
+    and a HOOI sweep is taken instead (this library's safeguard away from a
+    maximum).  ``method`` "hooi" continues with HOOI sweeps alone.
+    Monotone safeguard (this library's reading): the current point
+    (Uh = [I;0], Wh = [I;0], which is (U0, W0) in the bases) is kept as a
+    second candidate, and the continuation starts from whichever of the two
+    has the larger ||F||; so ||F|| never decreases over the outer
+    iterations (eq. (Fnon-decr)).  Returns (Uh, Wh, info)."""
     k1, _, k3 = C.shape
     Uh_a, Wh_a = hosvd_truncated(C, r1, r3)
     Uh_b = np.eye(k1, r1)
@@ -603,9 +686,27 @@ def inner_solve(C: np.ndarray, r1: int, r3: int, tol: float, max_inner: int = 10
     A_ = _hooi_sweeps(C, Uh_a, Wh_a, init_sweeps, 0.0)
     B_ = _hooi_sweeps(C, Uh_b, Wh_b, 0, 0.0)
     start = A_ if A_[3] >= B_[3] else B_
-    Uh, Wh, g, nf, done = _hooi_sweeps(C, start[0], start[1], max_inner, tol)
-    return Uh, Wh, {"grad": g, "normF": nf,
-                    "sweeps": done + (A_[4] if start is A_ else 0),
+    pre = A_[4] if start is A_ else 0
+    if method == "hooi":
+        Uh, Wh, g, nf, done = _hooi_sweeps(C, start[0], start[1], max_inner, tol)
+        return Uh, Wh, {"grad": g, "normF": nf, "sweeps": done + pre, "ng_steps": 0,
+                        "hosvd_won": start is A_}
+    Uh, Wh = start[0], start[1]
+    g, nf = start[2], start[3]
+    sweeps, steps = pre, 0
+    while g > tol * nf and steps + sweeps - pre < max_inner:
+        Un, Wn, ok = ng_step(C, Uh, Wh)
+        if ok:
+            T1, T3 = _c_t1(C, Un, Wn), _c_t3(C, Un)
+            gn, nfn, _ = _inner_grad(Un, Wn, T1, T3)
+            ok = nfn >= nf * (1.0 - 1e-14)
+        if ok:
+            Uh, Wh, g, nf = Un, Wn, gn, nfn
+            steps += 1
+        else:
+            Uh, Wh, g, nf, _ = _hooi_sweeps(C, Uh, Wh, 1, 0.0)
+            sweeps += 1
+    return Uh, Wh, {"grad": g, "normF": nf, "sweeps": sweeps, "ng_steps": steps,
                     "hosvd_won": start is A_}
 
 
@@ -627,15 +728,17 @@ class BKSResult:
 def bks(A: SymTensor, U0: np.ndarray, W0: np.ndarray, s: int = 2, p: int = 4,
         tol: float = 1e-10, max_outer: int = 500, variant: str = "bk",
         drop_tol: float = 1e-14, inner_tol: float | None = None,
-        max_inner: int = 1000, scale_free: bool = False) -> BKSResult:
+        max_inner: int = 1000, scale_free: bool = False,
+        inner_method: str = "ng") -> BKSResult:
     """Tensor Krylov-Schur for a (1,2)-symmetric tensor (Algorithm 5 with
     U = V, X = Y, Section 5).  Each outer iteration: one BK stage from
     (U0, W0) gives the G-gradient by Proposition 2 (steps (iii)-(iv)); stop
     if ||grad||/||F|| <= tol (Section 6.2); else finish the s-stage
     expansion (step (v)), form C = A.(X,X,Z) (eq. (tkd)), solve the inner
     problem (step (i)) to the same criterion, ||grad_C||/||F_C|| <= tol
-    (Section 6.2), and restart from U0 = X Uh, W0 = Z Wh (eq. (tks1), step
-    (ii)).  ``inner_tol`` replaces the inner tolerance when given.
+    (Section 6.2) by Newton-Grassmann (``inner_method`` "hooi": HOOI
+    sweeps), and restart from U0 = X Uh, W0 = Z Wh (eq. (tks1), step (ii)).
+    ``inner_tol`` replaces the inner tolerance when given.
     ``scale_free`` (this library's option) stops on ||grad||/||F||^2 <= tol
     instead, a test that does not change when A is scaled; the inner
     tolerance is then carried over through ||F|| (tol * ||F||)."""
@@ -656,8 +759,9 @@ def bks(A: SymTensor, U0: np.ndarray, W0: np.ndarray, s: int = 2, p: int = 4,
         hist[-1]["k1"], hist[-1]["k3"] = X.shape[1], Z.shape[1]
         Cc = core(A, X, Z)
         itol = inner_tol if inner_tol is not None else (tol * nf if scale_free else tol)
-        Uh, Wh, iinfo = inner_solve(Cc, r1, r3, itol, max_inner)
+        Uh, Wh, iinfo = inner_solve(Cc, r1, r3, itol, max_inner, method=inner_method)
         hist[-1]["inner_sweeps"] = iinfo["sweeps"]
+        hist[-1]["ng_steps"] = iinfo["ng_steps"]
         U = X @ Uh
         W = Z @ Wh
     return BKSResult(U, W, F, False, max_outer, hist[-1]["grad_rel"], hist[-1]["normF"], hist)
