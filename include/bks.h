@@ -72,8 +72,9 @@ extern "C" {
 #define BKS_VARIANT_MAX 2  /* max-BK, Table 2 */
 
 #define BKS_INNER_PAPER 0  /* inner solve as Section 6.2: truncated HOSVD + 5 HOOI sweeps,
-                              then sweeps to the outer stopping criterion */
-#define BKS_INNER_FAST  1  /* truncated HOSVD without start sweeps, inexact inner tolerance */
+                              then Newton-Grassmann to the outer stopping criterion */
+#define BKS_INNER_FAST  1  /* truncated HOSVD without start sweeps, HOOI sweeps to an inexact
+                              inner tolerance */
 
 typedef struct bks_tensor bks_tensor;
 
@@ -204,10 +205,12 @@ typedef struct {
                           replaced by FP64 projections of the stage-1 results) */
   int inner_schedule;  /* BKS_INNER_PAPER (default) or BKS_INNER_FAST: the inner solve of
                           Algorithm 5 step (i).  Both start from the better (larger ||F||) of
-                          the truncated HOSVD of C and the current point and continue with
-                          HOOI sweeps; PAPER gives the HOSVD start 5 sweeps first and solves
-                          to the outer tolerance (Section 6.2), FAST gives it none and stops
-                          at the inexact tolerance above (fewer sweeps, same optimum) */
+                          the truncated HOSVD of C and the current point.  PAPER (Section 6.2)
+                          gives the HOSVD start 5 HOOI sweeps, then takes Newton-Grassmann
+                          steps (a HOOI sweep where the Hessian is not negative definite or
+                          ||F|| would drop) to the outer tolerance; FAST takes HOOI sweeps to
+                          the inexact tolerance above.  info.inner_sweeps counts sweeps and
+                          Newton steps */
 } bks_params;
 
 typedef struct {

@@ -12,11 +12,13 @@
 // their eigenvectors are computed in FP32 (k_hosvd); the sweeps, the
 // gradient and every result are FP64.
 #include <algorithm>
+#include <cmath>
 
 #include <cooperative_groups.h>
 
 #include "common.cuh"
 #include "jacobi.cuh"
+#include "newton.cuh"
 
 namespace bks {
 
@@ -489,6 +491,7 @@ struct CoopArgs {
   double* negU;
   double* negW;
   double* info;
+  int from_current;   // 1: continue from (Ug, Wg) as given (no start candidates)
 };
 
 __device__ __forceinline__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
@@ -629,6 +632,8 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_coop(CoopArgs a) {
   extern __shared__ double shd[];
   InnerShared& S = *reinterpret_cast<InnerShared*>(shd);
   const int nu = a.k1 * a.r1, nw = a.k3 * a.r3;
+  bool hosvd_won = false;
+  if (!a.from_current) {  // uniform over the grid (a kernel argument)
   // candidate 1: truncated HOSVD (+ init sweeps).  Its FP32 eigenvectors
   // are orthonormalised in FP64 first: ||F|| is compared between points of
   // the Stiefel manifolds, and a start whose columns are longer than one
@@ -655,13 +660,16 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_coop(CoopArgs a) {
   grid.sync();
   coop_sweeps(a, 0, 0.0, S, grid);
   const double nf_b = a.ctl[1];
-  const bool hosvd_won = nf_a >= nf_b;
+  hosvd_won = nf_a >= nf_b;
   grid.sync();
   if (hosvd_won) {
     for (int64_t x = gtid(); x < nu; x += gsize()) a.Ug[x] = a.Ub[x];
     for (int64_t x = gtid(); x < nw; x += gsize()) a.Wg[x] = a.Wb[x];
   }
   grid.sync();
+  }
+  // HOOI sweeps to the tolerance (none with max_inner = 0: the contractions
+  // and the gradient at the current point are still formed)
   const int done = coop_sweeps(a, a.max_inner, a.tol, S, grid);
   if (blockIdx.x == 0) {
     for (int x = threadIdx.x; x < nu; x += blockDim.x) {
@@ -684,16 +692,23 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_coop(CoopArgs a) {
 }  // namespace
 
 struct InnerWork {
-  DevBuf part1, part3, Uh0, Wh0, D, E, Ug, Wg, Ub, Wb, T1, T3, ctl, K;
+  DevBuf part1, part3, Uh0, Wh0, D, E, Ug, Wg, Ub, Wb, Uo, Wo, T1, T3, ctl, K;
   int coop_grid = 0;
+  NewtonWork ng;
+  double host_info[4] = {0, 0, 0, 0};
+  int host_flag = 0;
 };
 
 // Inner solve: C (k1 x k1 x k3, FP64, device) -> Uh (k1 x r1), Wh (k3 x r3),
 // their negatives (for the restart combine) and info[4] = {grad, ||F||,
-// sweeps, hosvd_won} on the device.
+// sweeps (HOOI sweeps plus Newton steps), hosvd_won} on the device.  The
+// start is the better of the truncated HOSVD (after init_sweeps HOOI
+// sweeps) and the current point; then, with `newton`, Newton-Grassmann
+// steps (newton.cu) to the tolerance, a HOOI sweep wherever a step is
+// refused; without, HOOI sweeps.  At most max_inner sweeps and steps.
 int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int max_inner,
-                int init_sweeps, double* Uh, double* Wh, double* negU, double* negW, double* info,
-                cudaStream_t s) {
+                int init_sweeps, bool newton, double* Uh, double* Wh, double* negU, double* negW,
+                double* info, cudaStream_t s) {
   if (k1 > 128 || k3 > 128) return fail(BKS_EUNSUPPORTED, "inner solve: k1, k3 must be <= 128");
   if (r1 > kMaxR || r3 > kMaxR) return fail(BKS_EUNSUPPORTED, "inner solve: r1, r3 must be <= 8");
   // workspace of the calling thread on the current device
@@ -729,7 +744,7 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
                                        r1, r3, w.Uh0.as<double>(), w.Wh0.as<double>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   const size_t mat = sizeof(double) * 128 * kMaxR;
-  for (DevBuf* b : {&w.Ug, &w.Wg, &w.Ub, &w.Wb})
+  for (DevBuf* b : {&w.Ug, &w.Wg, &w.Ub, &w.Wb, &w.Uo, &w.Wo})
     if (b->bytes < mat) { BKS_TRY(b->alloc(mat, s)); b->persist(); }
   const size_t tsz = sizeof(double) * 128 * kMaxW;
   for (DevBuf* b : {&w.T1, &w.T3})
@@ -753,17 +768,79 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   const int64_t work = std::max<int64_t>((int64_t)k1 * k1 * r3, (int64_t)k1 * k3 * r1);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(w.coop_grid, (work + 511) / 512));
   CoopArgs a;
-  a.C = C; a.k1 = k1; a.k3 = k3; a.r1 = r1; a.r3 = r3; a.tol = tol; a.max_inner = max_inner;
+  a.C = C; a.k1 = k1; a.k3 = k3; a.r1 = r1; a.r3 = r3; a.tol = tol;
+  a.max_inner = newton ? 0 : max_inner;
   a.init_sweeps = std::max(0, init_sweeps); a.Uh0 = w.Uh0.as<double>(); a.Wh0 = w.Wh0.as<double>();
   a.Ug = w.Ug.as<double>(); a.Wg = w.Wg.as<double>(); a.Ub = w.Ub.as<double>();
   a.Wb = w.Wb.as<double>(); a.D = w.D.as<double>(); a.E = w.E.as<double>();
   a.T1 = w.T1.as<double>(); a.T3 = w.T3.as<double>(); a.ctl = w.ctl.as<double>();
   a.P = w.K.as<double>(); a.R = a.P + kMaxW * kMaxW; a.E2 = a.R + kMaxW * kMaxW;
   a.Uh_out = Uh; a.Wh_out = Wh; a.negU = negU; a.negW = negW; a.info = info;
-  void* kargs[] = {&a};
-  BKS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_inner_coop, dim3(grid),
-                                           dim3(kInnerThreads), kargs, sizeof(InnerShared), s));
-  ::bks::note_launch();
+  a.from_current = 0;
+  auto launch = [&]() -> int {
+    void* kargs[] = {&a};
+    BKS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_inner_coop, dim3(grid),
+                                             dim3(kInnerThreads), kargs, sizeof(InnerShared), s));
+    ::bks::note_launch();
+    return BKS_OK;
+  };
+  // the start (truncated HOSVD with its start sweeps, or the current point)
+  // and, without Newton, the HOOI sweeps to the tolerance
+  BKS_TRY(launch());
+  if (!newton) return BKS_OK;
+  // Newton-Grassmann continuation: a step is taken when -H is positive
+  // definite and ||F|| does not drop, else one HOOI sweep from the point
+  auto read_state = [&](bool with_flag) -> int {
+    BKS_CUDA_TRY(cudaMemcpyAsync(w.host_info, info, sizeof(w.host_info), cudaMemcpyDeviceToHost, s));
+    if (with_flag)
+      BKS_CUDA_TRY(cudaMemcpyAsync(&w.host_flag, w.ng.flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BKS_CUDA_TRY(cudaStreamSynchronize(s));
+    return BKS_OK;
+  };
+  BKS_TRY(w.ng.ensure(k1, k3, r1, r3, s));
+  BKS_TRY(read_state(false));
+  double g = w.host_info[0], nf = w.host_info[1];
+  const double start_sweeps = w.host_info[2], hosvd_won = w.host_info[3];
+  int steps = 0, sweeps = 0;
+  const int64_t nu = (int64_t)k1 * r1, nw = (int64_t)k3 * r3;
+  a.from_current = 1;
+  while (std::isfinite(g) && g > tol * nf && steps + sweeps < max_inner) {
+    BKS_TRY(newton_step(w.D.as<double>(), w.T1.as<double>(), w.E.as<double>(), w.T3.as<double>(),
+                        w.Ug.as<double>(), w.Wg.as<double>(), k1, k3, r1, r3, w.Ub.as<double>(),
+                        w.Wb.as<double>(), w.ng, s));
+    // keep the point, move to the step and evaluate it there
+    BKS_CUDA_TRY(cudaMemcpyAsync(w.Uo.p, w.Ug.p, sizeof(double) * nu, cudaMemcpyDeviceToDevice, s));
+    BKS_CUDA_TRY(cudaMemcpyAsync(w.Wo.p, w.Wg.p, sizeof(double) * nw, cudaMemcpyDeviceToDevice, s));
+    BKS_CUDA_TRY(cudaMemcpyAsync(w.Ug.p, w.Ub.p, sizeof(double) * nu, cudaMemcpyDeviceToDevice, s));
+    BKS_CUDA_TRY(cudaMemcpyAsync(w.Wg.p, w.Wb.p, sizeof(double) * nw, cudaMemcpyDeviceToDevice, s));
+    a.max_inner = 0;
+    a.tol = 0.0;
+    BKS_TRY(launch());
+    BKS_TRY(read_state(true));
+    const double gn = w.host_info[0], nfn = w.host_info[1];
+    if (w.host_flag == 0 && std::isfinite(gn) && nfn >= nf * (1.0 - 1e-14)) {
+      g = gn;
+      nf = nfn;
+      ++steps;
+      continue;
+    }
+    // refused: back to the point, one HOOI sweep
+    BKS_CUDA_TRY(cudaMemcpyAsync(w.Ug.p, w.Uo.p, sizeof(double) * nu, cudaMemcpyDeviceToDevice, s));
+    BKS_CUDA_TRY(cudaMemcpyAsync(w.Wg.p, w.Wo.p, sizeof(double) * nw, cudaMemcpyDeviceToDevice, s));
+    a.max_inner = 1;
+    BKS_TRY(launch());
+    BKS_TRY(read_state(false));
+    g = w.host_info[0];
+    nf = w.host_info[1];
+    ++sweeps;
+  }
+  // info[2]: the HOOI sweeps (start and refused steps) plus the Newton steps
+  w.host_info[0] = g;
+  w.host_info[1] = nf;
+  w.host_info[2] = start_sweeps + sweeps + steps;
+  w.host_info[3] = hosvd_won;
+  BKS_CUDA_TRY(cudaMemcpyAsync(info, w.host_info, sizeof(w.host_info), cudaMemcpyHostToDevice, s));
+  BKS_CUDA_TRY(cudaStreamSynchronize(s));
   return BKS_OK;
 }
 

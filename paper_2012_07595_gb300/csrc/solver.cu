@@ -354,16 +354,17 @@ struct BksState {
     // inner tolerance (the inner test is ||grad_C|| / ||F_C||; with the
     // scale-free outer test the tolerance is carried over through ||F||).
     // BKS_INNER_PAPER (Section 6.2): the truncated HOSVD start gets 5 HOOI
-    // sweeps and the inner problem is solved to the outer criterion.
-    // BKS_INNER_FAST: no start sweeps and an inexact inner solve, a hundred
-    // times below the current outer gradient and at least a tenth of the
-    // outer tolerance.  inner_tol > 0 replaces either tolerance.
+    // sweeps, then Newton-Grassmann steps solve the inner problem to the
+    // outer criterion.  BKS_INNER_FAST: no start sweeps, HOOI sweeps and an
+    // inexact inner solve, a hundred times below the current outer
+    // gradient and at least a tenth of the outer tolerance.  inner_tol > 0
+    // replaces either tolerance.
     const double otol = P.tol_scale_free ? cur_tol * last_nf : cur_tol;
     const bool fast = P.inner_schedule == BKS_INNER_FAST;
     const double itol = P.inner_tol > 0 ? P.inner_tol
                         : fast ? std::max(0.1 * otol, 0.01 * last_grad_rel) : otol;
     BKS_TRY(inner_solve(C.as<double>(), k1, k3, r1, r3, itol, P.max_inner,
-                        fast ? 0 : kInnerStartSweeps, Uh.as<double>(), Wh.as<double>(),
+                        fast ? 0 : kInnerStartSweeps, !fast, Uh.as<double>(), Wh.as<double>(),
                         negU.as<double>(), negW.as<double>(), inner_info.as<double>(), s));
     BKS_CUDA_TRY(cudaEventRecord(ev[1], s));
     // U0 <- X Uh, W0 <- Z Wh (eq. (tks1)), in place in the first columns

@@ -138,10 +138,11 @@ def test_example1_bks_hooi_agree_with_oracle(rho):
 
 @pytest.mark.parametrize("seed", [101])
 def test_fast_inner_schedule_reaches_the_oracle_optimum(seed):
-    """BKS_INNER_FAST (no HOOI sweeps after the HOSVD start, inexact inner
-    tolerance) is a faster path to the same point: on the 300x300x100
-    planted workload it ends where the oracle (Section 6.2 inner schedule)
-    ends, ||F|| within 1e-10 relative and subspaces within 1e-8."""
+    """BKS_INNER_FAST (no HOOI sweeps after the HOSVD start, HOOI sweeps to
+    an inexact inner tolerance) reaches the same point as the Section 6.2
+    schedule (HOSVD, 5 HOOI sweeps, Newton-Grassmann to the outer
+    tolerance): on the 300x300x100 planted workload it ends where the
+    oracle ends, ||F|| within 1e-10 relative and subspaces within 1e-8."""
     bk = _bk()
     coo, _ = synth.small_planted(1)
     A = O.symmetrise(coo.m, coo.n, coo.i, coo.j, coo.k, coo.v)
@@ -158,9 +159,6 @@ def test_fast_inner_schedule_reaches_the_oracle_optimum(seed):
     assert abs(info["normF"] - ro.normF) <= 1e-10 * ro.normF
     assert O.sin_theta_max(ro.U, U.cpu().numpy()) < 1e-8
     assert O.sin_theta_max(ro.W, W.cpu().numpy()) < 1e-8
-    # the paper schedule does the start sweeps and solves to the outer
-    # tolerance: at least as many inner sweeps
-    assert paper["inner_sweeps"] >= info["inner_sweeps"]
     # paper mode follows the oracle's outer iteration
     assert abs(paper["iters"] - ro.iters) <= 1
 
@@ -252,3 +250,26 @@ def test_hooi_parity_with_the_oracle(prec):
     assert O.sin_theta_max(rh.W, W.cpu().numpy()) < 1e-8
     assert np.allclose(F.cpu().numpy(), O.core(A, U.cpu().numpy(), W.cpu().numpy()), rtol=0,
                        atol=1e-10 * rh.normF)
+
+
+def test_newton_inner_solve_on_a_near_degenerate_job():
+    """A very sparse batched job (4,400 x 4,400 x 65, 2,462 stored entries,
+    rank 2) whose projected problems are nearly degenerate (nearly equal
+    S-values): HOOI inner solves stall at their sweep cap, while the
+    Section 6.2 schedule with Newton-Grassmann converges, on the GPU as in
+    the oracle, to the same optimum from the same start."""
+    bk = _bk()
+    job = synth.batch_jobs(seed=4, count=256, scale=0.25)[96]
+    c = synth.job_tensor(job)
+    A = O.symmetrise(c.m, c.n, c.i, c.j, c.k, c.v)
+    T = bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v)
+    g = synth.rng(1096)
+    U0 = synth.orthonormal(g, c.m, 2); W0 = synth.orthonormal(g, c.n, 2)
+    ro = O.bks(A, U0, W0, s=2, p=4, tol=1e-9, scale_free=True, max_outer=100)
+    prm = bk.BksParams(r1=2, r3=2, stages=2, block_p=4, tol=1e-9, tol_scale_free=1,
+                       max_outer=100)
+    U, W, F, info = bk.bks_solve(T, prm, _t(U0), _t(W0))
+    assert ro.converged and info["converged"]
+    assert abs(info["normF"] - ro.normF) <= 1e-10 * ro.normF
+    gg, nf, _ = O.gradient_global(A, U.cpu().numpy(), W.cpu().numpy())
+    assert gg / nf ** 2 <= 2e-9
