@@ -73,8 +73,8 @@ extern "C" {
 
 #define BKS_INNER_PAPER 0  /* inner solve as Section 6.2: truncated HOSVD + 5 HOOI sweeps,
                               then Newton-Grassmann to the outer stopping criterion */
-#define BKS_INNER_FAST  1  /* truncated HOSVD without start sweeps, HOOI sweeps to an inexact
-                              inner tolerance */
+#define BKS_INNER_FAST  1  /* truncated HOSVD without start sweeps, up to 20 HOOI sweeps, then
+                              Newton-Grassmann, to an inexact inner tolerance */
 
 typedef struct bks_tensor bks_tensor;
 
@@ -208,9 +208,10 @@ typedef struct {
                           the truncated HOSVD of C and the current point.  PAPER (Section 6.2)
                           gives the HOSVD start 5 HOOI sweeps, then takes Newton-Grassmann
                           steps (a HOOI sweep where the Hessian is not negative definite or
-                          ||F|| would drop) to the outer tolerance; FAST takes HOOI sweeps to
-                          the inexact tolerance above.  info.inner_sweeps counts sweeps and
-                          Newton steps */
+                          ||F|| would drop) to the outer tolerance; FAST takes up to 20 HOOI
+                          sweeps, then Newton-Grassmann steps, to the inexact tolerance above
+                          (cheap on well-separated problems, quadratic where HOOI creeps).
+                          info.inner_sweeps counts sweeps and Newton steps */
 } bks_params;
 
 typedef struct {

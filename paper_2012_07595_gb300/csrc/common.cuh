@@ -275,7 +275,7 @@ int contract_core_x(const bks_tensor* t, const double* U, int64_t ldu, int r1, c
                     int64_t ldw, int r3, double* F, bool fp32, cudaStream_t s);
 // inner solve (inner.cu)
 int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int max_inner,
-                int init_sweeps, bool newton, double* Uh, double* Wh, double* negU, double* negW, double* info,
+                int init_sweeps, int newton_after, double* Uh, double* Wh, double* negU, double* negW, double* info,
                 cudaStream_t s);
 
 }  // namespace bks

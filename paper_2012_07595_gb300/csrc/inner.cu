@@ -703,12 +703,14 @@ struct InnerWork {
 // their negatives (for the restart combine) and info[4] = {grad, ||F||,
 // sweeps (HOOI sweeps plus Newton steps), hosvd_won} on the device.  The
 // start is the better of the truncated HOSVD (after init_sweeps HOOI
-// sweeps) and the current point; then, with `newton`, Newton-Grassmann
-// steps (newton.cu) to the tolerance, a HOOI sweep wherever a step is
-// refused; without, HOOI sweeps.  At most max_inner sweeps and steps.
+// sweeps) and the current point; then HOOI sweeps towards the tolerance,
+// at most newton_after of them when newton_after >= 0, after which
+// Newton-Grassmann steps (newton.cu) continue to the tolerance, a HOOI
+// sweep wherever a step is refused; newton_after < 0: HOOI sweeps only.
+// At most max_inner sweeps and steps.
 int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int max_inner,
-                int init_sweeps, bool newton, double* Uh, double* Wh, double* negU, double* negW,
-                double* info, cudaStream_t s) {
+                int init_sweeps, int newton_after, double* Uh, double* Wh, double* negU,
+                double* negW, double* info, cudaStream_t s) {
   if (k1 > 128 || k3 > 128) return fail(BKS_EUNSUPPORTED, "inner solve: k1, k3 must be <= 128");
   if (r1 > kMaxR || r3 > kMaxR) return fail(BKS_EUNSUPPORTED, "inner solve: r1, r3 must be <= 8");
   // workspace of the calling thread on the current device
@@ -768,8 +770,9 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   const int64_t work = std::max<int64_t>((int64_t)k1 * k1 * r3, (int64_t)k1 * k3 * r1);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(w.coop_grid, (work + 511) / 512));
   CoopArgs a;
+  const bool newton = newton_after >= 0;
   a.C = C; a.k1 = k1; a.k3 = k3; a.r1 = r1; a.r3 = r3; a.tol = tol;
-  a.max_inner = newton ? 0 : max_inner;
+  a.max_inner = newton ? std::min(max_inner, newton_after) : max_inner;
   a.init_sweeps = std::max(0, init_sweeps); a.Uh0 = w.Uh0.as<double>(); a.Wh0 = w.Wh0.as<double>();
   a.Ug = w.Ug.as<double>(); a.Wg = w.Wg.as<double>(); a.Ub = w.Ub.as<double>();
   a.Wb = w.Wb.as<double>(); a.D = w.D.as<double>(); a.E = w.E.as<double>();
@@ -801,7 +804,7 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   BKS_TRY(read_state(false));
   double g = w.host_info[0], nf = w.host_info[1];
   const double start_sweeps = w.host_info[2], hosvd_won = w.host_info[3];
-  int steps = 0, sweeps = 0;
+  int steps = 0, sweeps = (int)start_sweeps - (hosvd_won != 0.0 ? a.init_sweeps : 0);
   const int64_t nu = (int64_t)k1 * r1, nw = (int64_t)k3 * r3;
   a.from_current = 1;
   while (std::isfinite(g) && g > tol * nf && steps + sweeps < max_inner) {
@@ -837,7 +840,7 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   // info[2]: the HOOI sweeps (start and refused steps) plus the Newton steps
   w.host_info[0] = g;
   w.host_info[1] = nf;
-  w.host_info[2] = start_sweeps + sweeps + steps;
+  w.host_info[2] = (hosvd_won != 0.0 ? a.init_sweeps : 0) + sweeps + steps;
   w.host_info[3] = hosvd_won;
   BKS_CUDA_TRY(cudaMemcpyAsync(info, w.host_info, sizeof(w.host_info), cudaMemcpyHostToDevice, s));
   BKS_CUDA_TRY(cudaStreamSynchronize(s));

@@ -17,6 +17,7 @@ namespace {
 constexpr int kBasisCap = 128;   // k1, k3 <= 128 (inner solve limit)
 constexpr int kBlockMax = 32;    // columns of one contraction result
 constexpr int kInnerStartSweeps = 5;  // HOOI sweeps after the HOSVD start (Section 6.2)
+constexpr int kFastHooiSweeps = 20;   // fast schedule: HOOI sweeps before Newton takes over
 
 __global__ void k_f3w(const double* __restrict__ H1, int r1, int r3, double* __restrict__ F3wT) {
   // F3wT (w3 x r3, ld w3): row tri(a,b), column c = w_ab F[a,b,c], F[a,b,c] = H1[a + r1(b + r1 c)]
@@ -355,16 +356,17 @@ struct BksState {
     // scale-free outer test the tolerance is carried over through ||F||).
     // BKS_INNER_PAPER (Section 6.2): the truncated HOSVD start gets 5 HOOI
     // sweeps, then Newton-Grassmann steps solve the inner problem to the
-    // outer criterion.  BKS_INNER_FAST: no start sweeps, HOOI sweeps and an
-    // inexact inner solve, a hundred times below the current outer
-    // gradient and at least a tenth of the outer tolerance.  inner_tol > 0
-    // replaces either tolerance.
+    // outer criterion.  BKS_INNER_FAST: no start sweeps, up to 20 HOOI
+    // sweeps, then Newton-Grassmann, to an inexact tolerance a hundred
+    // times below the current outer gradient and at least a tenth of the
+    // outer tolerance.  inner_tol > 0 replaces either tolerance.
     const double otol = P.tol_scale_free ? cur_tol * last_nf : cur_tol;
     const bool fast = P.inner_schedule == BKS_INNER_FAST;
     const double itol = P.inner_tol > 0 ? P.inner_tol
                         : fast ? std::max(0.1 * otol, 0.01 * last_grad_rel) : otol;
     BKS_TRY(inner_solve(C.as<double>(), k1, k3, r1, r3, itol, P.max_inner,
-                        fast ? 0 : kInnerStartSweeps, !fast, Uh.as<double>(), Wh.as<double>(),
+                        fast ? 0 : kInnerStartSweeps, fast ? kFastHooiSweeps : 0,
+                        Uh.as<double>(), Wh.as<double>(),
                         negU.as<double>(), negW.as<double>(), inner_info.as<double>(), s));
     BKS_CUDA_TRY(cudaEventRecord(ev[1], s));
     // U0 <- X Uh, W0 <- Z Wh (eq. (tks1)), in place in the first columns

@@ -1,7 +1,8 @@
 """Batched solves, the serving loop and the work-tile autotuner on the GPU.
 
 A job's result must be the same whether it runs alone or among others
-(within the mixed-precision tolerance 1e-6 in the subspace angle), and the
+(within 1e-6 in the subspace angle wherever the stopping criterion fixes
+the subspace to that), and the
 host-side failure paths (over-budget submission, cancellation, a bad job
 among good ones) must not disturb the rest."""
 import numpy as np
@@ -34,12 +35,16 @@ def _sin(a, b):
     return O.sin_theta_max(np.asarray(a), np.asarray(b))
 
 
-def _determined(F, mode):
-    """The mode's subspace is unique only when its last S-value
-    (Section 2.6) is clearly nonzero; with a zero S-value a column of the
-    factor is arbitrary and two correct runs may differ there."""
+def _angle_bound(F, mode, tol=1e-9):
+    """How far the stopping criterion fixes a factor's subspace.  Turning
+    the mode's last column by an angle t changes ||F||^2 by about
+    sigma^2 t^2, sigma the mode's last S-value (Section 2.6), so a point
+    whose gradient is at most tol ||F||^2 (Section 2.5) lies within an
+    angle of about tol ||F||^2 / sigma^2 of the maximiser.  With a zero or
+    tiny S-value the subspace is not fixed and two correct runs may differ
+    there."""
     sv = O.s_values(np.asarray(F))[mode]
-    return sv[-1] > 1e-6 * sv[0]
+    return tol * float((sv ** 2).sum()) / max(float(sv[-1]) ** 2, 1e-300)
 
 
 def _oracle_check(c, U, W, F, normF, tol):
@@ -63,10 +68,10 @@ def _oracle_check(c, U, W, F, normF, tol):
 
 def _same_solution(a, b, Fa):
     assert abs(a["normF"] - b["normF"]) <= 1e-9 * a["normF"]
-    if _determined(Fa, 0):
-        assert _sin(a["U"], b["U"]) < 1e-6
-    if _determined(Fa, 2):
-        assert _sin(a["W"], b["W"]) < 1e-6
+    for key, mode in (("U", 0), ("W", 2)):
+        bound = _angle_bound(Fa, mode)
+        if bound <= 1e-4:
+            assert _sin(a[key], b[key]) < max(1e-6, 10 * bound), (key, bound)
 
 
 def test_autotune_keeps_results():
