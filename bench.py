@@ -422,19 +422,25 @@ def large_workload(bk, torch, stream, flush, hbm, peak_kind):
                        precision=bk.BKS_PREC_MIXED, mixed_tol=1e-4, refine_sweeps=50,
                        max_outer=200, inner_schedule=bk.BKS_INNER_FAST)
     U0, W0 = torch.tensor(U0h, device="cuda"), torch.tensor(W0h, device="cuda")
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    U, W, F, info = bk.bks_solve(T, prm, U0, W0, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    solve = {"seconds": e0.elapsed_time(e1) / 1e3, "converged": info["converged"],
-             "iters": info["iters"], "fp32_iters": info["fp32_iters"], "k1": info["k1"],
-             "k3": info["k3"], "grad_rel": info["grad_rel"], "normF": info["normF"],
-             "phase_ms": info["phase_ms"],
-             "params": "rank (5,5,5), BK(2,4), ||grad||/||F||^2 <= 1e-9, mixed then FP64 "
-                       "refinement, fast inner schedule"}
+    solve = {}
+    for name, sched in (("fast", bk.BKS_INNER_FAST), ("paper", bk.BKS_INNER_PAPER)):
+        prm.inner_schedule = sched
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        U, W, F, info = bk.bks_solve(T, prm, U0, W0, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        solve[name] = {"seconds": e0.elapsed_time(e1) / 1e3, "converged": info["converged"],
+                       "iters": info["iters"], "fp32_iters": info["fp32_iters"],
+                       "inner_sweeps": info["inner_sweeps"], "k1": info["k1"], "k3": info["k3"],
+                       "grad_rel": info["grad_rel"], "normF": info["normF"],
+                       "phase_ms": info["phase_ms"]}
+    solve["params"] = ("rank (5,5,5), BK(2,4), ||grad||/||F||^2 <= 1e-9, mixed then FP64 "
+                       "refinement; fast: up to 20 HOOI sweeps then Newton-Grassmann to an "
+                       "inexact inner tolerance; paper: HOSVD + 5 HOOI sweeps then "
+                       "Newton-Grassmann to the outer tolerance (Section 6.2)")
     T.close()
     return roofline, kernels, solve
 
@@ -469,7 +475,8 @@ def ncu_case(args):
         U0h, W0h = start_matrices(coo.m, coo.n, w["r"])
         prm = bk.BksParams(r1=w["r"], r3=w["r"], stages=w["stages"], block_p=w["block_p"],
                            tol=w["tol"], precision=bk.BKS_PREC_MIXED, mixed_tol=w["mixed_tol"],
-                           tol_scale_free=w["tol_scale_free"], refine_sweeps=50, max_outer=500)
+                           tol_scale_free=w["tol_scale_free"], refine_sweeps=50, max_outer=500,
+                           inner_schedule=bk.BKS_INNER_FAST)
         for rep in range(2):
             c0 = bk.bks_launch_count()
             bk.bks_solve(T, prm, torch.tensor(U0h, device="cuda"), torch.tensor(W0h, device="cuda"))
@@ -494,12 +501,14 @@ def _sin_max(A, B):
     return float(np.linalg.norm(D, 2)) if D.size else 0.0
 
 
-def _determined(F, mode, rel=1e-6):
-    """A mode's subspace is unique when its last S-value (Section 2.6) is
-    clearly above zero."""
+def _angle_bound(F, mode, tol=1e-9):
+    """The subspace angle to which the stopping criterion fixes a factor:
+    turning the mode's last column by t changes ||F||^2 by about
+    sigma^2 t^2, sigma its last S-value (Section 2.6), so a gradient of at
+    most tol ||F||^2 leaves an angle of about tol ||F||^2 / sigma^2."""
     Fk = np.moveaxis(np.asarray(F), mode, 0).reshape(F.shape[mode], -1)
-    sv = np.sqrt(np.maximum(np.linalg.eigvalsh(Fk @ Fk.T), 0.0))
-    return sv[0] > 0 and sv[0] > rel * sv[-1]
+    ev = np.maximum(np.linalg.eigvalsh(Fk @ Fk.T), 0.0)
+    return tol * float(ev.sum()) / max(float(ev[0]), 1e-300)
 
 
 def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
@@ -507,8 +516,9 @@ def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
     tiles autotuned per size class) on the job-size law of the batched
     workload at `scale`, mixed precision at the scale-free tolerance 1e-9,
     against the same jobs solved one at a time in FP64; every job's result
-    compared with its FP64 solution (sin of the largest principal angle,
-    modes whose last S-value is zero skipped).  Then the serving loop on a
+    compared with its FP64 solution from the same seeded start (sin of the
+    largest principal angle, over the modes the stopping criterion fixes
+    to 1e-4 or better).  Then the serving loop on a
     Poisson stream of jobs drawn the same way: an offered-rate sweep below
     the measured service rate (latency = service time plus the queueing of
     a stable system) and the nominal 200 requests/s."""
@@ -517,30 +527,36 @@ def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
 
     def prm(r, prec):
         return bk.BksParams(r1=r, r3=r, stages=2, block_p=4, tol=1e-9, tol_scale_free=1,
-                            precision=prec, mixed_tol=1e-4, refine_sweeps=50, max_outer=200,
+                            precision=prec, mixed_tol=1e-4, refine_sweeps=300, max_outer=300,
                             max_inner=200, inner_schedule=bk.BKS_INNER_FAST)
 
     tens = [bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v) for c in coos]
+    # one seeded start per job, shared by the batched and the FP64 solves
+    U0s, W0s = [], []
+    for q, (c, j) in enumerate(zip(coos, jobs)):
+        g = synth.rng(1000 + q)
+        U0s.append(torch.tensor(synth.orthonormal(g, c.m, j["r"]), device="cuda"))
+        W0s.append(torch.tensor(synth.orthonormal(g, c.n, j["r"]), device="cuda"))
     for T in tens[:4]:
         bk.bks_tensor_autotune(T)   # warm the library's kernels
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = bk.bks_batch_solve(tens, [prm(j["r"], bk.BKS_PREC_MIXED) for j in jobs],
+    res = bk.bks_batch_solve(tens, [prm(j["r"], bk.BKS_PREC_MIXED) for j in jobs], U0s, W0s,
                              nstreams=8, autotune=True, stream=stream)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     seq, seq_lat = [], []
     t0 = time.perf_counter()
-    for T, j in zip(tens, jobs):
+    for T, j, U0, W0 in zip(tens, jobs, U0s, W0s):
         t1 = time.perf_counter()
         try:
-            seq.append(bk.bks_solve(T, prm(j["r"], bk.BKS_PREC_FP64), stream=stream))
+            seq.append(bk.bks_solve(T, prm(j["r"], bk.BKS_PREC_FP64), U0, W0, stream=stream))
         except bk.BksError as e:
             seq.append(None)
         torch.cuda.synchronize()
         seq_lat.append(time.perf_counter() - t1)
     t_seq = time.perf_counter() - t0
-    errs, failed = [], []
+    errs, failed, loose = [], [], 0
     for q, (r, sq, j) in enumerate(zip(res, seq, jobs)):
         U, W, F, info, st = r
         if st != 0:
@@ -552,10 +568,11 @@ def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
             continue
         F64 = sq[2].cpu().numpy()
         e = 0.0
-        if _determined(F64, 0):
-            e = max(e, _sin_max(sq[0].cpu().numpy(), U.cpu().numpy()))
-        if _determined(F64, 2):
-            e = max(e, _sin_max(sq[1].cpu().numpy(), W.cpu().numpy()))
+        for mode, A64, B in ((0, sq[0], U), (2, sq[1], W)):
+            if _angle_bound(F64, mode) <= 1e-4:
+                e = max(e, _sin_max(A64.cpu().numpy(), B.cpu().numpy()))
+            else:
+                loose += 1
         errs.append(e)
     ok = n_batch - len(failed)
     batched = {"jobs": n_batch, "ok": ok, "solves_per_s": n_batch / t_batch,
@@ -565,9 +582,10 @@ def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
                "nnz_stored_total": int(sum(T.nnz for T in tens)),
                "subspace_sin_vs_fp64": {"max": max(errs) if errs else None,
                                         "median": float(np.median(errs)) if errs else None,
-                                        "jobs_compared": len(errs)},
+                                        "jobs_compared": len(errs),
+                                        "modes_not_fixed_by_tolerance": loose},
                "failed": failed[:20]}
-    del tens
+    del tens, U0s, W0s
     seq_sorted = sorted(seq_lat)
     one_at_a_time = {"p50_s": seq_sorted[len(seq_sorted) // 2],
                      "p99_s": seq_sorted[min(len(seq_sorted) - 1, int(0.99 * len(seq_sorted)))],
