@@ -87,7 +87,7 @@ typedef struct bks_tensor bks_tensor;
  *   v         : values of type vdtype (BKS_F32 or BKS_F64)
  *   flags     : BKS_MIRROR adds the mirror (j,i,k,v) of each off-diagonal
  *               entry.  The stored list is the input in input order, then
- *               the mirrors in input order, stably sorted by (i,k,j);
+ *               the mirrors in input order, stably sorted by (i,j,k);
  *               entries with equal (i,j,k) are summed left to right in
  *               vdtype; exact zeros are kept.  BKS_VALIDATE_SYMMETRIC
  *               (without MIRROR) rejects a summed tensor that is not
@@ -109,7 +109,7 @@ void bks_tensor_destroy(bks_tensor* t);
 int bks_tensor_info(const bks_tensor* t, int64_t* m, int64_t* n,
                     int64_t* nnz_stored, double* fro2);
 
-/* Copy the stored tensor in its canonical order (sorted by (i,k,j)) into
+/* Copy the stored tensor in its canonical order (sorted by (i,j,k)) into
  * caller device buffers of nnz_stored entries each; v has the input
  * vdtype.  Used for bit-exact checks of the ingest. */
 int bks_tensor_export_coo(const bks_tensor* t, int32_t* i, int32_t* j,

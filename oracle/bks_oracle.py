@@ -48,7 +48,7 @@ __all__ = [
 # ----------------------------------------------------------------------------
 @dataclasses.dataclass
 class SymTensor:
-    """Canonical stored form: entries sorted by (i, k, j), duplicates summed,
+    """Canonical stored form: entries sorted by (i, j, k), duplicates summed,
     both halves present.  ``v`` keeps the input value dtype (the sums are
     taken in that dtype); arithmetic below promotes to float64."""
     m: int
@@ -82,7 +82,7 @@ def symmetrise(m, n, i, j, k, v, mirror=True, validate=False) -> SymTensor:
     library's reading: with ``mirror`` the stored list is every input entry
     in input order followed by the mirror (j, i, k, v) of every input entry
     with i != j, again in input order (diagonal entries are not mirrored).
-    The list is stably sorted by the key (i, k, j) and entries with equal
+    The list is stably sorted by the key (i, j, k) and entries with equal
     keys are summed left to right in the value dtype; exact zeros are kept.
     Without ``mirror`` the input must already hold both halves; with
     ``validate`` the summed tensor must satisfy A(i,j,k) == A(j,i,k)
@@ -105,7 +105,7 @@ def symmetrise(m, n, i, j, k, v, mirror=True, validate=False) -> SymTensor:
         vv = np.concatenate([v, v[off]])
     else:
         ii, jj, kk, vv = i, j, k, v
-    order = np.lexsort((jj, kk, ii))          # stable: primary i, then k, then j
+    order = np.lexsort((kk, jj, ii))          # stable: primary i, then j, then k
     ii, jj, kk, vv = ii[order], jj[order], kk[order], vv[order]
     if ii.size == 0:
         return SymTensor(m, n, ii.astype(np.int32), jj.astype(np.int32),

@@ -51,7 +51,7 @@ def threads() -> int:
 
 
 def csr_rowptr(A) -> np.ndarray:
-    """Row pointers of a stored tensor (entries sorted by (i, k, j))."""
+    """Row pointers of a stored tensor (entries sorted by (i, j, k))."""
     return np.searchsorted(A.i, np.arange(A.m + 1), side="left").astype(np.int64)
 
 

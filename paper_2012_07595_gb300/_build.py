@@ -12,8 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbks_gb300.so")
-SOURCES = ["scan.cu", "ingest.cu", "contract.cu", "dense.cu", "inner.cu", "newton.cu", "solver.cu",
-           "tune.cu", "serve.cu"]
+SOURCES = ["scan.cu", "ingest.cu", "contract.cu", "contract_tile_f32.cu", "contract_tile_f32d.cu",
+           "contract_tile_f64.cu", "dense.cu", "inner.cu", "newton.cu", "solver.cu", "tune.cu",
+           "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-diag-suppress", "177,550"]

@@ -1,9 +1,10 @@
 // Sparse tensor x dense block contractions (Section 2.2; Algorithm 3 step
 // (i); Section 4.3.1) and the cores F = A.(U,U,W), C = A.(X,X,Z)
-// (eq. (Rayleigh), eq. (tkd)).
+// (eq. (Rayleigh), eq. (tkd)): the front end (operand packing, column
+// chunks, cores); the tile kernels are in contract_tile_impl.cuh.
 //
 // Layout.  The stored tensor has two sorted copies: rows i (entries sorted
-// by (k, j) inside a row) for the mode-1 contraction, and rows k (sorted by
+// by (j, k) inside a row) for the mode-1 contraction, and rows k (sorted by
 // (i, j)) for the mode-3 contraction and the cores.  A contraction writes
 // one output row per tensor row, so the work is a segmented reduction over
 // the entries of each row:
@@ -11,6 +12,10 @@
 //   out_row[a + p*b] = sum over the row's entries e of v_e * A[ia_e, a] * B[ib_e, b]
 //
 // with (A, ia, B, ib) = (X, j, Y, k) for mode 1 and (X, i, X2, j) for mode 3.
+// Sorting a mode-1 row by j puts the entries that gather the same X row
+// next to each other (a long row of a power-law tensor meets each frequent
+// j under many k), so that the lanes of one step share cache lines; Y has
+// only n rows and is read from shared memory.
 //
 // Kernel design (work plan in common.cuh): rows longer than `split` are cut
 // into pieces whose partial sums a second kernel adds in a fixed order.
@@ -29,13 +34,11 @@
 // costs one 8-64 byte gather per operand.
 #include <algorithm>
 
-#include "common.cuh"
+#include "contract_tile.cuh"
 
 namespace bks {
 
 namespace {
-
-template <typename T, int W> struct VecLoad;
 
 // ---- pack a column-major m x p block into row-major m x PB (zero padded)
 template <typename IT, typename T>
@@ -45,119 +48,6 @@ __global__ void k_pack(const IT* __restrict__ X, int64_t ldx, int64_t rows, int 
        r += (int64_t)gridDim.x * blockDim.x) {
     for (int a = 0; a < PB; ++a) out[r * PB + a] = a < p ? (T)X[r + ldx * a] : T(0);
   }
-}
-
-// Row stride of a packed operand of (bucket) width N: FP32 rows are padded
-// to 2, 4 or 8 values so that a row is one or two aligned vector loads (a
-// 3-wide row is one float4, a 5-wide row one float4 and one float); FP64
-// rows keep 3 and 5 values (those kernels are bound by the FP64 pipe, not
-// by loads).
-template <typename T, int N>
-struct RowStride {
-  static constexpr int v = sizeof(T) == 4 ? (N <= 2 ? 2 : N <= 4 ? 4 : 8) : N;
-};
-template <typename T> inline int row_stride(int N) {
-  return sizeof(T) == 4 ? (N <= 2 ? 2 : N <= 4 ? 4 : 8) : N;
-}
-
-// The first N values of a packed row (stride RowStride<T, N>): one 32-byte
-// load for 8-float rows, 16-byte vector loads when rows are 16-byte aligned
-// (the unused tail of the last vector is padding of the row), else 8-byte
-// loads for FP32, else scalar.
-// One 32-byte row (8 floats, 32-byte aligned) by a single 256-bit load
-// (sm_100 and later): one request per gathered row instead of two.
-__device__ __forceinline__ void ldg_v8(const float* __restrict__ p, float (&v)[8]) {
-  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
-                 "=f"(v[6]), "=f"(v[7])
-               : "l"(p));
-}
-
-template <typename T, int N>
-__device__ __forceinline__ void load_row(const T* __restrict__ base, T (&x)[N]) {
-  constexpr int S = RowStride<T, N>::v;
-  if constexpr (sizeof(T) == 4 && S == 8) {
-    float v[8];
-    ldg_v8(reinterpret_cast<const float*>(base), v);
-#pragma unroll
-    for (int u = 0; u < N; ++u) x[u] = v[u];
-  } else if constexpr ((sizeof(T) * S) % 16 == 0) {
-    constexpr int V = (int)(16 / sizeof(T));
-    constexpr int NV = (N + V - 1) / V;  // NV V <= S: S is a multiple of V and S >= N
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-      const float4 q = __ldg(reinterpret_cast<const float4*>(base) + t);
-      const T* qq = reinterpret_cast<const T*>(&q);
-#pragma unroll
-      for (int u = 0; u < V; ++u)
-        if (t * V + u < N) x[t * V + u] = qq[u];
-    }
-  } else if constexpr (sizeof(T) == 4 && S % 2 == 0) {
-#pragma unroll
-    for (int t = 0; t < N / 2; ++t) {
-      const float2 q = __ldg(reinterpret_cast<const float2*>(base) + t);
-      x[2 * t] = q.x;
-      x[2 * t + 1] = q.y;
-    }
-  } else {
-#pragma unroll
-    for (int t = 0; t < N; ++t) x[t] = __ldg(base + t);
-  }
-}
-
-// accumulator shape: TRI -> upper triangle of PB x PB, else PB x QB
-template <int PB, int QB, bool TRI>
-struct Shape {
-  static constexpr int W = TRI ? PB * (PB + 1) / 2 : PB * QB;
-};
-
-template <typename T, int PB, int QB, bool TRI>
-__device__ __forceinline__ void accumulate(T (&acc)[Shape<PB, QB, TRI>::W], T v,
-                                           const T (&xa)[PB], const T (&xb)[TRI ? PB : QB]) {
-  T va[PB];
-#pragma unroll
-  for (int a = 0; a < PB; ++a) va[a] = v * xa[a];
-  if constexpr (TRI) {
-#pragma unroll
-    for (int b = 0; b < PB; ++b)
-#pragma unroll
-      for (int a = 0; a <= b; ++a) acc[a + b * (b + 1) / 2] = fma(va[a], xb[b], acc[a + b * (b + 1) / 2]);
-  } else {
-#pragma unroll
-    for (int b = 0; b < QB; ++b)
-#pragma unroll
-      for (int a = 0; a < PB; ++a) acc[a + PB * b] = fma(va[a], xb[b], acc[a + PB * b]);
-  }
-}
-
-struct TileArgs {
-  const int4* items;      // per work item (vorder order): first entry, end, row, slot
-  const int32_t* vorder;  // the nvec warp rows, then the short rows by decreasing length
-  const int32_t* vptr;
-  const int32_t* vrow;
-  const int32_t* vslot;
-  int32_t nvec, nshortv;
-  const int32_t* ia;   // index into operand A per entry
-  const int32_t* ib;   // index into operand B per entry
-  const int32_t* sia;  // the same for the lane-interleaved copy of the short rows
-  const int32_t* sib;
-};
-
-// One entry's products into acc: v * A[ia,:]^T B[ib,:].
-template <typename T, int PB, int QB, bool TRI>
-__device__ __forceinline__ void one_entry(int e, const int32_t* __restrict__ iap,
-                                          const int32_t* __restrict__ ibp,
-                                          const T* __restrict__ vals, const T* __restrict__ Ap,
-                                          const T* __restrict__ Bp,
-                                          T (&acc)[Shape<PB, QB, TRI>::W]) {
-  constexpr int NB = TRI ? PB : QB;
-  const int ia = __ldg(iap + e);
-  const int ib = __ldg(ibp + e);
-  const T v = __ldg(vals + e);
-  T xa[PB], xb[NB];
-  load_row<T, PB>(Ap + (int64_t)ia * RowStride<T, PB>::v, xa);
-  load_row<T, NB>(Bp + (int64_t)ib * RowStride<T, NB>::v, xb);
-  accumulate<T, PB, QB, TRI>(acc, v, xa, xb);
 }
 
 template <typename T>
@@ -172,273 +62,6 @@ __device__ __forceinline__ void load4(const T* __restrict__ p, T (&v)[4]) {
   }
 }
 
-template <typename T, typename OT, int PB, int QB, bool TRI>
-__device__ __forceinline__ void flush_row(int64_t row, int slot,
-                                          const T (&acc)[Shape<PB, QB, TRI>::W], int p, int q,
-                                          OT* __restrict__ out, int64_t ldo,
-                                          T* __restrict__ partial) {
-  constexpr int W = Shape<PB, QB, TRI>::W;
-  if (slot >= 0) {
-    T* dst = partial + (int64_t)slot * W;
-#pragma unroll
-    for (int c = 0; c < W; ++c) dst[c] = acc[c];
-    return;
-  }
-  if constexpr (TRI) {
-#pragma unroll
-    for (int b = 0; b < PB; ++b)
-#pragma unroll
-      for (int a = 0; a <= b; ++a)
-        if (b < p) out[row + ldo * (a + b * (b + 1) / 2)] = (OT)acc[a + b * (b + 1) / 2];
-  } else {
-#pragma unroll
-    for (int b = 0; b < QB; ++b)
-#pragma unroll
-      for (int a = 0; a < PB; ++a)
-        if (a < p && b < q) out[row + ldo * (a + p * b)] = (OT)acc[a + PB * b];
-  }
-}
-
-constexpr int kWarpsPerBlock = 4;
-
-constexpr int next_pow2(int x) { return x <= 1 ? 1 : 2 * next_pow2((x + 1) / 2); }
-
-// One level of a recursive-halving sum over the lanes: each lane holds N
-// values; the lanes with bit `o` set keep the upper half and receive it
-// from the partner lane (lane ^ o), the others keep the lower half, so that
-// every lane ends with N/2 sums.  With N = 1 the value is added as it is.
-template <typename T, int N>
-__device__ __forceinline__ void halve(T* a, int lane, int o) {
-  if constexpr (N >= 2) {
-    constexpr int H = N / 2;
-    const bool upper = (lane & o) != 0;
-#pragma unroll
-    for (int c = 0; c < H; ++c) {
-      const T send = upper ? a[c] : a[H + c];
-      const T keep = upper ? a[H + c] : a[c];
-      a[c] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  } else {
-    a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
-  }
-}
-
-// Warp sum of acc[W] (five halving levels, a fixed order), written to the
-// virtual row's output row or partial slot by the lanes that hold each sum.
-template <typename T, typename OT, int PB, int QB, bool TRI>
-__device__ __forceinline__ void warp_reduce_flush(int64_t row, int slot,
-                                                  const T (&acc)[Shape<PB, QB, TRI>::W], int p,
-                                                  int q, OT* __restrict__ out, int64_t ldo,
-                                                  T* __restrict__ partial, int lane) {
-  constexpr int W = Shape<PB, QB, TRI>::W;
-  constexpr int W2 = next_pow2(W);
-  T a[W2];
-#pragma unroll
-  for (int c = 0; c < W2; ++c) a[c] = c < W ? acc[c] : T(0);
-  halve<T, W2>(a, lane, 16);
-  halve<T, (W2 / 2 > 1 ? W2 / 2 : 1)>(a, lane, 8);
-  halve<T, (W2 / 4 > 1 ? W2 / 4 : 1)>(a, lane, 4);
-  halve<T, (W2 / 8 > 1 ? W2 / 8 : 1)>(a, lane, 2);
-  halve<T, (W2 / 16 > 1 ? W2 / 16 : 1)>(a, lane, 1);
-  // index of a[0] in this lane, and whether this lane is the first of the
-  // lanes that hold the same sums
-  int base = 0;
-  bool writer = true;
-  {
-    int n = W2;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      if (n >= 2) {
-        n >>= 1;
-        if (lane & o) base += n;
-      } else if (lane & o) {
-        writer = false;
-      }
-    }
-  }
-  if (!writer) return;
-  constexpr int R = W2 / 32 > 1 ? W2 / 32 : 1;
-#pragma unroll
-  for (int c = 0; c < R; ++c) {
-    const int idx = base + c;
-    if (idx >= W) continue;
-    if (slot >= 0) {
-      partial[(int64_t)slot * W + idx] = a[c];
-      continue;
-    }
-    if constexpr (TRI) {
-      int b = 0;
-      while ((b + 1) * (b + 2) / 2 <= idx) ++b;
-      if (b < p) out[row + ldo * idx] = (OT)a[c];
-    } else {
-      const int aa = idx % PB, bb = idx / PB;
-      if (aa < p && bb < q) out[row + ldo * (aa + p * bb)] = (OT)a[c];
-    }
-  }
-}
-
-// Mode-1 / mode-3 contraction over the work plan (see common.cuh):
-// warps [0, nvec) take one long virtual row each, the lanes striding over
-// its entries 4 at a time (coalesced index and value loads) and the lane
-// sums combined by warp_reduce_flush; the following warps take 32 short
-// virtual rows each, one per lane, ordered by decreasing length, each lane
-// summing its row in registers from the lane-interleaved copy (svals and
-// ta.sia / ta.sib), so that these loads are coalesced too.  No atomics:
-// the sums have a fixed order.
-template <typename T, typename OT, int PB, int QB, bool TRI>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ svals,
-           const T* __restrict__ Ap,
-           const T* __restrict__ Bp, int p, int q, OT* __restrict__ out, int64_t ldo,
-           T* __restrict__ partial) {
-  constexpr int W = Shape<PB, QB, TRI>::W;
-  constexpr int NB = TRI ? PB : QB;
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  T acc[W];
-#pragma unroll
-  for (int c = 0; c < W; ++c) acc[c] = T(0);
-  if (gw < ta.nvec) {
-    const int4 it = __ldg(ta.items + gw);
-    const int s = it.x, e = it.y;
-    int x = s + lane;
-    // software pipeline: the next group's indices and values are loaded
-    // while the current group's gathers are in flight
-    int iav[4], ibv[4];
-    T v[4];
-    if (x + 96 < e) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        iav[u] = __ldg(ta.ia + x + 32 * u);
-        ibv[u] = __ldg(ta.ib + x + 32 * u);
-        v[u] = __ldg(vals + x + 32 * u);
-      }
-    }
-    while (x + 96 < e) {
-      T xa[4][PB], xb[4][NB];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        load_row<T, PB>(Ap + (int64_t)iav[u] * RowStride<T, PB>::v, xa[u]);
-        load_row<T, NB>(Bp + (int64_t)ibv[u] * RowStride<T, NB>::v, xb[u]);
-      }
-      T vc[4] = {v[0], v[1], v[2], v[3]};
-      x += 128;
-      if (x + 96 < e) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          iav[u] = __ldg(ta.ia + x + 32 * u);
-          ibv[u] = __ldg(ta.ib + x + 32 * u);
-          v[u] = __ldg(vals + x + 32 * u);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, vc[u], xa[u], xb[u]);
-    }
-    for (; x < e; x += 32) one_entry<T, PB, QB, TRI>(x, ta.ia, ta.ib, vals, Ap, Bp, acc);
-    warp_reduce_flush<T, OT, PB, QB, TRI>(it.z, it.w, acc, p, q, out, ldo, partial, lane);
-    return;
-  }
-  const int sidx = (gw - ta.nvec) * 32 + lane;
-  if (sidx >= ta.nshortv) return;
-  // the row's entries in the lane-interleaved copy: it.x, it.x + 32, ... < it.y
-  // (the 32 lanes' loads of one step are consecutive)
-  const int4 it = __ldg(ta.items + ta.nvec + sidx);
-  const int e = it.y;
-  int x = it.x;
-  for (; x + 96 < e; x += 128) {
-    int iav[4], ibv[4];
-    T v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      iav[u] = __ldg(ta.sia + x + 32 * u);
-      ibv[u] = __ldg(ta.sib + x + 32 * u);
-      v[u] = __ldg(svals + x + 32 * u);
-    }
-    T xa[4][PB], xb[4][NB];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      load_row<T, PB>(Ap + (int64_t)iav[u] * RowStride<T, PB>::v, xa[u]);
-      load_row<T, NB>(Bp + (int64_t)ibv[u] * RowStride<T, NB>::v, xb[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) accumulate<T, PB, QB, TRI>(acc, v[u], xa[u], xb[u]);
-  }
-  for (; x < e; x += 32) one_entry<T, PB, QB, TRI>(x, ta.sia, ta.sib, svals, Ap, Bp, acc);
-  flush_row<T, OT, PB, QB, TRI>(it.z, it.w, acc, p, q, out, ldo, partial);
-}
-
-// number of warps of a plan
-inline int plan_warps(const Part& P) { return P.nvec + (P.nshortv + 31) / 32; }
-
-
-// s + y into the unevaluated sum s + c, the rounding error of s + y going
-// to c (TwoSum, Knuth's error-free transformation: exact in IEEE
-// arithmetic, no FMA contraction involved).
-template <typename T>
-__device__ __forceinline__ void two_sum_acc(T& s, T& c, T y) {
-  const T t = s + y;
-  const T bp = t - s;
-  c += (s - (t - bp)) + (y - bp);
-  s = t;
-}
-
-// Rows cut into pieces: add the pieces' partial sums in a fixed order, with
-// TwoSum compensation at both levels (pieces into 256 / W group sums, the
-// group sums into one), so that the error of a cut row does not grow with
-// its number of pieces.
-template <typename T, typename OT, int PB, int QB, bool TRI>
-__global__ void k_split_reduce(const int32_t* __restrict__ split_row,
-                               const int32_t* __restrict__ split_first, int nsplit,
-                               const T* __restrict__ partial, int p, int q, OT* __restrict__ out,
-                               int64_t ldo) {
-  constexpr int W = Shape<PB, QB, TRI>::W;
-  __shared__ T sh[256], shc[256];
-  const int s = blockIdx.x;
-  if (s >= nsplit) return;
-  const int f0 = split_first[s], f1 = split_first[s + 1];
-  const int groups = 256 / W;
-  const int c = threadIdx.x % W, g = threadIdx.x / W;
-  T acc = T(0), cmp = T(0);
-  if (g < groups)
-    for (int f = f0 + g; f < f1; f += groups) two_sum_acc(acc, cmp, partial[(int64_t)f * W + c]);
-  sh[threadIdx.x] = acc;
-  shc[threadIdx.x] = cmp;
-  __syncthreads();
-  if (threadIdx.x < W) {
-    T tot = T(0), tc = T(0);
-    for (int t = 0; t < groups; ++t) {
-      tc += shc[t * W + threadIdx.x];
-      two_sum_acc(tot, tc, sh[t * W + threadIdx.x]);
-    }
-    const int64_t row = split_row[s];
-    int col = -1;
-    if constexpr (TRI) {
-      int b = 0;
-      while ((b + 1) * (b + 2) / 2 <= c) ++b;
-      if (b < p) col = c;
-    } else {
-      int a = c % PB, b = c / PB;
-      if (a < p && b < q) col = a + p * b;
-    }
-    if (col >= 0) out[row + ldo * col] = (OT)(tot + tc);
-  }
-}
-
-template <typename T>
-__global__ void k_zero_rows(const int32_t* __restrict__ rows, int nrows, int w,
-                            T* __restrict__ out, int64_t ldo) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nrows * w;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int r = (int)(t % nrows), c = (int)(t / nrows);
-    out[rows[r] + ldo * c] = T(0);
-  }
-}
-
-inline int grid_for(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 32));
-}
-
 // Width buckets of the kernels: 1 -> 2, 2..5 as they are, 6..8 -> 8.  The
 // kernels multiply only the bucket width (3 x 4 is 12 products per entry,
 // 5 x 5 is 25), whatever the row stride.
@@ -447,83 +70,6 @@ template <typename T> int bucket_t(int x) { return bucket(x); }
 // Columns of the second operand per kernel call: the accumulators of one
 // output row (PB x QB) stay at most 32.
 inline int qchunk_of(int PB) { return PB <= 4 ? 8 : (PB == 5 ? 5 : 4); }
-
-template <typename T> const T* values_of(const Part& P, int vdtype);
-template <typename T> const T* sell_values_of(const Part& P);
-template <> const float* sell_values_of<float>(const Part& P) { return P.sv32.as<float>(); }
-template <> const double* sell_values_of<double>(const Part& P) { return P.sv64.as<double>(); }
-// the interleaved copy of the index array `a` (c0 or c1 of P)
-inline const int32_t* sell_of(const Part& P, const int32_t* a) {
-  return a == P.c0.as<int32_t>() ? P.sc0.as<int32_t>() : P.sc1.as<int32_t>();
-}
-template <> const float* values_of<float>(const Part& P, int vdtype) {
-  return vdtype == BKS_F32 ? P.v.as<float>() : P.v32.as<float>();
-}
-template <> const double* values_of<double>(const Part& P, int vdtype) {
-  return vdtype == BKS_F64 ? P.v.as<double>() : P.v64.as<double>();
-}
-
-// One launch pair (tile kernel + piece reduction) for fixed buckets.  The
-// partial sums of cut rows go to `part` (nslots x W values) when the caller
-// provides it, else to a stream-ordered allocation.
-template <typename T, typename OT, int PB, int QB, bool TRI>
-int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib,
-                    const T* Ap, const T* Bp, int p, int q, OT* out, int64_t ldo,
-                    T* part, cudaStream_t s) {
-  constexpr int W = Shape<PB, QB, TRI>::W;
-  TileArgs ta{P.vitems.as<int4>(), P.vorder.as<int32_t>(), P.vptr.as<int32_t>(),
-              P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib,
-              sell_of(P, ia), sell_of(P, ib)};
-  DevBuf partial;
-  if (P.nslots > 0 && !part) {
-    BKS_TRY(partial.alloc(sizeof(T) * (size_t)P.nslots * W, s));
-    part = partial.as<T>();
-  }
-  const int warps = kWarpsPerBlock;
-  const int blocks = (plan_warps(P) + warps - 1) / warps;
-  if (P.nv > 0) {
-    k_contract<T, OT, PB, QB, TRI><<<blocks, warps * 32, 0, s>>>(ta, values_of<T>(P, vdtype),
-                                                                 sell_values_of<T>(P), Ap,
-                                                                 Bp, p, q, out, ldo,
-                                                                 part); ::bks::note_launch();
-    BKS_CUDA_TRY(cudaGetLastError());
-  }
-  if (P.nsplit > 0) {
-    k_split_reduce<T, OT, PB, QB, TRI><<<P.nsplit, 256, 0, s>>>(
-        P.split_row.as<int32_t>(), P.split_first.as<int32_t>(), P.nsplit, part, p, q,
-        out, ldo); ::bks::note_launch();
-    BKS_CUDA_TRY(cudaGetLastError());
-  }
-  if (P.nempty > 0) {
-    const int w = TRI ? p * (p + 1) / 2 : p * q;
-    k_zero_rows<OT><<<grid_for((int64_t)P.nempty * w), 256, 0, s>>>(P.empty_rows.as<int32_t>(),
-                                                                    P.nempty, w, out, ldo); ::bks::note_launch();
-    BKS_CUDA_TRY(cudaGetLastError());
-  }
-  return BKS_OK;
-}
-
-template <typename T, typename OT>
-int dispatch(const Part& P, int vdtype, const int32_t* ia, const int32_t* ib, const T* Ap,
-             int PB, const T* Bp, int QB, bool tri, int p, int q, OT* out,
-             int64_t ldo, cudaStream_t s, T* part = nullptr) {
-#define BKS_CASE(pb, qb)                                                                      \
-  if (!tri && PB == pb && QB == qb)                                                           \
-    return launch_contract<T, OT, pb, qb, false>(P, vdtype, ia, ib, Ap, Bp, p, q, out, ldo,   \
-                                                 part, s);
-  BKS_CASE(2, 2) BKS_CASE(2, 3) BKS_CASE(2, 4) BKS_CASE(2, 5) BKS_CASE(2, 8)
-  BKS_CASE(3, 2) BKS_CASE(3, 3) BKS_CASE(3, 4) BKS_CASE(3, 5) BKS_CASE(3, 8)
-  BKS_CASE(4, 2) BKS_CASE(4, 3) BKS_CASE(4, 4) BKS_CASE(4, 5) BKS_CASE(4, 8)
-  BKS_CASE(5, 2) BKS_CASE(5, 3) BKS_CASE(5, 4) BKS_CASE(5, 5)
-  BKS_CASE(8, 2) BKS_CASE(8, 3) BKS_CASE(8, 4)
-#undef BKS_CASE
-#define BKS_TRI(pb)                                                                           \
-  if (tri && PB == pb)                                                                        \
-    return launch_contract<T, OT, pb, pb, true>(P, vdtype, ia, ib, Ap, Bp, p, p, out, ldo, part, s);
-  BKS_TRI(2) BKS_TRI(3) BKS_TRI(4) BKS_TRI(5) BKS_TRI(8)
-#undef BKS_TRI
-  return fail(BKS_EUNSUPPORTED, "contraction bucket not instantiated");
-}
 
 template <typename T, typename IT>
 int pack_into(const IT* X, int64_t ldx, int64_t rows, int p, int PB, T* dst, cudaStream_t s) {
@@ -589,7 +135,8 @@ int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
     BKS_TRY((pack_into<T, IT>(Y + ldy * q0, ldy, t->n, qq, row_stride<T>(QB), Yp, s)));
     // columns a + p*(q0 + b) of the full output start at column p*q0
     BKS_TRY((dispatch<T, OT>(t->m1, t->vdtype, t->m1.c1.as<int32_t>(), t->m1.c0.as<int32_t>(),
-                             Xp, PB, Yp, QB, false, p, qq, out + ldo * (p * q0), ldo, s, part)));
+                             Xp, PB, Yp, QB, t->n, false, p, qq, out + ldo * (p * q0), ldo, s,
+                             part)));
   }
   return BKS_OK;
 }
@@ -611,7 +158,7 @@ int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
   BKS_TRY((pack<T, IT>(X, ldx, t->m, p, row_stride<T>(PB), Xp, s)));
   if (!X2)
     return dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
-                           Xp.as<T>(), PB, Xp.as<T>(), PB, true, p, p, out, ldo, s);
+                           Xp.as<T>(), PB, Xp.as<T>(), PB, t->m, true, p, p, out, ldo, s);
   const int qchunk = qchunk_of(PB);
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
@@ -619,7 +166,7 @@ int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
     DevBuf X2p;
     BKS_TRY((pack<T, IT>(X2 + ldx2 * q0, ldx2, t->m, qq, row_stride<T>(QB), X2p, s)));
     BKS_TRY((dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
-                             Xp.as<T>(), PB, X2p.as<T>(), QB, false, p, qq,
+                             Xp.as<T>(), PB, X2p.as<T>(), QB, t->m, false, p, qq,
                              out + ldo * (p * q0), ldo, s)));
   }
   return BKS_OK;

@@ -37,18 +37,18 @@ __global__ void k_offdiag_flags(const int32_t* i, const int32_t* j, int64_t nnz,
 }
 
 // Expanded list: entries 0..nnz-1 are the input, nnz+t is the mirror of the
-// t-th off-diagonal input entry.  Key = (i << (bk+bj)) | (k << bj) | j.
+// t-th off-diagonal input entry.  Key = (i << (bj+bk)) | (j << bk) | k.
 __global__ void k_build_keys(const int32_t* i, const int32_t* j, const int32_t* k, int64_t nnz,
                              const int32_t* offpos, int mirror, int bj, int bk, uint64_t* keys,
                              uint32_t* pay, uint32_t* mirror_src) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
        e += (int64_t)gridDim.x * blockDim.x) {
     uint64_t a = (uint64_t)i[e], b = (uint64_t)j[e], c = (uint64_t)k[e];
-    keys[e] = (a << (bk + bj)) | (c << bj) | b;
+    keys[e] = (a << (bj + bk)) | (b << bk) | c;
     pay[e] = (uint32_t)e;
     if (mirror && a != b) {
       int64_t slot = nnz + offpos[e];
-      keys[slot] = (b << (bk + bj)) | (c << bj) | a;
+      keys[slot] = (b << (bj + bk)) | (a << bk) | c;
       pay[slot] = (uint32_t)slot;
       mirror_src[offpos[e]] = (uint32_t)e;
     }
@@ -84,9 +84,9 @@ __global__ void k_sum_runs(const uint64_t* keys, const uint32_t* pay, const int3
       acc = (t == s) ? x : add_rn(acc, x);
     }
     uint64_t key = keys[s];
-    row[u] = (int32_t)(key >> (bk + bj));
-    kk[u] = (int32_t)((key >> bj) & ((1ull << bk) - 1ull));
-    jj[u] = (int32_t)(key & ((1ull << bj) - 1ull));
+    row[u] = (int32_t)(key >> (bj + bk));
+    jj[u] = (int32_t)((key >> bk) & ((1ull << bj) - 1ull));
+    kk[u] = (int32_t)(key & ((1ull << bk) - 1ull));
     vout[u] = acc;
   }
 }
@@ -104,7 +104,7 @@ __global__ void k_row_ptr(const int32_t* row, int64_t nnz, int64_t rows, int32_t
 template <typename V>
 __global__ void k_check_symmetric(const int32_t* ptr, const int32_t* kk, const int32_t* jj,
                                   const V* v, int64_t m, int* bad) {
-  // entry (i, j, k) at row i; find (j, i, k) in row j by binary search on (k, j)
+  // entry (i, j, k) at row i; find (j, i, k) in row j by binary search on (j, k)
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) {
@@ -112,7 +112,7 @@ __global__ void k_check_symmetric(const int32_t* ptr, const int32_t* kk, const i
       int32_t lo = ptr[j], hi = ptr[j + 1];
       while (lo < hi) {
         int32_t mid = (lo + hi) >> 1;
-        bool less = kk[mid] < k || (kk[mid] == k && jj[mid] < (int32_t)i);
+        bool less = jj[mid] < (int32_t)i || (jj[mid] == (int32_t)i && kk[mid] < k);
         if (less) lo = mid + 1; else hi = mid;
       }
       bool ok = lo < ptr[j + 1] && kk[lo] == k && jj[lo] == (int32_t)i;
@@ -372,9 +372,9 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   P.rows = m;
   const int64_t S = std::max<int64_t>(nseg, 1);
   BKS_TRY(row.alloc(sizeof(int32_t) * S, s));
-  BKS_TRY(P.c0.alloc(sizeof(int32_t) * S, s));
-  BKS_TRY(P.c1.alloc(sizeof(int32_t) * S, s));
-  BKS_TRY(P.v.alloc(sizeof(V) * S, s));
+  BKS_TRY(P.c0.alloc(sizeof(int32_t) * (S + kStreamPad), s));
+  BKS_TRY(P.c1.alloc(sizeof(int32_t) * (S + kStreamPad), s));
+  BKS_TRY(P.v.alloc(sizeof(V) * (S + kStreamPad), s));
   if (nseg > 0)
     k_sum_runs<V><<<grid_for(nseg), 256, 0, s>>>(keys.as<uint64_t>(), pay.as<uint32_t>(),
                                                  starts.as<int32_t>(), nseg, N, dv,
@@ -400,10 +400,10 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   }
   // value copies in the other precision
   if (sizeof(V) == 8) {
-    BKS_TRY(P.v32.alloc(sizeof(float) * S, s));
+    BKS_TRY(P.v32.alloc(sizeof(float) * (S + kStreamPad), s));
     k_convert<double, float><<<grid_for(nseg), 256, 0, s>>>((const double*)P.v.p, P.v32.as<float>(), nseg); ::bks::note_launch();
   } else {
-    BKS_TRY(P.v64.alloc(sizeof(double) * S, s));
+    BKS_TRY(P.v64.alloc(sizeof(double) * (S + kStreamPad), s));
     k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)P.v.p, P.v64.as<double>(), nseg); ::bks::note_launch();
   }
   BKS_CUDA_TRY(cudaGetLastError());
@@ -420,9 +420,9 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   // mode-3 copy sorted by (k, i, j)
   Part& Q = T->m3;
   Q.rows = n;
-  BKS_TRY(Q.c0.alloc(sizeof(int32_t) * S, s));
-  BKS_TRY(Q.c1.alloc(sizeof(int32_t) * S, s));
-  BKS_TRY(Q.v.alloc(sizeof(V) * S, s));
+  BKS_TRY(Q.c0.alloc(sizeof(int32_t) * (S + kStreamPad), s));
+  BKS_TRY(Q.c1.alloc(sizeof(int32_t) * (S + kStreamPad), s));
+  BKS_TRY(Q.v.alloc(sizeof(V) * (S + kStreamPad), s));
   {
     DevBuf krow;
     BKS_TRY(krow.alloc(sizeof(int32_t) * S, s));
@@ -443,10 +443,10 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (sizeof(V) == 8) {
-    BKS_TRY(Q.v32.alloc(sizeof(float) * S, s));
+    BKS_TRY(Q.v32.alloc(sizeof(float) * (S + kStreamPad), s));
     k_convert<double, float><<<grid_for(nseg), 256, 0, s>>>((const double*)Q.v.p, Q.v32.as<float>(), nseg); ::bks::note_launch();
   } else {
-    BKS_TRY(Q.v64.alloc(sizeof(double) * S, s));
+    BKS_TRY(Q.v64.alloc(sizeof(double) * (S + kStreamPad), s));
     k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)Q.v.p, Q.v64.as<double>(), nseg); ::bks::note_launch();
   }
   BKS_CUDA_TRY(cudaGetLastError());

@@ -160,3 +160,23 @@ def test_ragged_widths_and_leading_dimensions():
     assert rel_err(out3f.cpu().numpy(), O.mode3(A, Xh[:, :2], X2.cpu().numpy())) < 1e-13
     F = bk.bks_core(T, X, Y).cpu().numpy()
     assert rel_err(F, O.core(A, Xh, Yh)) < 1e-12
+
+
+@pytest.mark.parametrize("p,q", [(3, 4), (5, 5), (8, 2)])
+def test_many_items_per_warp(p, q):
+    """A tensor with more warp items than the persistent grid has warps, so
+    that every warp takes several items in turn, element by element against
+    the oracle in FP64, mode 1 and mode 3."""
+    import torch
+    bk = _bk()
+    c = synth.zipf_tensor(6, 300_000, 40, 1_600_000, 1.1)
+    A = O.symmetrise(c.m, c.n, c.i, c.j, c.k, c.v)
+    T = bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v)
+    g = synth.rng(17)
+    X = g.standard_normal((c.m, p))
+    Y = g.standard_normal((c.n, q))
+    got = bk.bks_contract_mode1(T, torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"))
+    assert rel_err(got.cpu().numpy(), O.mode1(A, X, Y)) < 1e-13
+    got3 = bk.bks_contract_mode3(T, torch.tensor(X, device="cuda"))
+    assert rel_err(got3.cpu().numpy(), O.mode3(A, X)) < 1e-13
+    T.close()

@@ -9,17 +9,17 @@ import synth
 def dict_model(m, n, i, j, k, v, mirror=True):
     """Mirror rule written out with a dict: entries in input order, then the
     mirrors of the off-diagonal entries in input order; equal keys summed left
-    to right in the value dtype; sorted by (i, k, j)."""
+    to right in the value dtype; sorted by (i, j, k)."""
     seq = list(zip(i.tolist(), j.tolist(), k.tolist(), list(v)))
     if mirror:
         seq = seq + [(b, a, c, x) for (a, b, c, x) in seq if a != b]
     acc = {}
     for a, b, c, x in seq:
-        key = (a, c, b)
+        key = (a, b, c)
         acc[key] = x if key not in acc else acc[key] + x
     keys = sorted(acc)
-    return (np.array([t[0] for t in keys]), np.array([t[2] for t in keys]),
-            np.array([t[1] for t in keys]), np.array([acc[t] for t in keys], dtype=v.dtype))
+    return (np.array([t[0] for t in keys]), np.array([t[1] for t in keys]),
+            np.array([t[2] for t in keys]), np.array([acc[t] for t in keys], dtype=v.dtype))
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
