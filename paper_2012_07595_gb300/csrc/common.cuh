@@ -92,10 +92,6 @@ struct DevBuf {
 // loops of nearly equal trip count; longer ones are processed one per warp
 // with the lanes striding over the entries.  The sizes are per tensor
 // (defaults below; bks_tensor_autotune picks them by timing).
-// Entry arrays (indices and values of a sorted copy) carry this many
-// elements past their end, so that bulk copies of whole 16-byte units
-// stay inside the allocation; the padding is never used in arithmetic.
-constexpr int64_t kStreamPad = 16;
 constexpr int kTile = 32;
 constexpr int kSplit = 512;
 // Default plan by size (measured on GB300 Zipf tensors, FP32 mode-1 calls

@@ -372,9 +372,9 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   P.rows = m;
   const int64_t S = std::max<int64_t>(nseg, 1);
   BKS_TRY(row.alloc(sizeof(int32_t) * S, s));
-  BKS_TRY(P.c0.alloc(sizeof(int32_t) * (S + kStreamPad), s));
-  BKS_TRY(P.c1.alloc(sizeof(int32_t) * (S + kStreamPad), s));
-  BKS_TRY(P.v.alloc(sizeof(V) * (S + kStreamPad), s));
+  BKS_TRY(P.c0.alloc(sizeof(int32_t) * S, s));
+  BKS_TRY(P.c1.alloc(sizeof(int32_t) * S, s));
+  BKS_TRY(P.v.alloc(sizeof(V) * S, s));
   if (nseg > 0)
     k_sum_runs<V><<<grid_for(nseg), 256, 0, s>>>(keys.as<uint64_t>(), pay.as<uint32_t>(),
                                                  starts.as<int32_t>(), nseg, N, dv,
@@ -400,10 +400,10 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   }
   // value copies in the other precision
   if (sizeof(V) == 8) {
-    BKS_TRY(P.v32.alloc(sizeof(float) * (S + kStreamPad), s));
+    BKS_TRY(P.v32.alloc(sizeof(float) * S, s));
     k_convert<double, float><<<grid_for(nseg), 256, 0, s>>>((const double*)P.v.p, P.v32.as<float>(), nseg); ::bks::note_launch();
   } else {
-    BKS_TRY(P.v64.alloc(sizeof(double) * (S + kStreamPad), s));
+    BKS_TRY(P.v64.alloc(sizeof(double) * S, s));
     k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)P.v.p, P.v64.as<double>(), nseg); ::bks::note_launch();
   }
   BKS_CUDA_TRY(cudaGetLastError());
@@ -420,9 +420,9 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   // mode-3 copy sorted by (k, i, j)
   Part& Q = T->m3;
   Q.rows = n;
-  BKS_TRY(Q.c0.alloc(sizeof(int32_t) * (S + kStreamPad), s));
-  BKS_TRY(Q.c1.alloc(sizeof(int32_t) * (S + kStreamPad), s));
-  BKS_TRY(Q.v.alloc(sizeof(V) * (S + kStreamPad), s));
+  BKS_TRY(Q.c0.alloc(sizeof(int32_t) * S, s));
+  BKS_TRY(Q.c1.alloc(sizeof(int32_t) * S, s));
+  BKS_TRY(Q.v.alloc(sizeof(V) * S, s));
   {
     DevBuf krow;
     BKS_TRY(krow.alloc(sizeof(int32_t) * S, s));
@@ -443,10 +443,10 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
     BKS_CUDA_TRY(cudaGetLastError());
   }
   if (sizeof(V) == 8) {
-    BKS_TRY(Q.v32.alloc(sizeof(float) * (S + kStreamPad), s));
+    BKS_TRY(Q.v32.alloc(sizeof(float) * S, s));
     k_convert<double, float><<<grid_for(nseg), 256, 0, s>>>((const double*)Q.v.p, Q.v32.as<float>(), nseg); ::bks::note_launch();
   } else {
-    BKS_TRY(Q.v64.alloc(sizeof(double) * (S + kStreamPad), s));
+    BKS_TRY(Q.v64.alloc(sizeof(double) * S, s));
     k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)Q.v.p, Q.v64.as<double>(), nseg); ::bks::note_launch();
   }
   BKS_CUDA_TRY(cudaGetLastError());
