@@ -22,6 +22,15 @@ Pins (what fixes each function other than itself) live in
 * ``ng_model``/``ng_step`` -- finite differences of the pulled-back
                              objective; quadratic convergence; the same
                              optimum as HOOI.
+* ``s_values_gaps``        -- brute force with an explicit orthogonal
+                             complement and einsum; S-values of a planted
+                             exact-rank tensor are those of F0 with zero
+                             (r+1)-st values; invariance under a change of
+                             basis.
+* ``slice_norms``/``scale_slices`` -- closed-form largest eigenvalues of
+                             path, cycle, star and complete graphs; the
+                             Frobenius norm by a dict sum; scaled slices
+                             have unit norm and stay (1,2)-symmetric.
 * ``inner_solve``/``bks``/``hooi`` -- closed forms n=1 (Eckart-Young) and
                              rank-one slices, exact recovery of a planted
                              multilinear-rank tensor, monotone ||F||, and
@@ -40,6 +49,7 @@ __all__ = [
     "gradient_global", "inner_solve", "bks", "hooi", "sin_theta_max",
     "top_left_singular", "unfold1", "unfold3", "s_values", "tri_index",
     "BKSResult", "hosvd_truncated", "INNER_INIT_SWEEPS", "ng_model", "ng_step",
+    "s_values_gaps", "slice_norms", "slice_scales", "scale_slices",
 ]
 
 
@@ -502,6 +512,77 @@ def s_values(F: np.ndarray):
         ev = np.linalg.eigvalsh(Fk @ Fk.T)[::-1]
         out.append(np.sqrt(np.maximum(ev, 0.0)))
     return out
+
+
+def s_values_gaps(A: SymTensor, U: np.ndarray, W: np.ndarray):
+    """S-values and gaps of Section 2.6 at (U, U, W).
+
+    For k = 1 and 3 (mode 2 equals mode 1 by the (1,2)-symmetry):
+    s_i^(k) = sqrt(lambda_i(<F,F>_{-k})), i <= r_k, and
+    s_{r_k+1}^(k) = sqrt(lambda_max(<F_perp^k, F_perp^k>_{-k})) with
+    F_perp^1 = A.(U_perp, U, W) and F_perp^3 = A.(U, U, W_perp)
+    (Section 2.5), (U U_perp) orthogonal.  unfold_1(F_perp^1) is
+    U_perp^T T1 with T1 = unfold_1(A.(I, U, W)) (m x r1 r3), so
+    lambda_max(<F_perp^1, F_perp^1>_{-1}) = ||(I - U U^T) T1||_2^2; likewise
+    mode 3 with T3 = unfold_3(A.(U, U, I)) (n x r1^2).  Returns
+    (s1, s3, gap1, gap3), s1 holding r1 + 1 values and s3 r3 + 1, and
+    gap_k = s_{r_k}^(k) - s_{r_k+1}^(k)."""
+    T1 = mode1(A, U, W)
+    F = (U.T @ T1).reshape(U.shape[1], U.shape[1], W.shape[1], order="F")
+    sv = s_values(F)
+    P1 = T1 - U @ (U.T @ T1)
+    P3 = mode3(A, U, U)
+    P3 = P3 - W @ (W.T @ P3)
+    s1 = np.append(sv[0], np.linalg.norm(P1, 2) if P1.size else 0.0)
+    s3 = np.append(sv[2], np.linalg.norm(P3, 2) if P3.size else 0.0)
+    return s1, s3, float(s1[-2] - s1[-1]), float(s3[-2] - s3[-1])
+
+
+# ----------------------------------------------------------------------------
+# Slice normalisation (Section 7: slices of an adjacency tensor scaled so that
+# the largest eigenvalue of each is 1, or to unit Frobenius norm)
+# ----------------------------------------------------------------------------
+def slice_norms(A: SymTensor, kind: str) -> np.ndarray:
+    """Per frontal slice A(:,:,k) (a symmetric m x m matrix): "fro" the
+    Frobenius norm, "lmax" the largest eigenvalue (algebraic; for the
+    nonnegative slices of an adjacency tensor it is the spectral radius),
+    from the library eigensolver on the dense slice."""
+    out = np.zeros(A.n)
+    x = A.vf()
+    for kk in range(A.n):
+        sel = A.k == kk
+        if kind == "fro":
+            out[kk] = math.sqrt(float(np.dot(x[sel], x[sel])))
+        elif kind == "lmax":
+            if not sel.any():
+                continue
+            S = np.zeros((A.m, A.m))
+            np.add.at(S, (A.i[sel], A.j[sel]), x[sel])
+            out[kk] = float(np.linalg.eigvalsh(S)[-1])
+        else:
+            raise ValueError(kind)
+    return out
+
+
+def slice_scales(norms: np.ndarray) -> np.ndarray:
+    """Scale factor per slice: 1 / norm where the norm is positive, else 1
+    (an empty slice, or a slice whose largest eigenvalue is not positive,
+    keeps its values; this library's reading, the paper normalises
+    adjacency slices only)."""
+    norms = np.asarray(norms, dtype=np.float64)
+    sc = np.ones_like(norms)
+    pos = norms > 0
+    sc[pos] = 1.0 / norms[pos]
+    return sc
+
+
+def scale_slices(A: SymTensor, scales: np.ndarray) -> SymTensor:
+    """The stored tensor with slice k multiplied by scales[k]: each value
+    times its scale, rounded once to the value dtype (the order and the
+    entries are unchanged, so the result is still (1,2)-symmetric)."""
+    sc = np.asarray(scales, dtype=np.float64)[A.k]
+    v = (A.vf() * sc).astype(A.v.dtype)
+    return SymTensor(A.m, A.n, A.i.copy(), A.j.copy(), A.k.copy(), v)
 
 
 # ----------------------------------------------------------------------------
