@@ -366,6 +366,46 @@ void bks_server_destroy(bks_server* srv);
 /* Last error message of the calling thread ("" if none). */
 const char* bks_last_error_string(void);
 
+/* ---- conditioning diagnostics and slice normalisation (Sections 2.6, 7) ---- */
+
+/* S-values (Section 2.6) at the point (U, U, W) (U m x r1, W n x r3, both
+ * orthonormal, device, column-major with leading dimensions ldu, ldw; FP64):
+ *   s1[q] = sqrt(lambda_q(<F,F>_{-1})), q < r1, F = A.(U,U,W), and
+ *   s1[r1] = sqrt(lambda_max(<F_perp^1, F_perp^1>_{-1})), F_perp^1 =
+ *   A.(U_perp,U,W); s3 likewise for mode 3 with F_perp^3 = A.(U,U,W_perp).
+ *   (Mode 2 equals mode 1 by the symmetry.)  The gaps of Section 2.6 are
+ *   s1[r1-1] - s1[r1] and s3[r3-1] - s3[r3].
+ *   s1, s3 : HOST arrays of r1 + 1 and r3 + 1 doubles, descending for q < r.
+ * Cost: one mode-1 and one mode-3 FP64 contraction and tall-skinny passes;
+ * synchronises the stream.  Errors: BKS_EINVAL (null, r < 1, r >= m or n,
+ * r1 or r3 > 8, ld below the rows), BKS_ENOMEM, BKS_ECUDA. */
+int bks_s_values(const bks_tensor* t, const double* U, int64_t ldu, int r1,
+                 const double* W, int64_t ldw, int r3, double* s1, double* s3,
+                 void* stream);
+
+#define BKS_NORM_FRO  0  /* Frobenius norm of each frontal slice A(:,:,k) */
+#define BKS_NORM_LMAX 1  /* largest (algebraic) eigenvalue of each slice */
+
+/* Per-slice norms (Section 7): norms[k] for k < n, a DEVICE array of n
+ * doubles.  BKS_NORM_FRO: the Frobenius norm (fixed-order FP64 sum).
+ * BKS_NORM_LMAX: the largest eigenvalue of the symmetric slice by a batched
+ * Lanczos iteration (FP64, no reorthogonalisation, positive seeded start
+ * vectors); a slice stops when its estimate moves by at most 1e-13 of
+ * itself over 10 steps, at an invariant subspace, or after min(m, 400)
+ * steps; an empty slice gets 0.  Work memory: three m x nb FP64 blocks,
+ * nb slices at a time, at most 2 GB.  Synchronises the stream.
+ * Errors: BKS_EINVAL, BKS_ENOMEM, BKS_ECUDA. */
+int bks_slice_norms(const bks_tensor* t, int kind, double* norms, void* stream);
+
+/* A new tensor whose slice k is scales[k] times slice k of t (scales: DEVICE
+ * array of n doubles): every stored value times its slice's scale, rounded
+ * once to the value dtype; the order of the entries is unchanged.  With
+ * scales[k] = 1 / norms[k] from bks_slice_norms this is the slice
+ * normalisation of Section 7.  *out receives a handle the caller destroys.
+ * Synchronises the stream.  Errors as bks_tensor_create_coo. */
+int bks_tensor_scale_slices(const bks_tensor* t, const double* scales, void* stream,
+                            bks_tensor** out);
+
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all threads, all devices); a diagnostic counter for benchmarks. */
 uint64_t bks_launch_count(void);

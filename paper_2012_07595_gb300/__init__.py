@@ -26,13 +26,15 @@ __all__ = [
     "bks_contract_mode3", "bks_core", "bks_solve", "hooi_solve", "BksParams", "HooiParams",
     "col_major", "library_path", "bks_launch_count", "bks_tensor_autotune",
     "bks_tensor_set_tiles", "bks_batch_solve", "Server", "BKS_ECANCELED", "BKS_EPENDING",
-    "BKS_EBUDGET", "BKS_INNER_PAPER", "BKS_INNER_FAST", "bks_contract_mode1_noalloc",
+    "BKS_EBUDGET", "BKS_NORM_FRO", "BKS_NORM_LMAX", "bks_s_values", "bks_slice_norms",
+    "bks_tensor_scale_slices", "BKS_INNER_PAPER", "BKS_INNER_FAST", "bks_contract_mode1_noalloc",
 ]
 
 BKS_OK = 0
 BKS_EINVAL, BKS_ENOMEM, BKS_ECUDA, BKS_EASYM = -1, -2, -3, -4
 BKS_ENOTCONV, BKS_EBREAKDOWN, BKS_ENUMERIC, BKS_EUNSUPPORTED = -5, -6, -7, -8
 BKS_ECANCELED, BKS_EPENDING, BKS_EBUDGET = -9, -10, -11
+BKS_NORM_FRO, BKS_NORM_LMAX = 0, 1
 BKS_BATCH_AUTOTUNE = 1
 BKS_SERVE_AUTOTUNE = 1
 BKS_F32, BKS_F64 = 1, 2
@@ -157,6 +159,12 @@ def lib():
     L.bks_server_stats.restype = c_int
     L.bks_server_destroy.argtypes = [vp]
     L.bks_server_destroy.restype = None
+    L.bks_s_values.argtypes = [vp, vp, i64, c_int, vp, i64, c_int, vp, vp, vp]
+    L.bks_s_values.restype = c_int
+    L.bks_slice_norms.argtypes = [vp, c_int, vp, vp]
+    L.bks_slice_norms.restype = c_int
+    L.bks_tensor_scale_slices.argtypes = [vp, vp, vp, ctypes.POINTER(vp)]
+    L.bks_tensor_scale_slices.restype = c_int
     L.bks_launch_count.argtypes = []
     L.bks_launch_count.restype = ctypes.c_uint64
     L.bks_last_error_string.argtypes = []
@@ -277,7 +285,7 @@ def bks_tensor_info(t: Tensor):
 
 
 def bks_tensor_export_coo(t: Tensor, stream=None):
-    """Canonical stored entries (sorted by (i,k,j)) as torch CUDA tensors."""
+    """Canonical stored entries (sorted by (i,j,k)) as torch CUDA tensors."""
     import torch
     dt = torch.float64 if t.vdtype == BKS_F64 else torch.float32
     i = torch.empty(t.nnz, dtype=torch.int32, device="cuda")
@@ -289,6 +297,45 @@ def bks_tensor_export_coo(t: Tensor, stream=None):
                                        ctypes.c_void_p(k.data_ptr()),
                                        ctypes.c_void_p(v.data_ptr()), _stream(stream)))
     return i, j, k, v
+
+
+def bks_s_values(t: Tensor, U, W, stream=None):
+    """S-values of Section 2.6 at (U, U, W): (s1, s3, gap1, gap3) with s1
+    holding the r1 S-values of mode 1 and s_{r1+1}^(1) last (numpy), s3
+    likewise for mode 3, gap_k = s_{r_k}^(k) - s_{r_k+1}^(k)."""
+    import torch
+    U = col_major(U.to(device="cuda", dtype=torch.float64))
+    W = col_major(W.to(device="cuda", dtype=torch.float64))
+    r1, r3 = U.shape[1], W.shape[1]
+    s1 = np.zeros(r1 + 1)
+    s3 = np.zeros(r3 + 1)
+    _check(lib().bks_s_values(t.handle, ctypes.c_void_p(U.data_ptr()), _ld(U), r1,
+                              ctypes.c_void_p(W.data_ptr()), _ld(W), r3,
+                              s1.ctypes.data_as(ctypes.c_void_p), s3.ctypes.data_as(ctypes.c_void_p),
+                              _stream(stream)))
+    return s1, s3, float(s1[-2] - s1[-1]), float(s3[-2] - s3[-1])
+
+
+def bks_slice_norms(t: Tensor, kind: str = "fro", stream=None):
+    """Per-slice norms (Section 7) as a torch CUDA FP64 tensor of n values:
+    kind "fro" (Frobenius) or "lmax" (largest eigenvalue)."""
+    import torch
+    code = {"fro": BKS_NORM_FRO, "lmax": BKS_NORM_LMAX}[kind]
+    out = torch.empty(t.n, dtype=torch.float64, device="cuda")
+    _check(lib().bks_slice_norms(t.handle, code, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def bks_tensor_scale_slices(t: Tensor, scales, stream=None) -> Tensor:
+    """A new tensor with slice k scaled by scales[k] (n values)."""
+    import torch
+    sc = torch.as_tensor(scales, dtype=torch.float64).to("cuda").contiguous()
+    if sc.numel() != t.n:
+        raise ValueError("scales must have n entries")
+    h = ctypes.c_void_p()
+    _check(lib().bks_tensor_scale_slices(t.handle, ctypes.c_void_p(sc.data_ptr()), _stream(stream),
+                                         ctypes.byref(h)))
+    return Tensor(h, t.vdtype)
 
 
 def bks_contract_mode1(t: Tensor, X, Y, out=None, stream=None):
