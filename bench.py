@@ -296,7 +296,7 @@ def cpu_baseline_leg(coo, nnz_full, gpu_fp64_iters):
 # ---------------------------------------------------------------------------
 # DRAM bytes (read + write) of k_contract<float,float,4,4,0> in one ncu
 # capture of the 500,000 x 500,000 x 200 case (`--ncu-case mode1 --size mid`)
-MID_TRAFFIC_BYTES = 186_827_264 + 30_340_352
+MID_TRAFFIC_BYTES = 184_253_952 + 27_801_856
 MID_NNZ = 11_777_770
 LARGE = {"m": 1_000_000, "n": 200, "draws": 60_000_000, "zipf_s": 1.2, "seed": 3, "r": 5}
 
@@ -386,14 +386,14 @@ def large_workload(bk, torch, stream, flush, hbm, peak_kind):
                 "frac": alg / t / 1e9 / hbm}
 
     r44 = mode1(4, 4)
-    roofline = {"kernel": "bks_contract_mode1 FP32 (pack + k_contract<float,float,4,4> + piece "
-                          "reduction + zero rows)",
+    roofline = {"kernel": "bks_contract_mode1 FP32 (pack + k_contract<float,float,4,4,0,1> + "
+                          "piece reduction + zero rows)",
                 "workload": f"zipf1.2 (1,2)-symmetric 1e6 x 1e6 x 200, {nnz} stored "
                             f"({L['draws']} draws mirrored, duplicates summed), X 4 cols, Y 4 cols",
                 "bound": "hbm", "achieved": r44["GB_per_s"], "peak": hbm, "unit": "GB/s",
                 "frac": r44["frac"], "peak_kind": peak_kind,
                 "traffic": int(MID_TRAFFIC_BYTES * nnz / MID_NNZ),
-                "traffic_note": "ncu dram bytes of k_contract<float,float,4,4> on the 11.8M-entry "
+                "traffic_note": "ncu dram bytes of k_contract<float,float,4,4,0,1> on the 11.8M-entry "
                                 "case, scaled by stored entries",
                 "alg_bytes_per_launch": r44["alg_bytes"], "median_launch_s": r44["us"] * 1e-6,
                 "nnz_stored": nnz}
@@ -764,7 +764,7 @@ def main():
         + w["m"] * 12 * 4
     achieved = alg_bytes / kt / 1e9
     roofline_workload = {"kernel": "bks_contract_mode1 FP32 3 x 4 (pack + k_contract<float,float,"
-                                   "4,4> + piece reduction + zero rows)",
+                                   "3,4,0,1> + piece reduction + zero rows)",
                          "workload": w["workload"],
                          "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
