@@ -294,7 +294,7 @@ def cpu_baseline_leg(coo, nnz_full, gpu_fp64_iters):
 
 
 # ---------------------------------------------------------------------------
-# DRAM bytes (read + write) of k_contract<float,float,4,4,0> in one ncu
+# DRAM bytes (read + write) of k_contract<float,float,4,4,0,1> in one ncu
 # capture of the 500,000 x 500,000 x 200 case (`--ncu-case mode1 --size mid`)
 MID_TRAFFIC_BYTES = 184_253_952 + 27_801_856
 MID_NNZ = 11_777_770
