@@ -161,8 +161,14 @@ struct CorePlan {
   DevBuf lo, hi;      // int32 [nch]: entry range of each chunk
   DevBuf sl_k;        // int32 [nsl]: slice index k of each non-empty slice
   DevBuf sl_first;    // int32 [nsl+1]: first chunk of each non-empty slice
+  // runs: maximal ranges of entries with equal (k, i), cut at chunk starts
+  // and every 32 entries; the core sums v X[j, :] over a run before its
+  // outer product with X[i, :]
+  int32_t nruns = 0;
+  DevBuf run_start;   // int32 [nruns+1]: first entry of each run (nnz at the end)
+  DevBuf chunk_run;   // int32 [nch+1]: first run of each chunk
   void persist() {
-    for (DevBuf* b : {&lo, &hi, &sl_k, &sl_first}) b->persist();
+    for (DevBuf* b : {&lo, &hi, &sl_k, &sl_first, &run_start, &chunk_run}) b->persist();
   }
 };
 

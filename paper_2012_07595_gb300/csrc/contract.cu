@@ -239,7 +239,7 @@ __device__ __forceinline__ void load4_shared(const T* p, T (&x)[4]) {
 
 template <typename T, int TPT>
 __global__ void __launch_bounds__(kCoreThreads)
-k_core_chunks(const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ chunk_hi,
+k_core_chunks(const int32_t* __restrict__ chunk_run, const int32_t* __restrict__ run_start,
               const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
               const T* __restrict__ vals, const T* __restrict__ Xp, int K, int KP, int batch,
               int ngroups, T* __restrict__ Mpart) {
@@ -247,7 +247,7 @@ k_core_chunks(const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ 
   T* As = reinterpret_cast<T*>(smem_raw);          // [batch][KP]
   T* Bs = As + (size_t)batch * KP;                  // [batch][KP]
   const int ch = blockIdx.x;
-  const int lo = chunk_lo[ch], hi = chunk_hi[ch];
+  const int lo = chunk_run[ch], hi = chunk_run[ch + 1];  // the chunk's runs
   const int nt = KP / 4;                            // tiles per side
   const int ntiles = nt * (nt + 1) / 2;
   const int slots = kCoreThreads / ngroups;         // threads per group
@@ -275,15 +275,29 @@ k_core_chunks(const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ 
   for (int base = lo; base < hi; base += batch) {
     const int cnt = min(batch, hi - base);
     __syncthreads();
+    // run r of the batch: As[r] = X[i_r, :], Bs[r] = sum over the run's
+    // entries (in order) of v_e X[j_e, :]
     for (int t = threadIdx.x; t < cnt * nt; t += kCoreThreads) {
       const int e = t / nt, q = t % nt;
-      const int idx = base + e;
-      const T v = vals[idx];
-      T xa[4], xb[4];
-      load4(Xp + (int64_t)ii[idx] * KP + 4 * q, xa);
-      load4(Xp + (int64_t)jj[idx] * KP + 4 * q, xb);
+      const int e0 = run_start[base + e], e1 = run_start[base + e + 1];
+      T xa[4], xb[4] = {T(0), T(0), T(0), T(0)};
+      load4(Xp + (int64_t)ii[e0] * KP + 4 * q, xa);
+      int idx = e0;
+      for (; idx + 1 < e1; idx += 2) {  // two gathers in flight
+        T y0[4], y1[4];
+        const T v0 = vals[idx], v1 = vals[idx + 1];
+        load4(Xp + (int64_t)jj[idx] * KP + 4 * q, y0);
+        load4(Xp + (int64_t)jj[idx + 1] * KP + 4 * q, y1);
 #pragma unroll
-      for (int x = 0; x < 4; ++x) xa[x] *= v;
+        for (int x = 0; x < 4; ++x) xb[x] = fma(v1, y1[x], fma(v0, y0[x], xb[x]));
+      }
+      if (idx < e1) {
+        T y0[4];
+        const T v0 = vals[idx];
+        load4(Xp + (int64_t)jj[idx] * KP + 4 * q, y0);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) xb[x] = fma(v0, y0[x], xb[x]);
+      }
       store4_shared(As + e * KP + 4 * q, xa);
       store4_shared(Bs + e * KP + 4 * q, xb);
     }
@@ -429,9 +443,10 @@ int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* 
   if (attr != cudaSuccess)
     return fail(BKS_ECUDA, "k_core_chunks shared-memory limit not accepted");
   if (smem > kSmemMax) return fail(BKS_EUNSUPPORTED, "core: shared-memory tile above its limit");
-  kern<<<nch, kCoreThreads, smem, s>>>(cp.lo.as<int32_t>(), cp.hi.as<int32_t>(), P.c0.as<int32_t>(),
-                                       P.c1.as<int32_t>(), values_of<T>(P, t->vdtype), Xp.as<T>(),
-                                       r1, KP, batch, ngroups, Mp.as<T>()); ::bks::note_launch();
+  kern<<<nch, kCoreThreads, smem, s>>>(cp.chunk_run.as<int32_t>(), cp.run_start.as<int32_t>(),
+                                       P.c0.as<int32_t>(), P.c1.as<int32_t>(),
+                                       values_of<T>(P, t->vdtype), Xp.as<T>(), r1, KP, batch,
+                                       ngroups, Mp.as<T>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   const int64_t ntri = (int64_t)r1 * (r1 + 1) / 2;
   BKS_TRY(Sl.alloc(sizeof(T) * (size_t)cp.nsl * ntri, s));
@@ -441,6 +456,42 @@ int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* 
                                                                 cp.nsl, r1, W, ldw, r3, F); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   return BKS_OK;
+}
+
+// ---- run plan of the core ---------------------------------------------------
+// Runs: maximal ranges of equal (slice, i) of the mode-3 copy, cut at chunk
+// starts and after every kRunCap entries.
+constexpr int kRunCap = 32;
+
+// f[e] = 1 where i changes; chunk starts are set by k_mark_starts
+__global__ void k_run_flags(const int32_t* __restrict__ ii, int64_t nnz, int32_t* __restrict__ f) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    f[e] = (e == 0 || ii[e] != ii[e - 1]) ? 1 : 0;
+}
+__global__ void k_mark_starts(const int32_t* __restrict__ lo, int nch, int32_t* __restrict__ f) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x)
+    f[lo[c]] = 1;
+}
+__global__ void k_run_scatter(const int32_t* __restrict__ f, const int32_t* __restrict__ id,
+                              int64_t nnz, int32_t* __restrict__ start) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    if (f[e]) start[id[e]] = (int32_t)e;
+}
+// f2[e] = 1 where a run of f starts or kRunCap entries of it have passed
+__global__ void k_run_cap(const int32_t* __restrict__ f, const int32_t* __restrict__ id,
+                          const int32_t* __restrict__ start, int64_t nnz, int32_t* __restrict__ f2) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t run = id[e] - 1 + f[e];
+    f2[e] = (f[e] || (e - start[run]) % kRunCap == 0) ? 1 : 0;
+  }
+}
+__global__ void k_chunk_runs(const int32_t* __restrict__ lo, int nch, const int32_t* __restrict__ id,
+                             int32_t nruns, int32_t* __restrict__ chunk_run) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= nch; c += gridDim.x * blockDim.x)
+    chunk_run[c] = c < nch ? id[lo[c]] : nruns;
 }
 
 }  // namespace
@@ -476,6 +527,39 @@ int build_core_plan(const Part& m3, int64_t n, int64_t nnz, CorePlan& cp, cudaSt
   BKS_CUDA_TRY(cudaMemcpyAsync(cp.sl_first.p, slf.data(), 4 * slf.size(), cudaMemcpyHostToDevice, s));
   // the host vectors are read by the async copies: wait before they go
   BKS_CUDA_TRY(cudaStreamSynchronize(s));
+  // runs of equal (slice, i), cut at chunk starts and every kRunCap entries
+  {
+    DevBuf f1, id1, st1, f2, id2, tot;
+    BKS_TRY(f1.alloc(4 * nnz, s));
+    BKS_TRY(id1.alloc(4 * nnz, s));
+    BKS_TRY(st1.alloc(4 * nnz, s));
+    BKS_TRY(f2.alloc(4 * nnz, s));
+    BKS_TRY(id2.alloc(4 * nnz, s));
+    BKS_TRY(tot.alloc(4, s));
+    const int g = grid_for(nnz);
+    k_run_flags<<<g, 256, 0, s>>>(m3.c0.as<int32_t>(), nnz, f1.as<int32_t>()); ::bks::note_launch();
+    k_mark_starts<<<grid_for(cp.nch), 256, 0, s>>>(cp.lo.as<int32_t>(), cp.nch, f1.as<int32_t>()); ::bks::note_launch();
+    BKS_TRY(exclusive_scan_i32(f1.as<int32_t>(), id1.as<int32_t>(), nnz, tot.as<int32_t>(), s));
+    k_run_scatter<<<g, 256, 0, s>>>(f1.as<int32_t>(), id1.as<int32_t>(), nnz, st1.as<int32_t>()); ::bks::note_launch();
+    k_run_cap<<<g, 256, 0, s>>>(f1.as<int32_t>(), id1.as<int32_t>(), st1.as<int32_t>(), nnz,
+                                f2.as<int32_t>()); ::bks::note_launch();
+    BKS_TRY(exclusive_scan_i32(f2.as<int32_t>(), id2.as<int32_t>(), nnz, tot.as<int32_t>(), s));
+    int32_t nruns = 0;
+    BKS_CUDA_TRY(cudaMemcpyAsync(&nruns, tot.p, 4, cudaMemcpyDeviceToHost, s));
+    BKS_CUDA_TRY(cudaStreamSynchronize(s));
+    cp.nruns = nruns;
+    BKS_TRY(cp.run_start.alloc(4 * ((size_t)nruns + 1), s));
+    BKS_TRY(cp.chunk_run.alloc(4 * ((size_t)cp.nch + 1), s));
+    k_run_scatter<<<g, 256, 0, s>>>(f2.as<int32_t>(), id2.as<int32_t>(), nnz,
+                                    cp.run_start.as<int32_t>()); ::bks::note_launch();
+    const int32_t end = (int32_t)nnz;
+    BKS_CUDA_TRY(cudaMemcpyAsync(cp.run_start.as<int32_t>() + nruns, &end, 4,
+                                 cudaMemcpyHostToDevice, s));
+    k_chunk_runs<<<grid_for(cp.nch + 1), 256, 0, s>>>(cp.lo.as<int32_t>(), cp.nch, id2.as<int32_t>(),
+                                                      nruns, cp.chunk_run.as<int32_t>()); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+    BKS_CUDA_TRY(cudaStreamSynchronize(s));  // `end` is a host temporary
+  }
   return BKS_OK;
 }
 
