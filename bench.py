@@ -511,7 +511,7 @@ def _angle_bound(F, mode, tol=1e-9):
     return tol * float(ev.sum()) / max(float(ev[0]), 1e-300)
 
 
-def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
+def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream, n_sweep=None, distinct=0):
     """The batched form (independent solves on concurrent streams, work
     tiles autotuned per size class) on the job-size law of the batched
     workload at `scale`, mixed precision at the scale-free tolerance 1e-9,
@@ -596,7 +596,15 @@ def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
     def serve(rate, nreq, seed):
         arrivals, sjobs = synth.serving_stream(seed=seed, requests=nreq, scale=scale,
                                                mean_gap_s=1.0 / rate)
-        scoos = [synth.job_tensor(j) for j in sjobs]
+        if distinct > 0:
+            # the first `distinct` jobs of the stream, reused in turn (their
+            # tensors take minutes to draw at full scale)
+            base = sjobs[:distinct]
+            bcoos = [synth.job_tensor(j) for j in base]
+            sjobs = [base[q % len(base)] for q in range(nreq)]
+            scoos = [bcoos[q % len(base)] for q in range(nreq)]
+        else:
+            scoos = [synth.job_tensor(j) for j in sjobs]
         with bk.Server(150 << 30, max_slots=8, autotune=True) as srv:
             start = time.perf_counter()
             tickets = []
@@ -614,9 +622,11 @@ def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream):
                 "latency_p50_s": lat[len(lat) // 2],
                 "latency_p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
 
-    sweep = [serve(f * service_rate, n_serve, 50 + i) for i, f in enumerate((0.3, 0.6))]
+    n_sweep = n_serve if n_sweep is None else n_sweep
+    sweep = [serve(f * service_rate, n_sweep, 50 + i) for i, f in enumerate((0.3, 0.6))]
     nominal = serve(200.0, n_serve, 5)
     serving = {"slots": 8, "budget_bytes": 150 << 30, "scale": scale,
+               "distinct_tensors": distinct if distinct > 0 else "every request its own",
                "service_rate_batched_per_s": service_rate, "sweep": sweep,
                "nominal_200_per_s": nominal, "one_at_a_time_fp64": one_at_a_time}
     return batched, serving
@@ -634,6 +644,10 @@ def main():
                          "up to 5M stored entries per job); 0 skips them")
     ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-sweep-requests", type=int, default=None,
+                    help="requests per point of the offered-rate sweep (default: --serve-requests)")
+    ap.add_argument("--serve-distinct", type=int, default=0,
+                    help="serve the first D jobs of the stream in turn (0: every request its own)")
     ap.add_argument("--ncu-case", default=None,
                     help="profiling entry: build the workload, run a few launches of one "
                          "kernel family (mode1, mode3, core, solve) and exit without a JSON line")
@@ -795,7 +809,9 @@ def main():
     batched = serving = None
     if args.batch_scale > 0:
         batched, serving = batch_and_serve(bk, torch, args.batch_scale, args.batch_jobs,
-                                           args.serve_requests, stream)
+                                           args.serve_requests, stream,
+                                           n_sweep=args.serve_sweep_requests,
+                                           distinct=args.serve_distinct)
 
     # ---- CPU oracle baseline (bounded sample; rank 0, N = 1) ----
     cpu = None
