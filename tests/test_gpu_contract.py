@@ -93,11 +93,16 @@ def test_deterministic_bits():
     assert c.tobytes() == d.tobytes()
 
 
-@pytest.mark.parametrize("name", ["uniform_small", "zipf"])
+@pytest.mark.parametrize("name", ["uniform_small", "zipf", "long_rows"])
 @pytest.mark.parametrize("r1,r3", [(2, 2), (3, 2), (5, 5), (9, 4), (14, 9), (36, 21), (70, 40),
                                    (100, 30)])
 def test_core_fp64(name, r1, r3):
+    """The core against the oracle; "long_rows" (50 x 50 x 4, 30,000 draws)
+    has runs of several hundred entries with equal (k, i), which the run
+    plan cuts every 32 entries and at chunk starts."""
     import torch
+    if name == "long_rows" and r1 >= 50:
+        pytest.skip("r1 must stay below m = 50")
     if name == "zipf" and r1 > 36:
         pytest.skip("the oracle's m x r1 r3 intermediate is large; covered on uniform_small")
     bk, A, T = _setup(name)
