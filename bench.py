@@ -528,7 +528,7 @@ def batch_and_serve(bk, torch, scale, n_batch, n_serve, stream, n_sweep=None, di
     def prm(r, prec):
         return bk.BksParams(r1=r, r3=r, stages=2, block_p=4, tol=1e-9, tol_scale_free=1,
                             precision=prec, mixed_tol=1e-4, refine_sweeps=300, max_outer=300,
-                            max_inner=200, inner_schedule=bk.BKS_INNER_FAST)
+                            inner_schedule=bk.BKS_INNER_FAST)
 
     tens = [bk.bks_tensor_create_coo(c.m, c.n, c.i, c.j, c.k, c.v) for c in coos]
     # one seeded start per job, shared by the batched and the FP64 solves
