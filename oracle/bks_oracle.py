@@ -755,11 +755,13 @@ def inner_solve(C: np.ndarray, r1: int, r3: int, tol: float, max_inner: int = 10
     step is refused where -H is not positive definite or ||F|| would drop,
     and a HOOI sweep is taken instead (this library's safeguard away from a
     maximum).  ``method`` "hooi" continues with HOOI sweeps alone.
-    Monotone safeguard (this library's reading): the current point
-    (Uh = [I;0], Wh = [I;0], which is (U0, W0) in the bases) is kept as a
-    second candidate, and the continuation starts from whichever of the two
-    has the larger ||F||; so ||F|| never decreases over the outer
-    iterations (eq. (Fnon-decr)).  Returns (Uh, Wh, info)."""
+    Safeguard (this library's reading): the current point (Uh = [I;0],
+    Wh = [I;0], which is (U0, W0) in the bases) is kept as a second
+    candidate, and the continuation starts from whichever of the two has
+    the larger ||F||, so the start never lies below the current point
+    (eq. (Fnon-decr)).  A symmetric HOOI sweep (U in modes 1 and 2 at once)
+    is not an ascent step, so a solve stopped by ``max_inner`` before
+    converging can end below its start.  Returns (Uh, Wh, info)."""
     k1, _, k3 = C.shape
     Uh_a, Wh_a = hosvd_truncated(C, r1, r3)
     Uh_b = np.eye(k1, r1)
