@@ -18,9 +18,15 @@ approximation of large and sparse tensors"):
 * the G-gradient by Proposition 2 and in global coordinates (Section 2.5);
 * the inner best rank-(r1,r1,r3) solve of the dense core (Section 6.2:
   truncated HOSVD + HOOI sweeps);
-* the tensor Krylov-Schur outer loop (Algorithm 5) and HOOI (Section 6.1).
+* the tensor Krylov-Schur outer loop (Algorithm 5) and HOOI (Section 6.1);
+* the same method for a general l x m x n tensor with three bases
+  (``bks_general_oracle``: Section 5, Proposition 2 with three terms).
 
 Parity status per function is stated in ``bks_oracle``'s module docstring.
 """
 from .bks_oracle import *  # noqa: F401,F403
-from .bks_oracle import __all__  # noqa: F401
+from .bks_oracle import __all__ as _sym_all
+from .bks_general_oracle import *  # noqa: F401,F403
+from .bks_general_oracle import __all__ as _gen_all
+
+__all__ = list(_sym_all) + list(_gen_all)

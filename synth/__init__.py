@@ -19,6 +19,8 @@ configurations:
 * ``serving_stream``   Poisson arrivals of batch-like jobs
 * ``dense_planted``    exact multilinear rank (U0,U0,W0).F0 on a dense support
 * ``example1``         signal + rho * noise, Example 1 of Section 6.2.1
+* ``general_*``        general (nonsymmetric) l x m x n tensors for the
+                       three-basis form of the method (Section 5)
 """
 from __future__ import annotations
 
@@ -30,7 +32,8 @@ import numpy as np
 __all__ = [
     "COO", "rng", "orthonormal", "small_planted", "zipf_tensor", "zipf_table",
     "dense_planted", "example1", "batch_jobs", "serving_stream", "dense_to_coo",
-    "random_coo", "CONFIG_SEEDS",
+    "random_coo", "CONFIG_SEEDS", "GenCOO", "general_random_coo", "general_zipf_tensor",
+    "general_dense_planted", "general_dense_to_coo", "general_sampled_planted",
 ]
 
 CONFIG_SEEDS = {"small": 1, "medium": 2, "large": 3, "batch": 4, "serve": 5}
@@ -264,3 +267,98 @@ def serving_stream(seed: int = 5, requests: int = 2000, mean_gap_s: float = 0.00
     t = np.cumsum(gaps)
     jobs = batch_jobs(seed=seed, count=requests, scale=scale)
     return t, jobs
+
+
+# ---- general (nonsymmetric) l x m x n tensors --------------------------------
+@dataclasses.dataclass
+class GenCOO:
+    """A general sparse 3-tensor of shape l x m x n as (i, j, k, v) lists
+    (0-based int32 indices; duplicates allowed, summed by the consumer)."""
+    l: int
+    m: int
+    n: int
+    i: np.ndarray
+    j: np.ndarray
+    k: np.ndarray
+    v: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.i.shape[0])
+
+
+def general_random_coo(seed: int, l: int, m: int, n: int, draws: int,
+                       vdtype=np.float64) -> GenCOO:
+    """Uniform random (i, j, k) draws with N(0,1) values, duplicates
+    allowed."""
+    g = rng(seed)
+    i = g.integers(0, l, size=draws)
+    j = g.integers(0, m, size=draws)
+    k = g.integers(0, n, size=draws)
+    v = g.standard_normal(draws).astype(vdtype)
+    return GenCOO(l, m, n, i.astype(np.int32), j.astype(np.int32), k.astype(np.int32), v)
+
+
+def general_zipf_tensor(seed: int, l: int, m: int, n: int, draws: int, s: float,
+                        values: str = "lognormal", vdtype=np.float64) -> GenCOO:
+    """Power-law general workload (a directed, bipartite or rectangular
+    relation per slice): i from a finite Zipf(s) law on l ranks and j from
+    one on m ranks, each through its own seeded permutation; k uniform on
+    [0, n); values lognormal(0,1) or |N(0,1)|.  No mirroring."""
+    g = rng(seed)
+    pi = g.permutation(l)
+    pj = g.permutation(m)
+    i = pi[_zipf_draw(g, zipf_table(l, s), draws)]
+    j = pj[_zipf_draw(g, zipf_table(m, s), draws)]
+    k = g.integers(0, n, size=draws)
+    if values == "lognormal":
+        v = g.lognormal(0.0, 1.0, size=draws)
+    elif values == "absnormal":
+        v = np.abs(g.standard_normal(draws))
+    else:
+        raise ValueError(values)
+    return GenCOO(l, m, n, i.astype(np.int32), j.astype(np.int32), k.astype(np.int32),
+                  v.astype(vdtype))
+
+
+def general_dense_to_coo(T: np.ndarray) -> GenCOO:
+    """All entries of a dense l x m x n array (zeros included)."""
+    l, m, n = T.shape
+    i, j, k = np.meshgrid(np.arange(l), np.arange(m), np.arange(n), indexing="ij")
+    return GenCOO(l, m, n, i.ravel().astype(np.int32), j.ravel().astype(np.int32),
+                  k.ravel().astype(np.int32), T.ravel().astype(np.float64))
+
+
+def general_dense_planted(seed: int, l: int = 30, m: int = 24, n: int = 10,
+                          r=(2, 3, 2)):
+    """A dense l x m x n tensor of exact multilinear rank r:
+    (U0, V0, W0).F0 with N(0,1) core entries.  Returns (T, U0, V0, W0, F0)."""
+    g = rng(seed)
+    U0 = orthonormal(g, l, r[0])
+    V0 = orthonormal(g, m, r[1])
+    W0 = orthonormal(g, n, r[2])
+    F0 = g.standard_normal(tuple(r))
+    T = np.einsum("ia,jb,kc,abc->ijk", U0, V0, W0, F0, optimize=True)
+    return T, U0, V0, W0, F0
+
+
+def general_sampled_planted(seed: int, l: int, m: int, n: int, draws: int, r=(2, 2, 2),
+                            snr: float = 10.0) -> GenCOO:
+    """``draws`` uniform (i, j, k) positions with |N(0,1)| noise plus
+    alpha * ((U0,V0,W0).F0)(i,j,k) at the drawn positions, alpha making the
+    planted part ``snr`` times the noise part in norm (a sparse general
+    analogue of ``small_planted``)."""
+    g = rng(seed)
+    i = g.integers(0, l, size=draws)
+    j = g.integers(0, m, size=draws)
+    k = g.integers(0, n, size=draws)
+    noise = np.abs(g.standard_normal(draws))
+    U0 = orthonormal(g, l, r[0])
+    V0 = orthonormal(g, m, r[1])
+    W0 = orthonormal(g, n, r[2])
+    F0 = g.standard_normal(tuple(r))
+    sig = np.einsum("za,zb,zc,abc->z", U0[i], V0[j], W0[k], F0, optimize=True)
+    ns, ss = float(np.linalg.norm(noise)), float(np.linalg.norm(sig))
+    alpha = snr * ns / ss if ss > 0 else 0.0
+    return GenCOO(l, m, n, i.astype(np.int32), j.astype(np.int32), k.astype(np.int32),
+                  noise + alpha * sig)
