@@ -228,6 +228,7 @@ typedef struct {
   double* history;     /* host, optional: 2 doubles (grad_rel, normF) per outer iteration */
   int history_cap;     /* capacity of history in iterations */
   int history_len;     /* filled entries */
+  int k2;              /* bks_gen_solve: mode-2 basis size of the last expansion */
 } bks_info;
 
 /* Default parameters: r1 = r3 = 2, s = 2, p = 4, tol 1e-10, max_outer 500,
@@ -409,6 +410,93 @@ int bks_tensor_scale_slices(const bks_tensor* t, const double* scales, void* str
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all threads, all devices); a diagnostic counter for benchmarks. */
 uint64_t bks_launch_count(void);
+
+/* ---- general (nonsymmetric) l x m x n tensors (Section 5) -----------------
+ * The method of Section 5 as the paper states it, before the (1,2)-symmetric
+ * specialisation: three bases X (l x k1), Y (m x k2), Z (n x k3) grown by the
+ * block-Krylov step of Algorithm 3 in each mode, the G-gradient from the
+ * three stage-1 blocks (Proposition 2), the core C = A.(X,Y,Z) (eq. (tkd)),
+ * its best rank-(r1,r2,r3) approximation (Algorithm 5 step (i)) and the
+ * restart (eq. (tks1)).  FP64 only.  A general handle is refused by the
+ * symmetric calls above (BKS_EUNSUPPORTED) and vice versa; destroy it with
+ * bks_tensor_destroy; bks_tensor_info reports m, n, nnz and ||A||^2 and
+ * bks_tensor_export_coo the sorted entries. */
+
+/* bks_gen_tensor_create_coo: store A (l x m x n) from nnz COO entries.
+ *   i < l, j < m, k < n (int32, 0-based); v BKS_F32 or BKS_F64 (vdtype).
+ *   Entries are sorted by (i, j, k) (stable) and entries with equal keys
+ *   summed left to right in the value dtype; nothing is mirrored.  flags:
+ *   BKS_INPUT_ON_DEVICE (i, j, k, v are device pointers) or 0 (host);
+ *   BKS_MIRROR / BKS_VALIDATE_SYMMETRIC give BKS_EINVAL.  Errors:
+ *   BKS_EINVAL (an index out of range, a dimension < 1, nnz < 0),
+ *   BKS_EUNSUPPORTED (a dimension or nnz above int32, l m n above a 64-bit
+ *   sort key), BKS_ENOMEM, BKS_ECUDA.  The library owns the handle. */
+int bks_gen_tensor_create_coo(int64_t l, int64_t m, int64_t n, int64_t nnz,
+                              const int32_t* i, const int32_t* j, const int32_t* k,
+                              const void* v, int vdtype, int flags, void* stream,
+                              bks_tensor** out);
+
+/* bks_gen_tensor_dims: l, m, n of any handle (l = m for a symmetric one) and
+ * general = 1 for a general handle, 0 for a (1,2)-symmetric one.  Host
+ * outputs, each nullable. */
+int bks_gen_tensor_dims(const bks_tensor* t, int64_t* l, int64_t* m, int64_t* n, int* general);
+
+/* bks_gen_contract: the block contraction of Algorithm 3 step (i) in mode
+ * `mode` (Section 2.2), column-major, column a + p*b, out overwritten:
+ *   mode 1: out (l x p q)[i, a + p b] = sum v B1[j, a] B2[k, b]; B1 m x p, B2 n x q
+ *   mode 2: out (m x p q)[j, a + p b] = sum v B1[i, a] B2[k, b]; B1 l x p, B2 n x q
+ *   mode 3: out (n x p q)[k, a + p b] = sum v B1[i, a] B2[j, b]; B1 l x p, B2 m x q
+ *   Device pointers of `dtype` (BKS_F32 or BKS_F64), leading dimensions at
+ *   least the rows; 1 <= p, q <= 8.  Deterministic (no atomics).  Errors:
+ *   BKS_EINVAL, BKS_EUNSUPPORTED (a width above 8, a symmetric handle). */
+int bks_gen_contract(const bks_tensor* t, int mode, const void* B1, int64_t ld1, int p,
+                     const void* B2, int64_t ld2, int q, void* out, int64_t ldo,
+                     int dtype, void* stream);
+
+/* bks_gen_core: C = A.(X,Y,Z) (eq. (tkd)), C[a + k1 (b + k2 c)] (k1 k2 k3
+ *   doubles, device); X l x k1 (ldx), Y m x k2 (ldy), Z n x k3 (ldz), FP64
+ *   device; 1 <= k1, k2, k3 <= 128. */
+int bks_gen_core(const bks_tensor* t, const double* X, int64_t ldx, int k1,
+                 const double* Y, int64_t ldy, int k2, const double* Z, int64_t ldz, int k3,
+                 double* C, void* stream);
+
+typedef struct {
+  int r1, r2, r3;      /* target multilinear rank, each 1..8, pairwise products <= 32 */
+  int stages;          /* s: BK stages per expansion */
+  int block_p;         /* p: leading columns of each ON-block used (block 0 whole) */
+  double tol;          /* stop when ||grad|| / ||F|| <= tol (tol_scale_free: / ||F||^2) */
+  int max_outer;       /* outer-iteration cap (BKS_ENOTCONV past it) */
+  int max_inner;       /* inner HOOI sweep cap per outer iteration */
+  int variant;         /* BKS_VARIANT_BK, _MIN or _MAX, in the general form: stage 1
+                          makes U1 from (V0,W0), V1 from (U0,W0), W1 from (U0,V0); BK stage
+                          t >= 2 (q = t-1) takes the pairs (0,q), (q,0), ..., (q-1,q), (q,q-1)
+                          of the other two modes' blocks in every mode; MIN the pair
+                          (t-1, t-1); MAX every unused pair of whole blocks */
+  int tol_scale_free;  /* 1: the test is ||grad|| / ||F||^2 <= tol */
+  uint64_t seed;       /* random start when a start matrix is NULL */
+  double drop_tol;     /* rank-drop threshold of the block QR (relative) */
+  double inner_tol;    /* inner tolerance; <= 0: the outer one */
+} bks_gen_params;
+
+/* Defaults: r = (2,2,2), s = 2, p = 4, tol 1e-10, max_outer 500,
+ * max_inner 1000, BK, seed 1, drop_tol 1e-14, inner_tol 0. */
+void bks_gen_params_default(bks_gen_params* p);
+
+/* bks_gen_solve: tensor Krylov-Schur for a general tensor (Algorithm 5).
+ *   U0 (l x r1), V0 (m x r2), W0 (n x r3): orthonormal device FP64 starts
+ *   (ld = rows), each nullable (seeded random start).  Inner solve: the
+ *   better of the truncated HOSVD of C after 5 HOOI sweeps and the current
+ *   point, then HOOI sweeps (each the leading singular vectors of one
+ *   mode's contraction given the other two, so ||F|| never drops) to the
+ *   outer tolerance.  Outputs U (l x r1), V (m x r2), W (n x r3), F
+ *   (r1 r2 r3, F[a + r1 (b + r2 c)]) on the device; info (host, nullable)
+ *   with k1, k2, k3 of the last expansion.  Returns BKS_OK, BKS_ENOTCONV
+ *   (the last evaluated point written), BKS_ENUMERIC, BKS_EINVAL,
+ *   BKS_EUNSUPPORTED, BKS_ENOMEM, BKS_ECUDA.  Synchronises `stream` once
+ *   per outer iteration. */
+int bks_gen_solve(const bks_tensor* t, const bks_gen_params* prm, const double* U0,
+                  const double* V0, const double* W0, double* U, double* V, double* W,
+                  double* F, bks_info* info, void* stream);
 
 #ifdef __cplusplus
 }

@@ -163,7 +163,7 @@ def gcore(A: GenTensor, X: np.ndarray, Y: np.ndarray, Z: np.ndarray) -> np.ndarr
     # per entry the outer product v X[i,:] x Y[j,:] x Z[k,:], summed; in
     # slices of entries to bound memory
     C = np.zeros((X.shape[1], Y.shape[1], Z.shape[1]))
-    step = 4096
+    step = 2048
     for s in range(0, A.nnz, step):
         e = slice(s, s + step)
         C += np.einsum("e,ea,eb,ec->abc", v[e], X[A.i[e]], Y[A.j[e]], Z[A.k[e]], optimize=True)

@@ -28,6 +28,8 @@ __all__ = [
     "bks_tensor_set_tiles", "bks_batch_solve", "Server", "BKS_ECANCELED", "BKS_EPENDING",
     "BKS_EBUDGET", "BKS_NORM_FRO", "BKS_NORM_LMAX", "bks_s_values", "bks_slice_norms",
     "bks_tensor_scale_slices", "BKS_INNER_PAPER", "BKS_INNER_FAST", "bks_contract_mode1_noalloc",
+    "bks_gen_tensor_create_coo", "bks_gen_tensor_dims", "bks_gen_contract", "bks_gen_core",
+    "BksGenParams", "bks_gen_solve",
 ]
 
 BKS_OK = 0
@@ -74,7 +76,16 @@ class _Info(ctypes.Structure):
                 ("fp32_iters", ctypes.c_int), ("seconds", ctypes.c_double),
                 ("phase_ms", ctypes.c_double * 5),
                 ("history", ctypes.POINTER(ctypes.c_double)), ("history_cap", ctypes.c_int),
-                ("history_len", ctypes.c_int)]
+                ("history_len", ctypes.c_int), ("k2", ctypes.c_int)]
+
+
+class _GenParams(ctypes.Structure):
+    _fields_ = [("r1", ctypes.c_int), ("r2", ctypes.c_int), ("r3", ctypes.c_int),
+                ("stages", ctypes.c_int), ("block_p", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
+                ("variant", ctypes.c_int), ("tol_scale_free", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("drop_tol", ctypes.c_double),
+                ("inner_tol", ctypes.c_double)]
 
 
 class _HooiParams(ctypes.Structure):
@@ -165,6 +176,21 @@ def lib():
     L.bks_slice_norms.restype = c_int
     L.bks_tensor_scale_slices.argtypes = [vp, vp, vp, ctypes.POINTER(vp)]
     L.bks_tensor_scale_slices.restype = c_int
+    L.bks_gen_tensor_create_coo.argtypes = [i64, i64, i64, i64, vp, vp, vp, vp, c_int, c_int, vp,
+                                            ctypes.POINTER(vp)]
+    L.bks_gen_tensor_create_coo.restype = c_int
+    L.bks_gen_tensor_dims.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i64), ctypes.POINTER(c_int)]
+    L.bks_gen_tensor_dims.restype = c_int
+    L.bks_gen_contract.argtypes = [vp, c_int, vp, i64, c_int, vp, i64, c_int, vp, i64, c_int, vp]
+    L.bks_gen_contract.restype = c_int
+    L.bks_gen_core.argtypes = [vp, vp, i64, c_int, vp, i64, c_int, vp, i64, c_int, vp, vp]
+    L.bks_gen_core.restype = c_int
+    L.bks_gen_params_default.argtypes = [ctypes.POINTER(_GenParams)]
+    L.bks_gen_params_default.restype = None
+    L.bks_gen_solve.argtypes = [vp, ctypes.POINTER(_GenParams), vp, vp, vp, vp, vp, vp, vp,
+                                ctypes.POINTER(_Info), vp]
+    L.bks_gen_solve.restype = c_int
     L.bks_launch_count.argtypes = []
     L.bks_launch_count.restype = ctypes.c_uint64
     L.bks_last_error_string.argtypes = []
@@ -216,7 +242,8 @@ def _empty_cm(rows, cols, dtype, device):
 
 
 class Tensor:
-    """Owning handle of a stored (1,2)-symmetric tensor."""
+    """Owning handle of a stored tensor: (1,2)-symmetric m x m x n
+    (general False, l == m) or general l x m x n (general True)."""
 
     def __init__(self, handle: ctypes.c_void_p, vdtype: int):
         self._h = handle
@@ -225,6 +252,9 @@ class Tensor:
         _check(lib().bks_tensor_info(self._h, ctypes.byref(m), ctypes.byref(n), ctypes.byref(nnz),
                                      ctypes.byref(f2)))
         self.m, self.n, self.nnz, self.fro2 = m.value, n.value, nnz.value, f2.value
+        l, gen = ctypes.c_int64(), ctypes.c_int()
+        _check(lib().bks_gen_tensor_dims(self._h, ctypes.byref(l), None, None, ctypes.byref(gen)))
+        self.l, self.general = l.value, bool(gen.value)
 
     @property
     def handle(self):
@@ -638,3 +668,120 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---- general (nonsymmetric) l x m x n tensors (Section 5) --------------------
+def _coo_ptrs(i, j, k, v):
+    import torch
+    if isinstance(i, torch.Tensor):
+        ii, jj, kk = (x.to(torch.int32).contiguous() for x in (i, j, k))
+        vv = v.contiguous()
+        return BKS_INPUT_ON_DEVICE, _dtype_code(vv), [x.data_ptr() for x in (ii, jj, kk, vv)], \
+            [ii, jj, kk, vv], ii.numel()
+    ii, jj, kk = (np.ascontiguousarray(x, dtype=np.int32) for x in (i, j, k))
+    vv = np.ascontiguousarray(v)
+    if vv.dtype == np.float64:
+        vdt = BKS_F64
+    elif vv.dtype == np.float32:
+        vdt = BKS_F32
+    else:
+        raise TypeError(f"unsupported value dtype {vv.dtype}")
+    return 0, vdt, [x.ctypes.data if x.size else 0 for x in (ii, jj, kk, vv)], \
+        [ii, jj, kk, vv], ii.size
+
+
+def bks_gen_tensor_create_coo(l: int, m: int, n: int, i, j, k, v, stream=None) -> Tensor:
+    """Store a general l x m x n tensor from COO entries (numpy host arrays
+    or torch CUDA tensors); duplicates are summed, nothing is mirrored."""
+    flags, vdt, ptrs, keep, nnz = _coo_ptrs(i, j, k, v)
+    h = ctypes.c_void_p()
+    _check(lib().bks_gen_tensor_create_coo(l, m, n, nnz, *[ctypes.c_void_p(p) for p in ptrs], vdt,
+                                           flags, _stream(stream), ctypes.byref(h)))
+    del keep
+    return Tensor(h, vdt)
+
+
+def bks_gen_tensor_dims(t: Tensor):
+    return {"l": t.l, "m": t.m, "n": t.n, "general": t.general}
+
+
+def bks_gen_contract(t: Tensor, mode: int, B1, B2, out=None, stream=None):
+    """The mode-`mode` block contraction of a general tensor: mode 1 ->
+    l x p q from (B1 m x p, B2 n x q), mode 2 -> m x p q from (B1 l x p,
+    B2 n x q), mode 3 -> n x p q from (B1 l x p, B2 m x q); column a + p b."""
+    B1, B2 = col_major(B1), col_major(B2)
+    p, q = B1.shape[1], B2.shape[1]
+    rows = {1: t.l, 2: t.m, 3: t.n}.get(mode, 1)  # the library rejects other modes
+    if out is None:
+        out = _empty_cm(rows, p * q, B1.dtype, B1.device)
+    _check(lib().bks_gen_contract(t.handle, mode, ctypes.c_void_p(B1.data_ptr()), _ld(B1), p,
+                                  ctypes.c_void_p(B2.data_ptr()), _ld(B2), q,
+                                  ctypes.c_void_p(out.data_ptr()), _ld(out), _dtype_code(B1),
+                                  _stream(stream)))
+    return out
+
+
+def bks_gen_core(t: Tensor, X, Y, Z, stream=None):
+    """C = A.(X,Y,Z) of a general tensor as a k1 x k2 x k3 torch FP64 tensor."""
+    import torch
+    X, Y, Z = (col_major(x.to(torch.float64)) for x in (X, Y, Z))
+    k1, k2, k3 = X.shape[1], Y.shape[1], Z.shape[1]
+    C = torch.empty(k1 * k2 * k3, dtype=torch.float64, device=X.device)
+    _check(lib().bks_gen_core(t.handle, ctypes.c_void_p(X.data_ptr()), _ld(X), k1,
+                              ctypes.c_void_p(Y.data_ptr()), _ld(Y), k2,
+                              ctypes.c_void_p(Z.data_ptr()), _ld(Z), k3,
+                              ctypes.c_void_p(C.data_ptr()), _stream(stream)))
+    return C.reshape(k3, k2, k1).permute(2, 1, 0)
+
+
+@dataclasses.dataclass
+class BksGenParams:
+    r1: int = 2
+    r2: int = 2
+    r3: int = 2
+    stages: int = 2
+    block_p: int = 4
+    tol: float = 1e-10
+    max_outer: int = 500
+    max_inner: int = 1000
+    variant: int = BKS_VARIANT_BK
+    tol_scale_free: int = 0
+    seed: int = 1
+    drop_tol: float = 1e-14
+    inner_tol: float = 0.0
+
+    def to_c(self) -> _GenParams:
+        p = _GenParams()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+def bks_gen_solve(t: Tensor, params: Optional[BksGenParams] = None, U0=None, V0=None, W0=None,
+                  stream=None, history_cap: int = 1000, raise_notconv: bool = False):
+    """Tensor Krylov-Schur for a general tensor (Algorithm 5, Section 5).
+    Returns (U, V, W, F, info): U l x r1, V m x r2, W n x r3 FP64 CUDA
+    tensors and F r1 x r2 x r3."""
+    import torch
+    prm = params or BksGenParams()
+    r = (prm.r1, prm.r2, prm.r3)
+    dims = (t.l, t.m, t.n)
+    outs = [_empty_cm(dims[q], r[q], torch.float64, "cuda") for q in range(3)]
+    F = torch.empty(r[0] * r[1] * r[2], dtype=torch.float64, device="cuda")
+    hist = (ctypes.c_double * (2 * max(history_cap, 1)))()
+    info = _Info()
+    info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    info.history_cap = history_cap
+    starts = [x.to(device="cuda", dtype=torch.float64).t().contiguous().t() if x is not None
+              else None for x in (U0, V0, W0)]
+    cp = prm.to_c()
+    rc = lib().bks_gen_solve(t.handle, ctypes.byref(cp),
+                             *[ctypes.c_void_p(x.data_ptr() if x is not None else 0) for x in starts],
+                             *[ctypes.c_void_p(x.data_ptr()) for x in outs],
+                             ctypes.c_void_p(F.data_ptr()), ctypes.byref(info), _stream(stream))
+    _check(rc, allow=() if raise_notconv else (BKS_ENOTCONV,))
+    out = {"iters": info.iters, "converged": bool(info.converged), "grad_rel": info.grad_rel,
+           "normF": info.normF, "k1": info.k1, "k2": info.k2, "k3": info.k3,
+           "inner_sweeps": info.inner_sweeps, "seconds": info.seconds, "status": rc,
+           "history": [(hist[2 * q], hist[2 * q + 1]) for q in range(info.history_len)]}
+    return outs[0], outs[1], outs[2], F.reshape(r[2], r[1], r[0]).permute(2, 1, 0), out

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbks_gb300.so")
 SOURCES = ["scan.cu", "ingest.cu", "contract.cu", "contract_tile_f32.cu", "contract_tile_f32d.cu",
-           "contract_tile_f64.cu", "dense.cu", "diag.cu", "inner.cu", "newton.cu", "solver.cu", "tune.cu",
+           "contract_tile_f64.cu", "dense.cu", "diag.cu", "general.cu", "inner.cu", "newton.cu", "solver.cu", "tune.cu",
            "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

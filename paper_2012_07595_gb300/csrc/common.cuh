@@ -176,14 +176,34 @@ int build_core_plan(const Part& m3, int64_t n, int64_t nnz, CorePlan& cp, cudaSt
 
 }  // namespace bks
 
+// A stored tensor.  (1,2)-symmetric (general == 0): l = m, two sorted
+// copies.  General l x m x n (general == 1, Section 5): a third copy for
+// the mode-2 contraction.
 struct bks_tensor {
-  int64_t m = 0, n = 0, nnz = 0;
+  int64_t l = 0, m = 0, n = 0, nnz = 0;
   int vdtype = BKS_F64;
+  int general = 0;
   double fro2 = 0.0;
-  bks::Part m1;   // sorted by (i, j, k): rows i, columns (j, k)
-  bks::Part m3;   // sorted by (k, i, j): rows k, columns (i, j)
+  bks::Part m1;   // sorted by (i, j, k): rows i, c0 = k, c1 = j
+  bks::Part m2;   // general only, sorted by (j, i, k): rows j, c0 = k, c1 = i
+  bks::Part m3;   // sorted by (k, i, j): rows k, c0 = i, c1 = j
   bks::CorePlan cp;
 };
+
+namespace bks {
+// Entry points of the (1,2)-symmetric method refuse a general tensor and
+// the general ones a symmetric tensor.
+inline int require_symmetric(const bks_tensor* t) {
+  if (t && t->general)
+    return fail(BKS_EUNSUPPORTED, "a general (l x m x n) tensor: use the bks_gen_* calls");
+  return BKS_OK;
+}
+inline int require_general(const bks_tensor* t) {
+  if (t && !t->general)
+    return fail(BKS_EUNSUPPORTED, "a (1,2)-symmetric tensor: use the symmetric calls");
+  return BKS_OK;
+}
+}  // namespace bks
 
 namespace bks {
 
@@ -279,9 +299,21 @@ int contract_mode3_x(const bks_tensor* t, const double* X, int64_t ldx, int p, c
                      int64_t ldx2, int q, double* out, int64_t ldo, bool fp32, cudaStream_t s);
 int contract_core_x(const bks_tensor* t, const double* U, int64_t ldu, int r1, const double* W,
                     int64_t ldw, int r3, double* F, bool fp32, cudaStream_t s);
+// general tensors (Section 5): mode md in {1, 2, 3} with the other two
+// modes' operands; the core C = A.(X,Y,Z) (k1, k2 <= 128), FP64
+int gen_contract_x(const bks_tensor* t, int md, const double* B1, int64_t ld1, int p,
+                   const double* B2, int64_t ld2, int q, double* out, int64_t ldo, cudaStream_t s);
+int gen_core_x(const bks_tensor* t, const double* X, int64_t ldx, int k1, const double* Y,
+               int64_t ldy, int k2, const double* Z, int64_t ldz, int k3, double* C,
+               cudaStream_t s);
 // inner solve (inner.cu)
 int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int max_inner,
                 int init_sweeps, int newton_after, double* Uh, double* Wh, double* negU, double* negW, double* info,
                 cudaStream_t s);
+// general core (k1 x k2 x k3): HOSVD start vs the current point, then HOOI
+// sweeps; negated factors and info[4] = {grad, ||F||, sweeps, hosvd_won}
+int gen_inner_solve(const double* C, int k1, int k2, int k3, int r1, int r2, int r3, double tol,
+                    int max_inner, int init_sweeps, double* negU, double* negV, double* negW,
+                    double* info, cudaStream_t s);
 
 }  // namespace bks

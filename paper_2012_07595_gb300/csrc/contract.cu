@@ -458,6 +458,228 @@ int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* 
   return BKS_OK;
 }
 
+// ---- general (nonsymmetric) tensors, Section 5 ----------------------------
+// Mode md in {1, 2, 3}: out_row[a + p b] = sum v B1[ia, a] B2[ib, b] over the
+// rows of the md-th sorted copy, with (copy, ia, ib, B1 rows, B2 rows) =
+// (m1, j, k, m, n), (m2, i, k, l, n), (m3, i, j, l, m).
+template <typename T, typename IT, typename OT>
+int gen_contract_typed(const bks_tensor* t, int md, const IT* B1, int64_t ld1, int p,
+                       const IT* B2, int64_t ld2, int q, OT* out, int64_t ldo, cudaStream_t s) {
+  const Part& P = md == 1 ? t->m1 : (md == 2 ? t->m2 : t->m3);
+  const int32_t* ia = md == 3 ? P.c0.as<int32_t>() : P.c1.as<int32_t>();
+  const int32_t* ib = md == 3 ? P.c1.as<int32_t>() : P.c0.as<int32_t>();
+  const int64_t rows1 = md == 1 ? t->m : t->l;
+  const int64_t rows2 = md == 3 ? t->m : t->n;
+  const int PB = bucket_t<T>(p);
+  DevBuf Ap;
+  BKS_TRY((pack<T, IT>(B1, ld1, rows1, p, row_stride<T>(PB), Ap, s)));
+  const int qchunk = qchunk_of(PB);
+  for (int q0 = 0; q0 < q; q0 += qchunk) {
+    const int qq = std::min(qchunk, q - q0);
+    const int QB = bucket_t<T>(qq);
+    DevBuf Bp;
+    BKS_TRY((pack<T, IT>(B2 + ld2 * q0, ld2, rows2, qq, row_stride<T>(QB), Bp, s)));
+    BKS_TRY((dispatch<T, OT>(P, t->vdtype, ia, ib, Ap.as<T>(), PB, Bp.as<T>(), QB, rows2, false,
+                             p, qq, out + ldo * (p * q0), ldo, s)));
+  }
+  return BKS_OK;
+}
+
+// General core C = A.(X,Y,Z) (eq. (tkd)), k1, k2 <= 128: per chunk of one
+// slice k of the mode-3 copy, M = sum over runs of equal (k, i) of
+// X[i,:]^T (sum over the run of v Y[j,:]), all 4x4 tiles of the k1 x k2
+// rectangle in registers (TPT tiles per thread); then C[a,b,c] =
+// sum_k Z[k,c] sum_{chunks of k} M[a,b].  Groups of threads take a batch's
+// runs round-robin when the rectangle has fewer tiles than the block has
+// threads; their sums are added in group order.
+template <typename T, int TPT>
+__global__ void __launch_bounds__(kCoreThreads)
+k_gcore_chunks(const int32_t* __restrict__ chunk_run, const int32_t* __restrict__ run_start,
+               const int32_t* __restrict__ ii, const int32_t* __restrict__ jj,
+               const T* __restrict__ vals, const T* __restrict__ Xp, int K1, int KP1,
+               const T* __restrict__ Yp, int K2, int KP2, int batch, int ngroups,
+               T* __restrict__ Mpart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);          // [batch][KP1]
+  T* Bs = As + (size_t)batch * KP1;                 // [batch][KP2]
+  const int ch = blockIdx.x;
+  const int lo = chunk_run[ch], hi = chunk_run[ch + 1];
+  const int nt1 = KP1 / 4, nt2 = KP2 / 4, ntiles = nt1 * nt2;
+  const int slots = kCoreThreads / ngroups;
+  const int g = threadIdx.x / slots, ts = threadIdx.x % slots;
+  const bool active = g < ngroups;
+  int ta[TPT], tb[TPT];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int id = ts + u * slots;
+    ta[u] = -1; tb[u] = -1;
+    if (active && id < ntiles) { ta[u] = id % nt1; tb[u] = id / nt1; }
+  }
+  T acc[TPT][4][4];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[u][x][y] = T(0);
+  for (int base = lo; base < hi; base += batch) {
+    const int cnt = min(batch, hi - base);
+    __syncthreads();
+    // run r of the batch: As[r] = X[i_r, :], Bs[r] = sum over the run's
+    // entries (in order) of v_e Y[j_e, :]
+    for (int t = threadIdx.x; t < cnt * nt1; t += kCoreThreads) {
+      const int e = t / nt1, q = t % nt1;
+      T xa[4];
+      load4(Xp + (int64_t)ii[run_start[base + e]] * KP1 + 4 * q, xa);
+      store4_shared(As + e * KP1 + 4 * q, xa);
+    }
+    for (int t = threadIdx.x; t < cnt * nt2; t += kCoreThreads) {
+      const int e = t / nt2, q = t % nt2;
+      const int e0 = run_start[base + e], e1 = run_start[base + e + 1];
+      T xb[4] = {T(0), T(0), T(0), T(0)};
+      for (int idx = e0; idx < e1; ++idx) {
+        T y0[4];
+        const T v0 = vals[idx];
+        load4(Yp + (int64_t)jj[idx] * KP2 + 4 * q, y0);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) xb[x] = fma(v0, y0[x], xb[x]);
+      }
+      store4_shared(Bs + e * KP2 + 4 * q, xb);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      if (ta[u] < 0) continue;
+      for (int e = g; e < cnt; e += ngroups) {
+        T xa[4], xb[4];
+        load4_shared(As + e * KP1 + ta[u] * 4, xa);
+        load4_shared(Bs + e * KP2 + tb[u] * 4, xb);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[u][x][y] = fma(xa[x], xb[y], acc[u][x][y]);
+      }
+    }
+  }
+  T* dst = Mpart + (int64_t)ch * K1 * K2;
+  if (ngroups == 1) {
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      if (ta[u] < 0) continue;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int a = ta[u] * 4 + x, b = tb[u] * 4 + y;
+          if (a < K1 && b < K2) dst[a + (int64_t)K1 * b] = acc[u][x][y];
+        }
+    }
+    return;
+  }
+  // ngroups > 1 (then TPT == 1): group sums in group order through shared
+  // memory ([ngroups][ntiles][16], reusing the staging area)
+  __syncthreads();
+  T* red = As;
+  if (ta[0] >= 0) {
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) red[((size_t)g * ntiles + ts) * 16 + 4 * x + y] = acc[0][x][y];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < ntiles * 16; o += kCoreThreads) {
+    const int id = o / 16, xy = o % 16;
+    T sum = red[(size_t)id * 16 + xy];
+    for (int q = 1; q < ngroups; ++q) sum += red[((size_t)q * ntiles + id) * 16 + xy];
+    const int a = (id % nt1) * 4 + xy / 4, b = (id / nt1) * 4 + xy % 4;
+    if (a < K1 && b < K2) dst[a + (int64_t)K1 * b] = sum;
+  }
+}
+
+// S[sl, x] = sum over the chunks of non-empty slice sl (in chunk order) of
+// M_chunk[x], x = a + K1 b.
+template <typename T>
+__global__ void k_gcore_slice_sum(const T* __restrict__ Mpart, const int32_t* __restrict__ sl_first,
+                                  int nsl, int64_t kk, T* __restrict__ S) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < (int64_t)nsl * kk;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = o % kk;
+    const int sl = (int)(o / kk);
+    T sum = T(0);
+    for (int ch = sl_first[sl]; ch < sl_first[sl + 1]; ++ch) sum += Mpart[(int64_t)ch * kk + x];
+    S[o] = sum;
+  }
+}
+
+// C[x + kk c] = sum over non-empty slices (in order) of Z[k,c] S[sl, x].
+template <typename T>
+__global__ void k_gcore_combine(const T* __restrict__ S, const int32_t* __restrict__ sl_k, int nsl,
+                                int64_t kk, const double* __restrict__ Z, int64_t ldz, int k3,
+                                double* __restrict__ C) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < kk * k3;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = o % kk;
+    const int c = (int)(o / kk);
+    T acc = T(0);
+    for (int sl = 0; sl < nsl; ++sl) acc = fma((T)Z[sl_k[sl] + ldz * c], S[(int64_t)sl * kk + x], acc);
+    C[o] = (double)acc;
+  }
+}
+
+int gen_core_fp64(const bks_tensor* t, const double* X, int64_t ldx, int k1, const double* Y,
+                  int64_t ldy, int k2, const double* Z, int64_t ldz, int k3, double* C,
+                  cudaStream_t s) {
+  using T = double;
+  const CorePlan& cp = t->cp;
+  const int64_t kk = (int64_t)k1 * k2;
+  if (cp.nch == 0 || kk * k3 == 0) {
+    if (kk * k3 > 0) BKS_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)kk * k3, s));
+    return BKS_OK;
+  }
+  const int KP1 = (k1 + 3) / 4 * 4, KP2 = (k2 + 3) / 4 * 4;
+  const int nt1 = KP1 / 4, nt2 = KP2 / 4, ntiles = nt1 * nt2;
+  const int tpt = ntiles <= kCoreThreads ? 1 : (ntiles <= 2 * kCoreThreads ? 2 : 4);
+  const int ngroups = ntiles <= kCoreThreads ? std::min(32, kCoreThreads / ntiles) : 1;
+  int batch = (int)std::min<size_t>(64, (64 * 1024) / (sizeof(T) * (size_t)(KP1 + KP2)));
+  batch = std::max(batch, 8);
+  // the group reduction reuses the staging area when there are groups
+  const size_t smem = std::max(sizeof(T) * (size_t)batch * (KP1 + KP2),
+                               ngroups > 1 ? sizeof(T) * (size_t)ngroups * ntiles * 16 : 0);
+  constexpr size_t kSmemMax = 64 * 1024;
+  static PerDeviceOnce once;
+  const cudaError_t attr = once.run([] {
+    cudaError_t e = cudaFuncSetAttribute(k_gcore_chunks<T, 1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_gcore_chunks<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemMax);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_gcore_chunks<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemMax);
+    return e;
+  });
+  if (attr != cudaSuccess) return fail(BKS_ECUDA, "k_gcore_chunks shared-memory limit not accepted");
+  if (smem > kSmemMax) return fail(BKS_EUNSUPPORTED, "general core: shared-memory tile above its limit");
+  DevBuf Xp, Yp, Mp, Sl;
+  BKS_TRY((pack<T, double>(X, ldx, t->l, k1, KP1, Xp, s)));
+  BKS_TRY((pack<T, double>(Y, ldy, t->m, k2, KP2, Yp, s)));
+  BKS_TRY(Mp.alloc(sizeof(T) * (size_t)cp.nch * kk, s));
+  const Part& P = t->m3;
+  auto kern = tpt == 1 ? k_gcore_chunks<T, 1> : (tpt == 2 ? k_gcore_chunks<T, 2> : k_gcore_chunks<T, 4>);
+  kern<<<cp.nch, kCoreThreads, smem, s>>>(cp.chunk_run.as<int32_t>(), cp.run_start.as<int32_t>(),
+                                          P.c0.as<int32_t>(), P.c1.as<int32_t>(),
+                                          values_of<T>(P, t->vdtype), Xp.as<T>(), k1, KP1,
+                                          Yp.as<T>(), k2, KP2, batch, ngroups, Mp.as<T>()); ::bks::note_launch();
+  BKS_CUDA_TRY(cudaGetLastError());
+  BKS_TRY(Sl.alloc(sizeof(T) * (size_t)cp.nsl * kk, s));
+  k_gcore_slice_sum<T><<<grid_for(cp.nsl * kk), 256, 0, s>>>(Mp.as<T>(), cp.sl_first.as<int32_t>(),
+                                                            cp.nsl, kk, Sl.as<T>()); ::bks::note_launch();
+  k_gcore_combine<T><<<grid_for(kk * k3), 256, 0, s>>>(Sl.as<T>(), cp.sl_k.as<int32_t>(), cp.nsl,
+                                                       kk, Z, ldz, k3, C); ::bks::note_launch();
+  BKS_CUDA_TRY(cudaGetLastError());
+  return BKS_OK;
+}
+
 // ---- run plan of the core ---------------------------------------------------
 // Runs: maximal ranges of equal (slice, i) of the mode-3 copy, cut at chunk
 // starts and after every kRunCap entries.
@@ -607,6 +829,16 @@ int contract_core_x(const bks_tensor* t, const double* U, int64_t ldu, int r1, c
   return core_typed<double, double, double>(t, U, ldu, r1, W, ldw, r3, F, s);
 }
 
+int gen_contract_x(const bks_tensor* t, int md, const double* B1, int64_t ld1, int p,
+                   const double* B2, int64_t ld2, int q, double* out, int64_t ldo, cudaStream_t s) {
+  return gen_contract_typed<double, double, double>(t, md, B1, ld1, p, B2, ld2, q, out, ldo, s);
+}
+int gen_core_x(const bks_tensor* t, const double* X, int64_t ldx, int k1, const double* Y,
+               int64_t ldy, int k2, const double* Z, int64_t ldz, int k3, double* C,
+               cudaStream_t s) {
+  return gen_core_fp64(t, X, ldx, k1, Y, ldy, k2, Z, ldz, k3, C, s);
+}
+
 }  // namespace bks
 
 using namespace bks;
@@ -624,6 +856,7 @@ static int check_common(const bks_tensor* t, const void* X, int64_t ldx, int p, 
 extern "C" int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
                                   const void* Y, int64_t ldy, int q, void* out, int64_t ldo,
                                   int dtype, void* stream) {
+  BKS_TRY(require_symmetric(t));
   BKS_TRY(check_common(t, X, ldx, p, dtype, t ? t->m : 0));
   BKS_TRY(check_common(t, Y, ldy, q, dtype, t->n));
   if (!out || ldo < t->m) return fail(BKS_EINVAL, "bad output");
@@ -634,6 +867,7 @@ extern "C" int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ld
 extern "C" int bks_contract_mode3(const bks_tensor* t, const void* X, int64_t ldx, int p,
                                   const void* X2, int64_t ldx2, int q, void* out, int64_t ldo,
                                   int dtype, void* stream) {
+  BKS_TRY(require_symmetric(t));
   BKS_TRY(check_common(t, X, ldx, p, dtype, t ? t->m : 0));
   if (X2) BKS_TRY(check_common(t, X2, ldx2, q, dtype, t->m));
   if (!out || ldo < t->n) return fail(BKS_EINVAL, "bad output");
@@ -643,6 +877,7 @@ extern "C" int bks_contract_mode3(const bks_tensor* t, const void* X, int64_t ld
 
 extern "C" int bks_core(const bks_tensor* t, const void* U, int64_t ldu, int r1, const void* W,
                         int64_t ldw, int r3, void* F, int dtype, void* stream) {
+  BKS_TRY(require_symmetric(t));
   BKS_TRY(check_common(t, U, ldu, r1, dtype, t ? t->m : 0));
   BKS_TRY(check_common(t, W, ldw, r3, dtype, t->n));
   if (!F) return fail(BKS_EINVAL, "null F");
@@ -708,6 +943,7 @@ int mode1_noalloc_typed(const bks_tensor* t, const T* X, int64_t ldx, int p, con
 extern "C" int bks_contract_mode1_noalloc(const bks_tensor* t, const void* X, int64_t ldx,
                                           int p, const void* Y, int64_t ldy, int q, void* out,
                                           int64_t ldo, int dtype, void* stream) {
+  BKS_TRY(require_symmetric(t));
   BKS_TRY(check_common(t, X, ldx, p, dtype, t ? t->m : 0));
   BKS_TRY(check_common(t, Y, ldy, q, dtype, t->n));
   if (!out || ldo < t->m) return fail(BKS_EINVAL, "bad output");
@@ -718,4 +954,39 @@ extern "C" int bks_contract_mode1_noalloc(const bks_tensor* t, const void* X, in
                                        (double*)out, ldo, s);
   return mode1_noalloc_typed<float>(t, (const float*)X, ldx, p, (const float*)Y, ldy, q,
                                     (float*)out, ldo, s);
+}
+
+extern "C" int bks_gen_contract(const bks_tensor* t, int mode, const void* B1, int64_t ld1, int p,
+                                const void* B2, int64_t ld2, int q, void* out, int64_t ldo,
+                                int dtype, void* stream) {
+  if (!t) return fail(BKS_EINVAL, "null tensor");
+  BKS_TRY(require_general(t));
+  if (mode < 1 || mode > 3) return fail(BKS_EINVAL, "mode must be 1, 2 or 3");
+  const int64_t rows1 = mode == 1 ? t->m : t->l;
+  const int64_t rows2 = mode == 3 ? t->m : t->n;
+  const int64_t rows_out = mode == 1 ? t->l : (mode == 2 ? t->m : t->n);
+  BKS_TRY(check_common(t, B1, ld1, p, dtype, rows1));
+  BKS_TRY(check_common(t, B2, ld2, q, dtype, rows2));
+  if (!out || ldo < rows_out) return fail(BKS_EINVAL, "bad output");
+  if (p > 8 || q > 8) return fail(BKS_EUNSUPPORTED, "widths p, q must be <= 8");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == BKS_F64)
+    return gen_contract_typed<double, double, double>(t, mode, (const double*)B1, ld1, p,
+                                                      (const double*)B2, ld2, q, (double*)out,
+                                                      ldo, s);
+  return gen_contract_typed<float, float, float>(t, mode, (const float*)B1, ld1, p,
+                                                 (const float*)B2, ld2, q, (float*)out, ldo, s);
+}
+
+extern "C" int bks_gen_core(const bks_tensor* t, const double* X, int64_t ldx, int k1,
+                            const double* Y, int64_t ldy, int k2, const double* Z, int64_t ldz,
+                            int k3, double* C, void* stream) {
+  if (!t) return fail(BKS_EINVAL, "null tensor");
+  BKS_TRY(require_general(t));
+  BKS_TRY(check_common(t, X, ldx, k1, BKS_F64, t->l));
+  BKS_TRY(check_common(t, Y, ldy, k2, BKS_F64, t->m));
+  BKS_TRY(check_common(t, Z, ldz, k3, BKS_F64, t->n));
+  if (!C) return fail(BKS_EINVAL, "null C");
+  if (k1 > 128 || k2 > 128 || k3 > 128) return fail(BKS_EUNSUPPORTED, "core ranks must be <= 128");
+  return gen_core_fp64(t, X, ldx, k1, Y, ldy, k2, Z, ldz, k3, C, (cudaStream_t)stream);
 }

@@ -515,6 +515,7 @@ extern "C" int bks_s_values(const bks_tensor* t, const double* U, int64_t ldu, i
                             const double* W, int64_t ldw, int r3, double* s1, double* s3,
                             void* stream) {
   if (!t || !U || !W || !s1 || !s3) return fail(BKS_EINVAL, "null argument");
+  BKS_TRY(require_symmetric(t));
   if (r1 < 1 || r3 < 1 || r1 > 8 || r3 > 8 || r1 >= t->m || r3 >= t->n)
     return fail(BKS_EINVAL, "need 1 <= r1 < m, 1 <= r3 < n and r1, r3 <= 8");
   if (ldu < t->m || ldw < t->n) return fail(BKS_EINVAL, "leading dimension below the rows");
@@ -523,6 +524,7 @@ extern "C" int bks_s_values(const bks_tensor* t, const double* U, int64_t ldu, i
 
 extern "C" int bks_slice_norms(const bks_tensor* t, int kind, double* norms, void* stream) {
   if (!t || !norms) return fail(BKS_EINVAL, "null argument");
+  BKS_TRY(require_symmetric(t));
   cudaStream_t s = (cudaStream_t)stream;
   const bool f64 = t->vdtype == BKS_F64;
   if (kind == BKS_NORM_FRO)
@@ -537,6 +539,7 @@ extern "C" int bks_tensor_scale_slices(const bks_tensor* t, const double* scales
   if (!out) return fail(BKS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!t || !scales) return fail(BKS_EINVAL, "null argument");
+  BKS_TRY(require_symmetric(t));
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t nnz = t->nnz;
   const size_t vs = t->vdtype == BKS_F64 ? 8 : 4;

@@ -1,7 +1,8 @@
-// Tensor ingest (Definition 2.1): validate, mirror, stable sort by (i,k,j),
-// sum duplicates left to right in the value dtype, build the two sorted
-// copies (rows i for the mode-1 contraction, rows k for mode 3 and the
-// cores) with their work-tile plans.  Runs once per tensor.
+// Tensor ingest (Definition 2.1): validate, mirror, stable sort by (i,j,k),
+// sum duplicates left to right in the value dtype, build the sorted copies
+// (rows i for the mode-1 contraction, rows k for mode 3 and the cores, and
+// for a general l x m x n tensor rows j for mode 2) with their work-tile
+// plans.  Runs once per tensor.
 #include <algorithm>
 #include <cstring>
 #include <atomic>
@@ -23,10 +24,10 @@ int fail(int code, const std::string& msg) {
 namespace {
 
 __global__ void k_validate(const int32_t* i, const int32_t* j, const int32_t* k, int64_t nnz,
-                           int64_t m, int64_t n, int* bad) {
+                           int64_t l, int64_t m, int64_t n, int* bad) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
        e += (int64_t)gridDim.x * blockDim.x) {
-    if (i[e] < 0 || i[e] >= m || j[e] < 0 || j[e] >= m || k[e] < 0 || k[e] >= n) atomicOr(bad, 1);
+    if (i[e] < 0 || i[e] >= l || j[e] < 0 || j[e] >= m || k[e] < 0 || k[e] >= n) atomicOr(bad, 1);
   }
 }
 
@@ -182,6 +183,29 @@ __global__ void k_gather_mode3(const uint64_t* keys, const uint32_t* pay, int64_
   }
 }
 
+// mode-2 copy of a general tensor: key (j << (bi+bk)) | (i << bk) | k
+__global__ void k_keys_mode2(const int32_t* row, const int32_t* kk, const int32_t* jj,
+                             int64_t nnz, int bi, int bk, uint64_t* keys, uint32_t* pay) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    keys[t] = ((uint64_t)jj[t] << (bi + bk)) | ((uint64_t)row[t] << bk) | (uint64_t)kk[t];
+    pay[t] = (uint32_t)t;
+  }
+}
+template <typename V>
+__global__ void k_gather_mode2(const uint64_t* keys, const uint32_t* pay, int64_t nnz, int bi,
+                               int bk, const V* vsrc, int32_t* jrow, int32_t* ii, int32_t* kk,
+                               V* v) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t key = keys[t];
+    jrow[t] = (int32_t)(key >> (bi + bk));
+    ii[t] = (int32_t)((key >> bk) & ((1ull << bi) - 1ull));
+    kk[t] = (int32_t)(key & ((1ull << bk) - 1ull));
+    v[t] = vsrc[pay[t]];
+  }
+}
+
 // ---- tile plan ------------------------------------------------------------
 __global__ void k_vcount(const int32_t* ptr, int64_t rows, int split, int32_t* nvr,
                          int32_t* nslot, int32_t* issplit, int32_t* isempty) {
@@ -320,11 +344,10 @@ int read_i32(const int32_t* dptr, int32_t* host, cudaStream_t s) {
 template <typename V>
 int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int32_t* dk,
                  const V* dv, int64_t nnz, int flags, cudaStream_t s) {
-  const int64_t m = T->m, n = T->n;
-  const bool mirror = flags & BKS_MIRROR;
-  const int bi = bits_for(m), bk = bits_for(n);
-  const int bj = bi;
-  if (bi + bi + bk > 64) return fail(BKS_EUNSUPPORTED, "m and n too large for a 64-bit sort key");
+  const int64_t l = T->l, m = T->m, n = T->n;
+  const bool mirror = !T->general && (flags & BKS_MIRROR);
+  const int bi = bits_for(l), bj = bits_for(m), bk = bits_for(n);
+  if (bi + bj + bk > 64) return fail(BKS_EUNSUPPORTED, "dimensions too large for a 64-bit sort key");
   // mirror positions
   DevBuf offf, offpos, mirror_src;
   int32_t noff = 0;
@@ -369,7 +392,7 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   }
   T->nnz = nseg;
   Part& P = T->m1;
-  P.rows = m;
+  P.rows = l;
   const int64_t S = std::max<int64_t>(nseg, 1);
   BKS_TRY(row.alloc(sizeof(int32_t) * S, s));
   BKS_TRY(P.c0.alloc(sizeof(int32_t) * S, s));
@@ -383,10 +406,10 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
                                                  P.c1.as<int32_t>(), P.v.as<V>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   head.release(); hpos.release(); starts.release(); offf.release(); offpos.release();
-  BKS_TRY(P.ptr.alloc(sizeof(int32_t) * (m + 1), s));
-  k_row_ptr<<<grid_for(nseg + 1), 256, 0, s>>>(row.as<int32_t>(), nseg, m, P.ptr.as<int32_t>()); ::bks::note_launch();
+  BKS_TRY(P.ptr.alloc(sizeof(int32_t) * (l + 1), s));
+  k_row_ptr<<<grid_for(nseg + 1), 256, 0, s>>>(row.as<int32_t>(), nseg, l, P.ptr.as<int32_t>()); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
-  if (!mirror && (flags & BKS_VALIDATE_SYMMETRIC)) {
+  if (!T->general && !mirror && (flags & BKS_VALIDATE_SYMMETRIC)) {
     DevBuf bad;
     BKS_TRY(bad.alloc(sizeof(int), s));
     BKS_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
@@ -450,13 +473,47 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
     k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)Q.v.p, Q.v64.as<double>(), nseg); ::bks::note_launch();
   }
   BKS_CUDA_TRY(cudaGetLastError());
+  if (T->general) {
+    // mode-2 copy sorted by (j, i, k)
+    Part& R = T->m2;
+    R.rows = m;
+    BKS_TRY(R.c0.alloc(sizeof(int32_t) * S, s));
+    BKS_TRY(R.c1.alloc(sizeof(int32_t) * S, s));
+    BKS_TRY(R.v.alloc(sizeof(V) * S, s));
+    DevBuf jrow;
+    BKS_TRY(jrow.alloc(sizeof(int32_t) * S, s));
+    if (nseg > 0) {
+      k_keys_mode2<<<grid_for(nseg), 256, 0, s>>>(row.as<int32_t>(), P.c0.as<int32_t>(),
+                                                  P.c1.as<int32_t>(), nseg, bi, bk,
+                                                  keys.as<uint64_t>(), pay.as<uint32_t>()); ::bks::note_launch();
+      BKS_CUDA_TRY(cudaGetLastError());
+      BKS_TRY(radix_sort_pairs(keys.as<uint64_t>(), pay.as<uint32_t>(), nseg, bj + bi + bk, s));
+      k_gather_mode2<V><<<grid_for(nseg), 256, 0, s>>>(keys.as<uint64_t>(), pay.as<uint32_t>(),
+                                                       nseg, bi, bk, P.v.as<V>(),
+                                                       jrow.as<int32_t>(), R.c1.as<int32_t>(),
+                                                       R.c0.as<int32_t>(), R.v.as<V>()); ::bks::note_launch();
+      BKS_CUDA_TRY(cudaGetLastError());
+    }
+    BKS_TRY(R.ptr.alloc(sizeof(int32_t) * (m + 1), s));
+    k_row_ptr<<<grid_for(nseg + 1), 256, 0, s>>>(jrow.as<int32_t>(), nseg, m, R.ptr.as<int32_t>()); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+    if (sizeof(V) == 8) {
+      BKS_TRY(R.v32.alloc(sizeof(float) * S, s));
+      k_convert<double, float><<<grid_for(nseg), 256, 0, s>>>((const double*)R.v.p, R.v32.as<float>(), nseg); ::bks::note_launch();
+    } else {
+      BKS_TRY(R.v64.alloc(sizeof(double) * S, s));
+      k_convert<float, double><<<grid_for(nseg), 256, 0, s>>>((const float*)R.v.p, R.v64.as<double>(), nseg); ::bks::note_launch();
+    }
+    BKS_CUDA_TRY(cudaGetLastError());
+  }
   {
     int tile = kTile, split = kSplit;
     default_plan(nseg, &tile, &split);
-    T->m1.tile = T->m3.tile = tile;
-    T->m1.split = T->m3.split = split;
+    T->m1.tile = T->m2.tile = T->m3.tile = tile;
+    T->m1.split = T->m2.split = T->m3.split = split;
   }
   BKS_TRY(build_tile_plan(T->m1, nseg, s));
+  if (T->general) BKS_TRY(build_tile_plan(T->m2, nseg, s));
   BKS_TRY(build_tile_plan(T->m3, nseg, s));
   Q.host_ptr.resize(n + 1);
   BKS_CUDA_TRY(cudaMemcpyAsync(Q.host_ptr.data(), Q.ptr.p, sizeof(int32_t) * (n + 1),
@@ -465,6 +522,7 @@ int ingest_typed(bks_tensor* T, const int32_t* di, const int32_t* dj, const int3
   BKS_TRY(build_core_plan(Q, n, nseg, T->cp, s));
   P.persist();
   Q.persist();
+  if (T->general) T->m2.persist();
   T->cp.persist();
   return BKS_OK;
 }
@@ -606,24 +664,31 @@ int build_tile_plan(Part& P, int64_t nnz, cudaStream_t s) {
 
 using namespace bks;
 
-extern "C" int bks_tensor_create_coo(int64_t m, int64_t n, int64_t nnz, const int32_t* i,
-                                     const int32_t* j, const int32_t* k, const void* v,
-                                     int vdtype, int flags, void* stream, bks_tensor** out) {
+namespace bks {
+namespace {
+int create_impl(int64_t l, int64_t m, int64_t n, int64_t nnz, const int32_t* i, const int32_t* j,
+                const int32_t* k, const void* v, int vdtype, int flags, bool general, void* stream,
+                bks_tensor** out) {
   if (!out) return fail(BKS_EINVAL, "out is NULL");
   *out = nullptr;
-  if (m < 1 || n < 1 || nnz < 0) return fail(BKS_EINVAL, "need m >= 1, n >= 1, nnz >= 0");
-  if (m >= (1ll << 31) || n >= (1ll << 31)) return fail(BKS_EUNSUPPORTED, "m, n must fit int32");
+  if (l < 1 || m < 1 || n < 1 || nnz < 0) return fail(BKS_EINVAL, "need dimensions >= 1, nnz >= 0");
+  if (l >= (1ll << 31) || m >= (1ll << 31) || n >= (1ll << 31))
+    return fail(BKS_EUNSUPPORTED, "dimensions must fit int32");
   if (nnz > 0 && (!i || !j || !k || !v)) return fail(BKS_EINVAL, "null index or value pointer");
   if (vdtype != BKS_F32 && vdtype != BKS_F64) return fail(BKS_EINVAL, "vdtype must be BKS_F32 or BKS_F64");
+  if (general && (flags & (BKS_MIRROR | BKS_VALIDATE_SYMMETRIC)))
+    return fail(BKS_EINVAL, "BKS_MIRROR and BKS_VALIDATE_SYMMETRIC apply to symmetric tensors only");
   if ((flags & BKS_MIRROR) && (flags & BKS_VALIDATE_SYMMETRIC))
     return fail(BKS_EINVAL, "BKS_VALIDATE_SYMMETRIC applies to input without BKS_MIRROR");
   if (nnz >= (1ll << 31)) return fail(BKS_EUNSUPPORTED, "nnz must fit int32");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t vs = vdtype == BKS_F64 ? 8 : 4;
   auto* T = new bks_tensor();
+  T->l = l;
   T->m = m;
   T->n = n;
   T->vdtype = vdtype;
+  T->general = general ? 1 : 0;
   int rc = BKS_OK;
   {
     DevBuf hi, hj, hk, hv;
@@ -649,11 +714,12 @@ extern "C" int bks_tensor_create_coo(int64_t m, int64_t n, int64_t nnz, const in
       if (rc == BKS_OK) {
         int hb = 0;
         cudaMemsetAsync(bad.p, 0, sizeof(int), s);
-        k_validate<<<grid_for(nnz), 256, 0, s>>>(di, dj, dk, nnz, m, n, bad.as<int>()); ::bks::note_launch();
+        k_validate<<<grid_for(nnz), 256, 0, s>>>(di, dj, dk, nnz, l, m, n, bad.as<int>()); ::bks::note_launch();
         cudaError_t e = cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = fail(BKS_ECUDA, std::string("validate: ") + cudaGetErrorString(e));
-        else if (hb) rc = fail(BKS_EINVAL, "index out of range (i, j >= m or k >= n or negative)");
+        else if (hb) rc = fail(BKS_EINVAL, general ? "index out of range (i >= l, j >= m, k >= n or negative)"
+                                                   : "index out of range (i, j >= m or k >= n or negative)");
       }
     }
     if (rc == BKS_OK) {
@@ -671,11 +737,36 @@ extern "C" int bks_tensor_create_coo(int64_t m, int64_t n, int64_t nnz, const in
   *out = T;
   return BKS_OK;
 }
+}  // namespace
+}  // namespace bks
+
+extern "C" int bks_tensor_create_coo(int64_t m, int64_t n, int64_t nnz, const int32_t* i,
+                                     const int32_t* j, const int32_t* k, const void* v,
+                                     int vdtype, int flags, void* stream, bks_tensor** out) {
+  return create_impl(m, m, n, nnz, i, j, k, v, vdtype, flags, false, stream, out);
+}
+
+extern "C" int bks_gen_tensor_create_coo(int64_t l, int64_t m, int64_t n, int64_t nnz,
+                                         const int32_t* i, const int32_t* j, const int32_t* k,
+                                         const void* v, int vdtype, int flags, void* stream,
+                                         bks_tensor** out) {
+  return create_impl(l, m, n, nnz, i, j, k, v, vdtype, flags, true, stream, out);
+}
 
 extern "C" void bks_tensor_destroy(bks_tensor* t) {
   if (!t) return;
   cudaDeviceSynchronize();
   delete t;
+}
+
+extern "C" int bks_gen_tensor_dims(const bks_tensor* t, int64_t* l, int64_t* m, int64_t* n,
+                                   int* general) {
+  if (!t) return fail(BKS_EINVAL, "null tensor");
+  if (l) *l = t->l;
+  if (m) *m = t->m;
+  if (n) *n = t->n;
+  if (general) *general = t->general;
+  return BKS_OK;
 }
 
 extern "C" int bks_tensor_info(const bks_tensor* t, int64_t* m, int64_t* n, int64_t* nnz,
@@ -695,7 +786,7 @@ extern "C" int bks_tensor_export_coo(const bks_tensor* t, int32_t* i, int32_t* j
   if (!i || !j || !k || !v) return fail(BKS_EINVAL, "null output pointer");
   cudaStream_t s = (cudaStream_t)stream;
   const Part& P = t->m1;
-  k_expand_rows<<<grid_for(t->m), 256, 0, s>>>(P.ptr.as<int32_t>(), t->m, i); ::bks::note_launch();
+  k_expand_rows<<<grid_for(P.rows), 256, 0, s>>>(P.ptr.as<int32_t>(), P.rows, i); ::bks::note_launch();
   BKS_CUDA_TRY(cudaGetLastError());
   BKS_CUDA_TRY(cudaMemcpyAsync(j, P.c1.p, 4 * t->nnz, cudaMemcpyDeviceToDevice, s));
   BKS_CUDA_TRY(cudaMemcpyAsync(k, P.c0.p, 4 * t->nnz, cudaMemcpyDeviceToDevice, s));

@@ -689,6 +689,290 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_coop(CoopArgs a) {
   }
 }
 
+// ---- general core (Section 5): three factors -------------------------------
+// C is k1 x k2 x k3 without symmetry.  A sweep updates Uh from
+// T1 = unfold_1(C.(Vh,Wh)_{2,3}), then Vh from T2 = unfold_2(C.(Uh,Wh)_{1,3})
+// with the new Uh, then Wh from T3 = unfold_3(C.(Uh,Vh)_{1,2}) with the new
+// Uh and Vh; each update is the r leading left singular vectors, which
+// maximises ||F|| over that factor, so ||F|| never drops.
+struct GenArgs {
+  const double* C;
+  int k1, k2, k3, r1, r2, r3;
+  double tol;
+  int max_inner, init_sweeps;
+  const double* Uh0;  // HOSVD candidate
+  const double* Vh0;
+  const double* Wh0;
+  double* Ug;         // current factors
+  double* Vg;
+  double* Wg;
+  double* Ub;         // saved candidate
+  double* Vb;
+  double* Wb;
+  double* D;          // k1 k2 x r3: C x_3 Wh^T
+  double* E;          // r1 x k2 x k3: C x_1 Uh^T
+  double* T1;         // k1 x r2 r3, column b' + r2 c'
+  double* T2;         // k2 x r1 r3, column a' + r1 c'
+  double* T3;         // k3 x r1 r2, column a' + r1 b'
+  double* ctl;        // [0] grad [1] normF [2] stop flag
+  double* P;
+  double* R;
+  double* E2;
+  double* negU;
+  double* negV;
+  double* negW;
+  double* info;
+};
+
+// D[x + k1 k2 t] = sum_c C[x + k1 k2 c] Wh[c, t]
+__device__ void gen_D(const GenArgs& a) {
+  const int64_t kk = (int64_t)a.k1 * a.k2;
+  for (int64_t o = gtid(); o < kk * a.r3; o += gsize()) {
+    const int64_t x = o % kk;
+    const int t = (int)(o / kk);
+    double s = 0.0;
+    for (int c = 0; c < a.k3; ++c) s = fma(a.C[x + kk * c], a.Wg[c + a.k3 * t], s);
+    a.D[o] = s;
+  }
+}
+// T1[i + k1 (b' + r2 c')] = sum_b D[i + k1 (b + k2 c')] Vh[b, b']
+__device__ void gen_T1(const GenArgs& a) {
+  const int64_t n = (int64_t)a.k1 * a.r2 * a.r3;
+  for (int64_t o = gtid(); o < n; o += gsize()) {
+    const int i = (int)(o % a.k1);
+    const int j = (int)(o / a.k1);
+    const int bp = j % a.r2, cp = j / a.r2;
+    double s = 0.0;
+    for (int b = 0; b < a.k2; ++b)
+      s = fma(a.D[i + (int64_t)a.k1 * (b + (int64_t)a.k2 * cp)], a.Vg[b + a.k2 * bp], s);
+    a.T1[o] = s;
+  }
+}
+// T2[b + k2 (a' + r1 c')] = sum_a D[a + k1 (b + k2 c')] Uh[a, a']
+__device__ void gen_T2(const GenArgs& a) {
+  const int64_t n = (int64_t)a.k2 * a.r1 * a.r3;
+  for (int64_t o = gtid(); o < n; o += gsize()) {
+    const int b = (int)(o % a.k2);
+    const int j = (int)(o / a.k2);
+    const int ap = j % a.r1, cp = j / a.r1;
+    const double* d = a.D + (int64_t)a.k1 * (b + (int64_t)a.k2 * cp);
+    double s = 0.0;
+    for (int i = 0; i < a.k1; ++i) s = fma(d[i], a.Ug[i + a.k1 * ap], s);
+    a.T2[o] = s;
+  }
+}
+// E[t + r1 (b + k2 c)] = sum_i Uh[i, t] C[i + k1 (b + k2 c)]
+__device__ void gen_E(const GenArgs& a) {
+  const int64_t bc = (int64_t)a.k2 * a.k3;
+  for (int64_t o = gtid(); o < bc * a.r1; o += gsize()) {
+    const int64_t x = o % bc;
+    const int t = (int)(o / bc);
+    const double* col = a.C + (int64_t)a.k1 * x;
+    double s = 0.0;
+    for (int i = 0; i < a.k1; ++i) s = fma(a.Ug[i + a.k1 * t], col[i], s);
+    a.E[t + (int64_t)a.r1 * x] = s;
+  }
+}
+// T3[c + k3 (a' + r1 b')] = sum_b E[a' + r1 (b + k2 c)] Vh[b, b']
+__device__ void gen_T3(const GenArgs& a) {
+  const int64_t n = (int64_t)a.k3 * a.r1 * a.r2;
+  for (int64_t o = gtid(); o < n; o += gsize()) {
+    const int c = (int)(o % a.k3);
+    const int j = (int)(o / a.k3);
+    const int ap = j % a.r1, bp = j / a.r1;
+    double s = 0.0;
+    for (int b = 0; b < a.k2; ++b)
+      s = fma(a.E[ap + (int64_t)a.r1 * (b + (int64_t)a.k2 * c)], a.Vg[b + a.k2 * bp], s);
+    a.T3[o] = s;
+  }
+}
+
+// One mode's part of the G-gradient at the current point: with F = Q^T T
+// (r x w), adds ||T F^T - Q (F F^T)||^2 of this thread's rows to g and,
+// for mode 1, ||F||^2 of its entries to nf.  Q (k x r) and T (k x w) in
+// global memory; F and F F^T in S.F1, S.FF1.  Every thread calls.
+__device__ void gen_mode_grad(const double* Q, const double* T, int k, int r, int w,
+                              InnerShared& S, bool first, double& g, double& nf) {
+  for (int x = threadIdx.x; x < r * w; x += blockDim.x) {
+    const int aa = x % r, j = x / r;
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s = fma(Q[i + k * aa], T[i + k * j], s);
+    S.F1[x] = s;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < r * r; x += blockDim.x) {
+    const int aa = x % r, bb = x / r;
+    double s = 0.0;
+    for (int j = 0; j < w; ++j) s = fma(S.F1[aa + r * j], S.F1[bb + r * j], s);
+    S.FF1[x] = s;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < k * r; x += blockDim.x) {
+    const int i = x % k, aa = x / k;
+    double d = 0.0;
+    for (int j = 0; j < w; ++j) d = fma(T[i + k * j], S.F1[aa + r * j], d);
+    for (int bb = 0; bb < r; ++bb) d = fma(-Q[i + k * bb], S.FF1[bb + r * aa], d);
+    g = fma(d, d, g);
+  }
+  if (first)
+    for (int x = threadIdx.x; x < r * w; x += blockDim.x) nf = fma(S.F1[x], S.F1[x], nf);
+  __syncthreads();
+}
+
+// ||grad||, ||F|| at (Ug, Vg, Wg) from T1, T2, T3 there, to ctl[0..1]
+// (block 0 only).
+__device__ void gen_grad(const GenArgs& a, InnerShared& S) {
+  double g = 0.0, nf = 0.0, z = 0.0;
+  gen_mode_grad(a.Ug, a.T1, a.k1, a.r1, a.r2 * a.r3, S, true, g, nf);
+  gen_mode_grad(a.Vg, a.T2, a.k2, a.r2, a.r1 * a.r3, S, false, g, nf);
+  gen_mode_grad(a.Wg, a.T3, a.k3, a.r3, a.r1 * a.r2, S, false, g, nf);
+  block_sum3(g, nf, z);
+  if (threadIdx.x == 0) {
+    a.ctl[0] = sqrt(g);
+    a.ctl[1] = sqrt(nf);
+  }
+  __syncthreads();
+}
+
+// new factor (k x r) into the global `dst`: the r leading left singular
+// vectors of T (k x w); block 0 only
+__device__ void gen_update(const GenArgs& a, const double* T, int k, int w, int r, double* dst,
+                           InnerShared& S) {
+  inner_topsvd(T, k, w, r, S, S.Uh, a.P, a.R, a.E2);
+  block_copy(S.Uh, dst, k * r);
+  __threadfence();
+}
+
+// General HOOI sweeps from (Ug, Vg, Wg); returns the sweeps done; ctl[0..1]
+// hold the gradient and ||F|| at the returned point.
+__device__ int gen_sweeps(const GenArgs& a, int max_sweeps, double tol, InnerShared& S,
+                          cg::grid_group& grid) {
+  gen_E(a);
+  grid.sync();
+  gen_T3(a);
+  grid.sync();
+  int done = 0;
+  for (;;) {
+    gen_D(a);
+    grid.sync();
+    gen_T1(a);
+    gen_T2(a);
+    grid.sync();
+    if (blockIdx.x == 0) {
+      gen_grad(a, S);
+      const double g = a.ctl[0], nf = a.ctl[1];
+      const bool stop = done >= max_sweeps || g <= tol * nf;
+      if (!stop) gen_update(a, a.T1, a.k1, a.r2 * a.r3, a.r1, a.Ug, S);
+      if (threadIdx.x == 0) a.ctl[2] = stop ? 1.0 : 0.0;
+      __threadfence();
+    }
+    grid.sync();
+    if (a.ctl[2] != 0.0) break;
+    gen_T2(a);
+    grid.sync();
+    if (blockIdx.x == 0) gen_update(a, a.T2, a.k2, a.r1 * a.r3, a.r2, a.Vg, S);
+    grid.sync();
+    gen_E(a);
+    grid.sync();
+    gen_T3(a);
+    grid.sync();
+    if (blockIdx.x == 0) gen_update(a, a.T3, a.k3, a.r1 * a.r2, a.r3, a.Wg, S);
+    grid.sync();
+    ++done;
+  }
+  return done;
+}
+
+__global__ void __launch_bounds__(kInnerThreads) k_inner_gen(GenArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ double shd[];
+  InnerShared& S = *reinterpret_cast<InnerShared*>(shd);
+  const int nu = a.k1 * a.r1, nv = a.k2 * a.r2, nw = a.k3 * a.r3;
+  // candidate 1: truncated HOSVD (FP32 eigenvectors orthonormalised in
+  // FP64 first) + init sweeps
+  if (blockIdx.x == 0) {
+    const double* src[3] = {a.Uh0, a.Vh0, a.Wh0};
+    double* dst[3] = {a.Ug, a.Vg, a.Wg};
+    const int kk[3] = {a.k1, a.k2, a.k3}, rr[3] = {a.r1, a.r2, a.r3};
+    for (int md = 0; md < 3; ++md) {
+      block_copy(src[md], S.Uh, kk[md] * rr[md]);
+      __syncthreads();
+      block_mgs2(S.Uh, kk[md], rr[md], S.red);
+      block_copy(S.Uh, dst[md], kk[md] * rr[md]);
+      __syncthreads();
+    }
+    __threadfence();
+  }
+  grid.sync();
+  gen_sweeps(a, a.init_sweeps, 0.0, S, grid);
+  const double nf_a = a.ctl[1];
+  for (int64_t x = gtid(); x < nu; x += gsize()) a.Ub[x] = a.Ug[x];
+  for (int64_t x = gtid(); x < nv; x += gsize()) a.Vb[x] = a.Vg[x];
+  for (int64_t x = gtid(); x < nw; x += gsize()) a.Wb[x] = a.Wg[x];
+  grid.sync();
+  // candidate 2: the current point [I; 0], evaluated without sweeps
+  for (int64_t x = gtid(); x < nu; x += gsize()) a.Ug[x] = (x % a.k1 == x / a.k1) ? 1.0 : 0.0;
+  for (int64_t x = gtid(); x < nv; x += gsize()) a.Vg[x] = (x % a.k2 == x / a.k2) ? 1.0 : 0.0;
+  for (int64_t x = gtid(); x < nw; x += gsize()) a.Wg[x] = (x % a.k3 == x / a.k3) ? 1.0 : 0.0;
+  grid.sync();
+  gen_sweeps(a, 0, 0.0, S, grid);
+  const double nf_b = a.ctl[1];
+  const bool hosvd_won = nf_a >= nf_b;
+  grid.sync();
+  if (hosvd_won) {
+    for (int64_t x = gtid(); x < nu; x += gsize()) a.Ug[x] = a.Ub[x];
+    for (int64_t x = gtid(); x < nv; x += gsize()) a.Vg[x] = a.Vb[x];
+    for (int64_t x = gtid(); x < nw; x += gsize()) a.Wg[x] = a.Wb[x];
+  }
+  grid.sync();
+  const int done = gen_sweeps(a, a.max_inner, a.tol, S, grid);
+  if (blockIdx.x == 0) {
+    for (int x = threadIdx.x; x < nu; x += blockDim.x) a.negU[x] = -a.Ug[x];
+    for (int x = threadIdx.x; x < nv; x += blockDim.x) a.negV[x] = -a.Vg[x];
+    for (int x = threadIdx.x; x < nw; x += blockDim.x) a.negW[x] = -a.Wg[x];
+    if (threadIdx.x == 0) {
+      a.info[0] = a.ctl[0];
+      a.info[1] = a.ctl[1];
+      a.info[2] = done + (hosvd_won ? a.init_sweeps : 0);
+      a.info[3] = hosvd_won ? 1.0 : 0.0;
+    }
+  }
+}
+
+// Partial Grams of the unfoldings of the general core in FP32: part[md]
+// (nparts x k_md x k_md) with block b of grid row md summing its share of
+// the other two indices (o = the column of unfold_md, first index fastest).
+__global__ void k_gen_grams(const double* __restrict__ C, int k1, int k2, int k3,
+                            float* __restrict__ p1, float* __restrict__ p2,
+                            float* __restrict__ p3) {
+  const int md = blockIdx.y;
+  const int n = md == 0 ? k1 : (md == 1 ? k2 : k3);
+  const int64_t ncol = (int64_t)k1 * k2 * k3 / n;
+  float* part = md == 0 ? p1 : (md == 1 ? p2 : p3);
+  const int nb = gridDim.x;
+  const int64_t o0 = ncol * blockIdx.x / nb, o1 = ncol * (blockIdx.x + 1) / nb;
+  for (int x = threadIdx.x; x < n * n; x += blockDim.x) {
+    const int u = x % n, w = x / n;
+    float s = 0.f;
+    for (int64_t o = o0; o < o1; ++o) {
+      int64_t eu, ew;
+      if (md == 0) {
+        eu = u + (int64_t)k1 * o;
+        ew = w + (int64_t)k1 * o;
+      } else if (md == 1) {
+        const int64_t aa = o % k1, cc = o / k1;
+        eu = aa + (int64_t)k1 * (u + (int64_t)k2 * cc);
+        ew = aa + (int64_t)k1 * (w + (int64_t)k2 * cc);
+      } else {
+        eu = o + (int64_t)k1 * k2 * u;
+        ew = o + (int64_t)k1 * k2 * w;
+      }
+      s += (float)C[eu] * (float)C[ew];
+    }
+    part[(int64_t)blockIdx.x * n * n + x] = s;
+  }
+}
+
 }  // namespace
 
 struct InnerWork {
@@ -844,6 +1128,100 @@ int inner_solve(const double* C, int k1, int k3, int r1, int r3, double tol, int
   w.host_info[3] = hosvd_won;
   BKS_CUDA_TRY(cudaMemcpyAsync(info, w.host_info, sizeof(w.host_info), cudaMemcpyHostToDevice, s));
   BKS_CUDA_TRY(cudaStreamSynchronize(s));
+  return BKS_OK;
+}
+
+
+struct GenInnerWork {
+  DevBuf p1, p2, p3, Uh0, Vh0, Wh0, scratch, Ug, Vg, Wg, Ub, Vb, Wb, D, E, T1, T2, T3, ctl, K;
+  int coop_grid = 0;
+};
+
+// General inner solve (Algorithm 5 step (i) for a k1 x k2 x k3 core): the
+// better (larger ||F||) of the truncated HOSVD after init_sweeps HOOI
+// sweeps and the current point, then HOOI sweeps until ||grad|| <= tol
+// ||F|| or max_inner sweeps.  Writes -Uh, -Vh, -Wh (for the restart
+// combine) and info[4] = {grad, ||F||, sweeps, hosvd_won} on the device.
+int gen_inner_solve(const double* C, int k1, int k2, int k3, int r1, int r2, int r3, double tol,
+                    int max_inner, int init_sweeps, double* negU, double* negV, double* negW,
+                    double* info, cudaStream_t s) {
+  if (k1 > 128 || k2 > 128 || k3 > 128)
+    return fail(BKS_EUNSUPPORTED, "inner solve: k1, k2, k3 must be <= 128");
+  if (r1 > kMaxR || r2 > kMaxR || r3 > kMaxR || r1 * r2 > kMaxW || r1 * r3 > kMaxW ||
+      r2 * r3 > kMaxW)
+    return fail(BKS_EUNSUPPORTED, "inner solve: ranks must be <= 8");
+  if (r1 > k1 || r2 > k2 || r3 > k3) return fail(BKS_EINVAL, "inner solve: rank above the basis size");
+  static thread_local GenInnerWork ws_by_dev[kMaxDevices];
+  const int dev = current_device();
+  if (dev < 0) return fail(BKS_EUNSUPPORTED, "inner solve: device index above 63");
+  GenInnerWork& w = ws_by_dev[dev];
+  auto grow = [&](DevBuf& b, size_t bytes) -> int {
+    if (b.bytes < bytes) {
+      BKS_TRY(b.alloc(bytes, s));
+      b.persist();
+    }
+    return BKS_OK;
+  };
+  const int kmax = std::max(k1, std::max(k2, k3));
+  const int nparts = std::min(64, kmax);
+  BKS_TRY(grow(w.p1, sizeof(float) * (size_t)nparts * k1 * k1));
+  BKS_TRY(grow(w.p2, sizeof(float) * (size_t)nparts * k2 * k2));
+  BKS_TRY(grow(w.p3, sizeof(float) * (size_t)nparts * k3 * k3));
+  const size_t mat = sizeof(double) * 128 * kMaxR;
+  for (DevBuf* b : {&w.Uh0, &w.Vh0, &w.Wh0, &w.scratch, &w.Ug, &w.Vg, &w.Wg, &w.Ub, &w.Vb, &w.Wb})
+    BKS_TRY(grow(*b, mat));
+  BKS_TRY(grow(w.D, sizeof(double) * (size_t)k1 * k2 * r3));
+  BKS_TRY(grow(w.E, sizeof(double) * (size_t)r1 * k2 * k3));
+  const size_t tsz = sizeof(double) * 128 * kMaxW;
+  for (DevBuf* b : {&w.T1, &w.T2, &w.T3}) BKS_TRY(grow(*b, tsz));
+  BKS_TRY(grow(w.ctl, sizeof(double) * 8));
+  BKS_TRY(grow(w.K, sizeof(double) * 3 * kMaxW * kMaxW));
+  k_gen_grams<<<dim3(nparts, 3), 256, 0, s>>>(C, k1, k2, k3, w.p1.as<float>(), w.p2.as<float>(),
+                                              w.p3.as<float>()); ::bks::note_launch();
+  BKS_CUDA_TRY(cudaGetLastError());
+  static PerDeviceOnce once;
+  const cudaError_t attr = once.run([] {
+    return cudaFuncSetAttribute(k_hosvd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(float) * (2 * 128 * 128 + 64 + 4 * 128)));
+  });
+  if (attr != cudaSuccess)
+    return fail(BKS_ECUDA, std::string("k_hosvd shared-memory limit: ") + cudaGetErrorString(attr));
+  auto hs = [](int nmax) {
+    return sizeof(float) * (2 * (size_t)nmax * nmax + 64 + std::max<size_t>(128, 4 * (size_t)nmax));
+  };
+  // modes 1 and 2 in one launch (block 0, block 1), mode 3 in a second
+  k_hosvd<<<2, kInnerThreads, hs(std::max(k1, k2)), s>>>(w.p1.as<float>(), w.p2.as<float>(), nparts,
+                                                        k1, k2, r1, r2, w.Uh0.as<double>(),
+                                                        w.Vh0.as<double>()); ::bks::note_launch();
+  k_hosvd<<<2, kInnerThreads, hs(k3), s>>>(w.p3.as<float>(), w.p3.as<float>(), nparts, k3, k3, r3,
+                                           r3, w.Wh0.as<double>(), w.scratch.as<double>()); ::bks::note_launch();
+  BKS_CUDA_TRY(cudaGetLastError());
+  if (w.coop_grid == 0) {
+    int per_sm = 0;
+    BKS_CUDA_TRY(cudaFuncSetAttribute(k_inner_gen, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(InnerShared)));
+    BKS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inner_gen,
+                                                               kInnerThreads, sizeof(InnerShared)));
+    if (per_sm < 1) return fail(BKS_ECUDA, "inner solve: cooperative kernel does not fit on an SM");
+    w.coop_grid = std::min(64, per_sm * num_sms());
+  }
+  const int64_t work = std::max<int64_t>((int64_t)k1 * k2 * r3, (int64_t)r1 * k2 * k3);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(w.coop_grid, (work + 511) / 512));
+  GenArgs a;
+  a.C = C; a.k1 = k1; a.k2 = k2; a.k3 = k3; a.r1 = r1; a.r2 = r2; a.r3 = r3;
+  a.tol = tol; a.max_inner = max_inner; a.init_sweeps = std::max(0, init_sweeps);
+  a.Uh0 = w.Uh0.as<double>(); a.Vh0 = w.Vh0.as<double>(); a.Wh0 = w.Wh0.as<double>();
+  a.Ug = w.Ug.as<double>(); a.Vg = w.Vg.as<double>(); a.Wg = w.Wg.as<double>();
+  a.Ub = w.Ub.as<double>(); a.Vb = w.Vb.as<double>(); a.Wb = w.Wb.as<double>();
+  a.D = w.D.as<double>(); a.E = w.E.as<double>();
+  a.T1 = w.T1.as<double>(); a.T2 = w.T2.as<double>(); a.T3 = w.T3.as<double>();
+  a.ctl = w.ctl.as<double>();
+  a.P = w.K.as<double>(); a.R = a.P + kMaxW * kMaxW; a.E2 = a.R + kMaxW * kMaxW;
+  a.negU = negU; a.negV = negV; a.negW = negW; a.info = info;
+  void* kargs[] = {&a};
+  BKS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_inner_gen, dim3(grid), dim3(kInnerThreads),
+                                           kargs, sizeof(InnerShared), s));
+  ::bks::note_launch();
   return BKS_OK;
 }
 

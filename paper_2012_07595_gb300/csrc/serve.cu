@@ -72,6 +72,7 @@ extern "C" int bks_batch_solve(int njobs, bks_tensor* const* T, const bks_params
   if (njobs < 0 || (njobs > 0 && (!T || !P || !U || !W || !F)))
     return fail(BKS_EINVAL, "batch: null arrays");
   if (njobs == 0) return BKS_OK;
+  for (int q = 0; q < njobs; ++q) BKS_TRY(require_symmetric(T[q]));
   nstreams = std::max(1, std::min(nstreams, njobs));
   int dev = 0;
   BKS_CUDA_TRY(cudaGetDevice(&dev));

@@ -385,6 +385,7 @@ struct BksState {
 
 int check_params(const bks_tensor* t, const bks_params* p) {
   if (!t || !p) return fail(BKS_EINVAL, "null tensor or params");
+  BKS_TRY(require_symmetric(t));
   if (p->r1 < 1 || p->r3 < 1 || p->r1 > 8 || p->r3 > 8)
     return fail(BKS_EUNSUPPORTED, "ranks must be in 1..8");
   if (p->r1 > t->m || p->r3 > t->n) return fail(BKS_EINVAL, "rank larger than the dimension");
@@ -619,6 +620,7 @@ extern "C" int hooi_solve(const bks_tensor* t, const hooi_params* prm, const dou
                           const double* W0, double* U, double* W, double* F, bks_info* info,
                           void* stream) {
   if (!t || !prm) return fail(BKS_EINVAL, "null tensor or params");
+  BKS_TRY(require_symmetric(t));
   if (!U || !W || !F) return fail(BKS_EINVAL, "null output");
   const int r1 = prm->r1, r3 = prm->r3;
   if (r1 < 1 || r3 < 1 || r1 > 8 || r3 > 8 || r1 * r3 > kBlockMax)

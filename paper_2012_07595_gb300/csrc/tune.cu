@@ -80,10 +80,12 @@ int set_tiles(bks_tensor* t, int tile, int split, cudaStream_t s) {
 
 extern "C" int bks_tensor_autotune(bks_tensor* t, int* tile, int* split, void* stream) {
   if (!t) return bks::fail(BKS_EINVAL, "null tensor");
+  BKS_TRY(bks::require_symmetric(t));
   return bks::autotune_tensor(t, (cudaStream_t)stream, tile, split);
 }
 
 extern "C" int bks_tensor_set_tiles(bks_tensor* t, int tile, int split, void* stream) {
   if (!t) return bks::fail(BKS_EINVAL, "null tensor");
+  BKS_TRY(bks::require_symmetric(t));
   return bks::set_tiles(t, tile, split, (cudaStream_t)stream);
 }

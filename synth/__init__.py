@@ -34,6 +34,7 @@ __all__ = [
     "dense_planted", "example1", "batch_jobs", "serving_stream", "dense_to_coo",
     "random_coo", "CONFIG_SEEDS", "GenCOO", "general_random_coo", "general_zipf_tensor",
     "general_dense_planted", "general_dense_to_coo", "general_sampled_planted",
+    "general_noisy_planted",
 ]
 
 CONFIG_SEEDS = {"small": 1, "medium": 2, "large": 3, "batch": 4, "serve": 5}
@@ -344,15 +345,16 @@ def general_dense_planted(seed: int, l: int = 30, m: int = 24, n: int = 10,
 
 def general_sampled_planted(seed: int, l: int, m: int, n: int, draws: int, r=(2, 2, 2),
                             snr: float = 10.0) -> GenCOO:
-    """``draws`` uniform (i, j, k) positions with |N(0,1)| noise plus
+    """``draws`` uniform (i, j, k) positions with N(0,1) noise plus
     alpha * ((U0,V0,W0).F0)(i,j,k) at the drawn positions, alpha making the
     planted part ``snr`` times the noise part in norm (a sparse general
-    analogue of ``small_planted``)."""
+    analogue of ``small_planted``; zero-mean noise, so that the planted
+    multilinear rank is the dominant structure)."""
     g = rng(seed)
     i = g.integers(0, l, size=draws)
     j = g.integers(0, m, size=draws)
     k = g.integers(0, n, size=draws)
-    noise = np.abs(g.standard_normal(draws))
+    noise = g.standard_normal(draws)
     U0 = orthonormal(g, l, r[0])
     V0 = orthonormal(g, m, r[1])
     W0 = orthonormal(g, n, r[2])
@@ -362,3 +364,13 @@ def general_sampled_planted(seed: int, l: int, m: int, n: int, draws: int, r=(2,
     alpha = snr * ns / ss if ss > 0 else 0.0
     return GenCOO(l, m, n, i.astype(np.int32), j.astype(np.int32), k.astype(np.int32),
                   noise + alpha * sig)
+
+
+def general_noisy_planted(seed: int, dims=(40, 30, 12), r=(2, 2, 2), rho: float = 0.3):
+    """A dense general tensor: (U0,V0,W0).F0 of exact multilinear rank r
+    plus N(0,1) noise scaled to rho times its norm, as a COO of every
+    entry (a well-separated problem with a unique nearby optimum)."""
+    T, _, _, _, _ = general_dense_planted(seed, *dims, r)
+    g = rng(seed + 1000)
+    N = g.standard_normal(T.shape)
+    return general_dense_to_coo(T + rho * np.linalg.norm(T) / np.linalg.norm(N) * N)
