@@ -219,3 +219,23 @@ def test_zipf_workload_solve_checked_by_the_oracle():
     U, V, W, F, info = bk.bks_gen_solve(T, bk.BksGenParams(r1=3, r2=3, r3=3, tol=1e-9, seed=5))
     assert info["converged"]
     _check_at_point(A, *(x.cpu().numpy() for x in (U, V, W, F)), 1e-9)
+
+
+def test_bench_size_general_solve_checked_by_the_oracle():
+    """The benchmark's general workload (100,000 x 80,000 x 50, 5M draws,
+    rank (3,3,3), BK(2,4), ||grad||/||F||^2 <= 1e-9) from the benchmark's
+    start: the oracle's gradient and core at the returned point."""
+    bk = _bk()
+    c = synth.general_zipf_tensor(6, 100_000, 80_000, 50, 5_000_000, 1.1)
+    A, T = _pair(bk, c)
+    U0, V0, W0 = _starts(23, (A.l, A.m, A.n), (3, 3, 3))
+    U, V, W, F, info = bk.bks_gen_solve(
+        T, bk.BksGenParams(r1=3, r2=3, r3=3, tol=1e-9, tol_scale_free=1, max_outer=300),
+        _t(U0), _t(V0), _t(W0))
+    assert info["converged"]
+    Ug, Vg, Wg, Fg = (x.cpu().numpy() for x in (U, V, W, F))
+    for Q in (Ug, Vg, Wg):
+        assert np.abs(Q.T @ Q - np.eye(3)).max() < 1e-12
+    g, nf, Fo = O.gen_gradient_global(A, Ug, Vg, Wg)
+    assert g / nf ** 2 <= 2e-9
+    assert np.abs(Fg - Fo).max() <= 1e-10 * np.abs(Fo).max()
