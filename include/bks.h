@@ -475,11 +475,16 @@ typedef struct {
   int tol_scale_free;  /* 1: the test is ||grad|| / ||F||^2 <= tol */
   uint64_t seed;       /* random start when a start matrix is NULL */
   double drop_tol;     /* rank-drop threshold of the block QR (relative) */
-  double inner_tol;    /* inner tolerance; <= 0: the outer one */
+  double inner_tol;    /* inner tolerance; <= 0: set by inner_schedule */
+  int inner_schedule;  /* BKS_INNER_PAPER (default): the HOSVD start gets 5 HOOI sweeps and
+                          the sweeps continue to the outer tolerance; BKS_INNER_FAST: no start
+                          sweeps and the inexact tolerance max(tol / 10, ||grad|| / ||F|| / 100)
+                          at the current outer point (tol in ||grad|| / ||F|| units) */
 } bks_gen_params;
 
 /* Defaults: r = (2,2,2), s = 2, p = 4, tol 1e-10, max_outer 500,
- * max_inner 1000, BK, seed 1, drop_tol 1e-14, inner_tol 0. */
+ * max_inner 1000, BK, seed 1, drop_tol 1e-14, inner_tol 0,
+ * BKS_INNER_PAPER. */
 void bks_gen_params_default(bks_gen_params* p);
 
 /* bks_gen_solve: tensor Krylov-Schur for a general tensor (Algorithm 5).

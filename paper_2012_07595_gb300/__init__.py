@@ -85,7 +85,7 @@ class _GenParams(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("variant", ctypes.c_int), ("tol_scale_free", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("drop_tol", ctypes.c_double),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("inner_schedule", ctypes.c_int)]
 
 
 class _HooiParams(ctypes.Structure):
@@ -749,6 +749,7 @@ class BksGenParams:
     seed: int = 1
     drop_tol: float = 1e-14
     inner_tol: float = 0.0
+    inner_schedule: int = BKS_INNER_PAPER
 
     def to_c(self) -> _GenParams:
         p = _GenParams()

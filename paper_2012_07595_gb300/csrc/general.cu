@@ -210,12 +210,12 @@ struct GenState {
     return BKS_OK;
   }
 
-  int inner_and_restart(double itol) {
+  int inner_and_restart(double itol, int start_sweeps) {
     for (int md = 0; md < 3; ++md) last_k[md] = k[md];
     BKS_TRY(gen_core_x(t, Bp(0), dim[0], k[0], Bp(1), dim[1], k[1], Bp(2), dim[2], k[2],
                        C.as<double>(), s));
     BKS_TRY(gen_inner_solve(C.as<double>(), k[0], k[1], k[2], r[0], r[1], r[2], itol,
-                            P.max_inner, kGenStartSweeps, neg[0].as<double>(),
+                            P.max_inner, start_sweeps, neg[0].as<double>(),
                             neg[1].as<double>(), neg[2].as<double>(), inner_info.as<double>(), s));
     // U0 <- X Uh, V0 <- Y Vh, W0 <- Z Wh (eq. (tks1)), in place
     for (int md = 0; md < 3; ++md)
@@ -244,6 +244,8 @@ int check_gen_params(const bks_tensor* t, const bks_gen_params* p) {
     return fail(BKS_EINVAL, "stages >= 1 and 1 <= block_p <= 8 required");
   if (p->variant < BKS_VARIANT_BK || p->variant > BKS_VARIANT_MAX)
     return fail(BKS_EINVAL, "unknown variant");
+  if (p->inner_schedule != BKS_INNER_PAPER && p->inner_schedule != BKS_INNER_FAST)
+    return fail(BKS_EINVAL, "unknown inner schedule");
   return BKS_OK;
 }
 
@@ -266,6 +268,7 @@ extern "C" void bks_gen_params_default(bks_gen_params* p) {
   p->seed = 1;
   p->drop_tol = 1e-14;
   p->inner_tol = 0.0;
+  p->inner_schedule = BKS_INNER_PAPER;
 }
 
 extern "C" int bks_gen_solve(const bks_tensor* t, const bks_gen_params* prm, const double* U0,
@@ -306,8 +309,14 @@ extern "C" int bks_gen_solve(const bks_tensor* t, const bks_gen_params* prm, con
     }
     if (it >= prm->max_outer) break;
     BKS_TRY(S.expand_rest());
+    // inner tolerance on ||grad_C|| / ||F_C||: the outer one (Section 6.2),
+    // or with BKS_INNER_FAST an inexact one a hundred times below the
+    // current outer gradient and at least a tenth of the outer tolerance
     const double otol = prm->tol_scale_free ? prm->tol * nf : prm->tol;
-    BKS_TRY(S.inner_and_restart(prm->inner_tol > 0 ? prm->inner_tol : otol));
+    const bool fast = prm->inner_schedule == BKS_INNER_FAST;
+    const double itol = prm->inner_tol > 0 ? prm->inner_tol
+                        : fast ? std::max(0.1 * otol, 0.01 * (nf > 0 ? grad / nf : 0.0)) : otol;
+    BKS_TRY(S.inner_and_restart(itol, fast ? 0 : kGenStartSweeps));
   }
   // outputs: the point whose gradient was evaluated last
   double* outs[3] = {U, V, W};

@@ -166,6 +166,23 @@ def test_solve_parity_planted_sparse(variant):
     assert info["iters"] == ref.iters
 
 
+def test_fast_inner_schedule_reaches_the_oracle_optimum():
+    """BKS_INNER_FAST (no start sweeps, inexact inner tolerance) against the
+    oracle on the Section 6.2 schedule: the same optimum."""
+    bk = _bk()
+    c = synth.general_noisy_planted(32, (50, 40, 15), (3, 2, 2), 0.5)
+    A, T = _pair(bk, c)
+    U0, V0, W0 = _starts(33, (50, 40, 15), (3, 2, 2))
+    ref = O.gen_bks(A, U0, V0, W0, s=2, p=2, tol=1e-10)
+    U, V, W, F, info = bk.bks_gen_solve(
+        T, bk.BksGenParams(r1=3, r2=2, r3=2, block_p=2, tol=1e-10,
+                           inner_schedule=bk.BKS_INNER_FAST), _t(U0), _t(V0), _t(W0))
+    assert ref.converged and info["converged"]
+    assert abs(info["normF"] - ref.normF) <= 1e-10 * ref.normF
+    for X, Y in ((ref.U, U), (ref.V, V), (ref.W, W)):
+        assert O.sin_theta_max(X, Y.cpu().numpy()) < 1e-8
+
+
 def test_planted_exact_rank_and_matrix_case():
     bk = _bk()
     T0, Ut, Vt, Wt, F0 = synth.general_dense_planted(23, 26, 19, 9, (2, 3, 2))
