@@ -528,6 +528,22 @@ def ncu_case(args):
     import paper_2012_07595_gb300 as bk
     from paper_2012_07595_gb300 import _build
     _build.build()
+    if args.ncu_case == "general":
+        # the general workload's solve on the fast inner schedule, twice
+        G = GENERAL
+        c = synth.general_zipf_tensor(G["seed"], G["l"], G["m"], G["n"], G["draws"], G["zipf_s"])
+        T = bk.bks_gen_tensor_create_coo(c.l, c.m, c.n, c.i, c.j, c.k, c.v)
+        gs = synth.rng(23)
+        starts = [torch.tensor(synth.orthonormal(gs, d, G["r"]), device="cuda")
+                  for d in (c.l, c.m, c.n)]
+        prm = bk.BksGenParams(r1=G["r"], r2=G["r"], r3=G["r"], stages=2, block_p=4, tol=1e-9,
+                              tol_scale_free=1, max_outer=300, inner_schedule=bk.BKS_INNER_FAST)
+        for rep in range(2):
+            c0 = bk.bks_launch_count()
+            bk.bks_gen_solve(T, prm, *starts)
+            torch.cuda.synchronize()
+            print(f"general solve {rep}: {bk.bks_launch_count() - c0} launches")
+        return
     if args.size == "large":
         L = LARGE
         coo = synth.zipf_tensor(L["seed"], L["m"], L["n"], L["draws"], L["zipf_s"],
@@ -726,7 +742,7 @@ def main():
                     help="serve the first D jobs of the stream in turn (0: every request its own)")
     ap.add_argument("--ncu-case", default=None,
                     help="profiling entry: build the workload, run a few launches of one "
-                         "kernel family (mode1, mode3, core, solve) and exit without a JSON line")
+                         "kernel family (mode1, mode3, core), or a solve (solve; general: the general-tensor solve) and exit without a JSON line")
     ap.add_argument("--size", default="medium", choices=["medium", "mid", "large"],
                     help="ncu-case workload: medium = 1e5 x 1e5 x 50 (5M stored), "
                          "mid = 5e5 x 5e5 x 200 (11.8M stored), large = 1e6 x 1e6 x 200 "
