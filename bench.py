@@ -731,15 +731,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch-scale", type=float, default=0.25,
+    ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="size scale of the batched/serving jobs (1.0 = m up to 2e5 and "
                          "up to 5M stored entries per job); 0 skips them")
     ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--serve-sweep-requests", type=int, default=None,
-                    help="requests per point of the offered-rate sweep (default: --serve-requests)")
-    ap.add_argument("--serve-distinct", type=int, default=0,
-                    help="serve the first D jobs of the stream in turn (0: every request its own)")
+    ap.add_argument("--serve-sweep-requests", type=int, default=100,
+                    help="requests per point of the offered-rate sweep")
+    ap.add_argument("--serve-distinct", type=int, default=32,
+                    help="serve the first D jobs of the stream in turn (0: every request its "
+                         "own; full-size tensors take long to draw on the host)")
     ap.add_argument("--ncu-case", default=None,
                     help="profiling entry: build the workload, run a few launches of one "
                          "kernel family (mode1, mode3, core), or a solve (solve; general: the general-tensor solve) and exit without a JSON line")
