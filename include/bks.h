@@ -503,6 +503,27 @@ int bks_gen_solve(const bks_tensor* t, const bks_gen_params* prm, const double* 
                   const double* V0, const double* W0, double* U, double* V, double* W,
                   double* F, bks_info* info, void* stream);
 
+typedef struct {
+  int r1, r2, r3;      /* target multilinear rank, each 1..8, pairwise products <= 32 */
+  double tol;          /* stop when ||grad|| / ||F|| <= tol */
+  int max_iter;        /* iteration cap (BKS_ENOTCONV past it) */
+  int grad_every;      /* gradient test cadence (Section 6.1: every 10) */
+  uint64_t seed;       /* random start when a start matrix is NULL */
+} bks_gen_hooi_params;
+
+/* Defaults: r = (2,2,2), tol 1e-10, max_iter 5000, grad_every 10, seed 1. */
+void bks_gen_hooi_params_default(bks_gen_hooi_params* p);
+
+/* bks_gen_hooi_solve: HOOI for a general tensor (Section 6.1): U from the
+ * r1 leading left singular vectors of unfold_1(A.(V,W)_{2,3}), then V from
+ * unfold_2(A.(U,W)_{1,3}) with the new U, then W from unfold_3(A.(U,V)_{1,2})
+ * with the new U and V; the G-gradient in global coordinates (three terms)
+ * every grad_every iterations at the start of the iteration.  FP64.  Same
+ * buffers, info fields and errors as bks_gen_solve (k1, k2, k3 = r). */
+int bks_gen_hooi_solve(const bks_tensor* t, const bks_gen_hooi_params* prm, const double* U0,
+                       const double* V0, const double* W0, double* U, double* V, double* W,
+                       double* F, bks_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

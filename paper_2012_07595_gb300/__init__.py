@@ -29,7 +29,7 @@ __all__ = [
     "BKS_EBUDGET", "BKS_NORM_FRO", "BKS_NORM_LMAX", "bks_s_values", "bks_slice_norms",
     "bks_tensor_scale_slices", "BKS_INNER_PAPER", "BKS_INNER_FAST", "bks_contract_mode1_noalloc",
     "bks_gen_tensor_create_coo", "bks_gen_tensor_dims", "bks_gen_contract", "bks_gen_core",
-    "BksGenParams", "bks_gen_solve",
+    "BksGenParams", "bks_gen_solve", "BksGenHooiParams", "bks_gen_hooi_solve",
 ]
 
 BKS_OK = 0
@@ -86,6 +86,12 @@ class _GenParams(ctypes.Structure):
                 ("variant", ctypes.c_int), ("tol_scale_free", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("drop_tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("inner_schedule", ctypes.c_int)]
+
+
+class _GenHooiParams(ctypes.Structure):
+    _fields_ = [("r1", ctypes.c_int), ("r2", ctypes.c_int), ("r3", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("grad_every", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 class _HooiParams(ctypes.Structure):
@@ -191,6 +197,11 @@ def lib():
     L.bks_gen_solve.argtypes = [vp, ctypes.POINTER(_GenParams), vp, vp, vp, vp, vp, vp, vp,
                                 ctypes.POINTER(_Info), vp]
     L.bks_gen_solve.restype = c_int
+    L.bks_gen_hooi_params_default.argtypes = [ctypes.POINTER(_GenHooiParams)]
+    L.bks_gen_hooi_params_default.restype = None
+    L.bks_gen_hooi_solve.argtypes = [vp, ctypes.POINTER(_GenHooiParams), vp, vp, vp, vp, vp, vp,
+                                     vp, ctypes.POINTER(_Info), vp]
+    L.bks_gen_hooi_solve.restype = c_int
     L.bks_launch_count.argtypes = []
     L.bks_launch_count.restype = ctypes.c_uint64
     L.bks_last_error_string.argtypes = []
@@ -758,13 +769,43 @@ class BksGenParams:
         return p
 
 
+@dataclasses.dataclass
+class BksGenHooiParams:
+    r1: int = 2
+    r2: int = 2
+    r3: int = 2
+    tol: float = 1e-10
+    max_iter: int = 5000
+    grad_every: int = 10
+    seed: int = 1
+
+    def to_c(self) -> _GenHooiParams:
+        p = _GenHooiParams()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
 def bks_gen_solve(t: Tensor, params: Optional[BksGenParams] = None, U0=None, V0=None, W0=None,
                   stream=None, history_cap: int = 1000, raise_notconv: bool = False):
     """Tensor Krylov-Schur for a general tensor (Algorithm 5, Section 5).
     Returns (U, V, W, F, info): U l x r1, V m x r2, W n x r3 FP64 CUDA
     tensors and F r1 x r2 x r3."""
+    return _gen_solve(lib().bks_gen_solve, t, params or BksGenParams(), U0, V0, W0, stream,
+                      history_cap, raise_notconv)
+
+
+def bks_gen_hooi_solve(t: Tensor, params: Optional[BksGenHooiParams] = None, U0=None, V0=None,
+                       W0=None, stream=None, history_cap: int = 1000,
+                       raise_notconv: bool = False):
+    """HOOI for a general tensor (Section 6.1).  Returns (U, V, W, F, info)
+    as bks_gen_solve."""
+    return _gen_solve(lib().bks_gen_hooi_solve, t, params or BksGenHooiParams(), U0, V0, W0,
+                      stream, history_cap, raise_notconv)
+
+
+def _gen_solve(fn, t: Tensor, prm, U0, V0, W0, stream, history_cap, raise_notconv):
     import torch
-    prm = params or BksGenParams()
     r = (prm.r1, prm.r2, prm.r3)
     dims = (t.l, t.m, t.n)
     outs = [_empty_cm(dims[q], r[q], torch.float64, "cuda") for q in range(3)]
@@ -776,10 +817,10 @@ def bks_gen_solve(t: Tensor, params: Optional[BksGenParams] = None, U0=None, V0=
     starts = [x.to(device="cuda", dtype=torch.float64).t().contiguous().t() if x is not None
               else None for x in (U0, V0, W0)]
     cp = prm.to_c()
-    rc = lib().bks_gen_solve(t.handle, ctypes.byref(cp),
-                             *[ctypes.c_void_p(x.data_ptr() if x is not None else 0) for x in starts],
-                             *[ctypes.c_void_p(x.data_ptr()) for x in outs],
-                             ctypes.c_void_p(F.data_ptr()), ctypes.byref(info), _stream(stream))
+    rc = fn(t.handle, ctypes.byref(cp),
+            *[ctypes.c_void_p(x.data_ptr() if x is not None else 0) for x in starts],
+            *[ctypes.c_void_p(x.data_ptr()) for x in outs],
+            ctypes.c_void_p(F.data_ptr()), ctypes.byref(info), _stream(stream))
     _check(rc, allow=() if raise_notconv else (BKS_ENOTCONV,))
     out = {"iters": info.iters, "converged": bool(info.converged), "grad_rel": info.grad_rel,
            "normF": info.normF, "k1": info.k1, "k2": info.k2, "k3": info.k3,

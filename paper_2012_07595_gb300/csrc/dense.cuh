@@ -52,6 +52,11 @@ int ts_combine(const double* Q, int64_t ldq, int K, const double* B, int64_t ldb
                const double* Mq, const double* Mb, int bo, double* Out, int64_t ldo, int64_t m,
                DenseWork& ws, cudaStream_t s);
 
+// Out = B Mb - Q Mq (as ts_combine) and G ((K+bo) x bo) = [Q Out]^T Out.
+int ts_combine_gram(const double* Q, int64_t ldq, int K, const double* B, int64_t ldb, int b,
+                    const double* Mq, const double* Mb, int bo, double* Out, int64_t ldo,
+                    int64_t m, double* G, DenseWork& ws, cudaStream_t s);
+
 // G ((K+b) x b, ld K+b) = [Q B]^T B: rows 0..K-1 hold Q^T B, the rest B^T B.
 int ts_gram(const double* Q, int64_t ldq, int K, const double* B, int64_t ldb, int b,
             int64_t m, double* G, DenseWork& ws, cudaStream_t s);

@@ -18,6 +18,7 @@
 #include <chrono>
 #include <cmath>
 #include <set>
+#include <vector>
 
 #include "dense.cuh"
 
@@ -249,10 +250,176 @@ int check_gen_params(const bks_tensor* t, const bks_gen_params* p) {
   return BKS_OK;
 }
 
+// From G = [Q T]^T T ((K + w) x w, F = Q^T T its first K rows): FT = F^T
+// (w x K), FF = F F^T (K x K) and nf2 = ||F||^2.
+__global__ void k_gh_small(const double* __restrict__ G, int K, int w, double* __restrict__ FT,
+                           double* __restrict__ FF, double* __restrict__ nf2) {
+  const int gw = K + w;
+  for (int x = threadIdx.x; x < w * K; x += blockDim.x) {
+    const int j = x % w, a = x / w;
+    FT[j + w * a] = G[a + gw * j];
+  }
+  for (int x = threadIdx.x; x < K * K; x += blockDim.x) {
+    const int a = x % K, b = x / K;
+    double s = 0.0;
+    for (int j = 0; j < w; ++j) s = fma(G[a + gw * j], G[b + gw * j], s);
+    FF[x] = s;
+  }
+  if (threadIdx.x == 0 && nf2) {
+    double s = 0.0;
+    for (int a = 0; a < K; ++a)
+      for (int j = 0; j < w; ++j) s = fma(G[a + gw * j], G[a + gw * j], s);
+    *nf2 = s;
+  }
+}
+// out = trace of the lower g x g block of G ((K + g) x g): ||Out||^2 after
+// ts_combine_gram
+__global__ void k_gh_trace(const double* __restrict__ G, int K, int g, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int j = 0; j < g; ++j) s += G[K + j + (int64_t)(K + g) * j];
+    *out = s;
+  }
+}
+
 }  // namespace
 }  // namespace bks
 
 using namespace bks;
+
+extern "C" void bks_gen_hooi_params_default(bks_gen_hooi_params* p) {
+  if (!p) return;
+  *p = bks_gen_hooi_params{};
+  p->r1 = p->r2 = p->r3 = 2;
+  p->tol = 1e-10;
+  p->max_iter = 5000;
+  p->grad_every = 10;
+  p->seed = 1;
+}
+
+// HOOI for a general tensor (Section 6.1): U from the r1 leading left
+// singular vectors of unfold_1(A.(V,W)_{2,3}), then V from
+// unfold_2(A.(U,W)_{1,3}) with the new U, then W from unfold_3(A.(U,V)_{1,2})
+// with the new U and V.  The G-gradient in global coordinates (three terms
+// (I - Q Q^T) T F^T) every grad_every iterations, at the start of the
+// iteration.  FP64.
+extern "C" int bks_gen_hooi_solve(const bks_tensor* t, const bks_gen_hooi_params* prm,
+                                  const double* U0, const double* V0, const double* W0,
+                                  double* U, double* V, double* W, double* F, bks_info* info,
+                                  void* stream) {
+  if (!t || !prm) return fail(BKS_EINVAL, "null tensor or params");
+  BKS_TRY(require_general(t));
+  if (!U || !V || !W || !F) return fail(BKS_EINVAL, "null output");
+  const int r[3] = {prm->r1, prm->r2, prm->r3};
+  const int64_t d[3] = {t->l, t->m, t->n};
+  for (int md = 0; md < 3; ++md) {
+    if (r[md] < 1 || r[md] > 8) return fail(BKS_EUNSUPPORTED, "ranks must be in 1..8");
+    if (r[md] > d[md]) return fail(BKS_EINVAL, "rank larger than the dimension");
+  }
+  const int w[3] = {r[1] * r[2], r[0] * r[2], r[0] * r[1]};
+  for (int md = 0; md < 3; ++md)
+    if (w[md] > kGenBlockMax) return fail(BKS_EUNSUPPORTED, "products of two ranks must be <= 32");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  DenseWork ws;
+  DevBuf Qb[3], Tb[3], gout[3], G, FT, FF, sc;
+  for (int md = 0; md < 3; ++md) {
+    BKS_TRY(Qb[md].alloc(sizeof(double) * (size_t)d[md] * r[md], s));
+    BKS_TRY(Tb[md].alloc(sizeof(double) * (size_t)d[md] * w[md], s));
+    BKS_TRY(gout[md].alloc(sizeof(double) * (size_t)d[md] * r[md], s));
+  }
+  BKS_TRY(G.alloc(sizeof(double) * (kGenBlockMax + 8) * kGenBlockMax, s));
+  BKS_TRY(FT.alloc(sizeof(double) * 3 * kGenBlockMax * 8, s));
+  BKS_TRY(FF.alloc(sizeof(double) * 3 * 64, s));
+  BKS_TRY(sc.alloc(sizeof(double) * 8, s));
+  const double* starts[3] = {U0, V0, W0};
+  for (int md = 0; md < 3; ++md) {
+    if (starts[md]) BKS_TRY(gcopy2d(starts[md], d[md], d[md], r[md], Qb[md].as<double>(), d[md], s));
+    else BKS_TRY(random_orthonormal(prm->seed, (uint64_t)(md + 1), d[md], r[md], Qb[md].as<double>(), ws, s));
+  }
+  double* Q[3] = {Qb[0].as<double>(), Qb[1].as<double>(), Qb[2].as<double>()};
+  double* T[3] = {Tb[0].as<double>(), Tb[1].as<double>(), Tb[2].as<double>()};
+  static const int oth[3][2] = {{1, 2}, {0, 2}, {0, 1}};
+  auto contract = [&](int md) -> int {
+    const int oa = oth[md][0], ob = oth[md][1];
+    return gen_contract_x(t, md + 1, Q[oa], d[oa], r[oa], Q[ob], d[ob], r[ob], T[md], d[md], s);
+  };
+  const int every = std::max(1, prm->grad_every);
+  int it = 0, hist_len = 0;
+  double grad = INFINITY, nf = 0;
+  bool converged = false;
+  for (;; ++it) {
+    BKS_TRY(contract(0));
+    if (it % every == 0 || it >= prm->max_iter) {
+      // the gradient at (U, V, W): T2, T3 at the same point
+      BKS_TRY(contract(1));
+      BKS_TRY(contract(2));
+      BKS_CUDA_TRY(cudaMemsetAsync(sc.p, 0, sizeof(double) * 4, s));
+      for (int md = 0; md < 3; ++md) {
+        double* ft = FT.as<double>() + md * kGenBlockMax * 8;
+        double* ff = FF.as<double>() + md * 64;
+        BKS_TRY(ts_gram(Q[md], d[md], r[md], T[md], d[md], w[md], d[md], G.as<double>(), ws, s));
+        k_gh_small<<<1, 128, 0, s>>>(G.as<double>(), r[md], w[md], ft, ff,
+                                     md == 0 ? sc.as<double>() + 3 : nullptr); ::bks::note_launch();
+        BKS_TRY(ts_combine_gram(Q[md], d[md], r[md], T[md], d[md], w[md], ff, ft, r[md],
+                                gout[md].as<double>(), d[md], d[md], G.as<double>(), ws, s));
+        k_gh_trace<<<1, 32, 0, s>>>(G.as<double>(), r[md], r[md], sc.as<double>() + md); ::bks::note_launch();
+        BKS_CUDA_TRY(cudaGetLastError());
+      }
+      double h[4];
+      BKS_CUDA_TRY(cudaMemcpyAsync(h, sc.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+      BKS_CUDA_TRY(cudaStreamSynchronize(s));
+      grad = std::sqrt(std::max(0.0, h[0] + h[1] + h[2]));
+      nf = std::sqrt(std::max(0.0, h[3]));
+      const double rel = nf > 0 ? grad / nf : INFINITY;
+      if (info && info->history && hist_len < info->history_cap) {
+        info->history[2 * hist_len] = rel;
+        info->history[2 * hist_len + 1] = nf;
+        ++hist_len;
+      }
+      if (!std::isfinite(grad)) return fail(BKS_ENUMERIC, "NaN or Inf in the gradient");
+      if (rel <= prm->tol) { converged = true; break; }
+      if (it >= prm->max_iter) break;
+    }
+    // U from T1 (at V, W); V from T2 at the new U; W from T3 at the new U, V
+    BKS_TRY(top_left_singular(T[0], d[0], d[0], w[0], r[0], Q[0], d[0], ws, s));
+    BKS_TRY(contract(1));
+    BKS_TRY(top_left_singular(T[1], d[1], d[1], w[1], r[1], Q[1], d[1], ws, s));
+    BKS_TRY(contract(2));
+    BKS_TRY(top_left_singular(T[2], d[2], d[2], w[2], r[2], Q[2], d[2], ws, s));
+  }
+  // F = U^T T1 at the evaluated point: FT of mode 1 holds F^T (w1 x r1)
+  {
+    const double* ft = FT.as<double>();
+    // unfold_1(F) = (F^T)^T: r1 x w1, F[a + r1 (b + r2 c)]
+    std::vector<double> h((size_t)w[0] * r[0]);
+    BKS_CUDA_TRY(cudaMemcpyAsync(h.data(), ft, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    BKS_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<double> f(h.size());
+    for (int a = 0; a < r[0]; ++a)
+      for (int j = 0; j < w[0]; ++j) f[a + (size_t)r[0] * j] = h[j + (size_t)w[0] * a];
+    BKS_CUDA_TRY(cudaMemcpyAsync(F, f.data(), sizeof(double) * f.size(), cudaMemcpyHostToDevice, s));
+  }
+  double* outs[3] = {U, V, W};
+  for (int md = 0; md < 3; ++md) BKS_TRY(gcopy2d(Q[md], d[md], d[md], r[md], outs[md], d[md], s));
+  BKS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = it;
+    info->converged = converged ? 1 : 0;
+    info->grad_rel = nf > 0 ? grad / nf : INFINITY;
+    info->normF = nf;
+    info->k1 = r[0];
+    info->k2 = r[1];
+    info->k3 = r[2];
+    info->inner_sweeps = 0;
+    info->fp32_iters = 0;
+    info->history_len = hist_len;
+    for (int q = 0; q < 5; ++q) info->phase_ms[q] = 0.0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (!converged) return fail(BKS_ENOTCONV, "HOOI not converged within max_iter");
+  return BKS_OK;
+}
 
 extern "C" void bks_gen_params_default(bks_gen_params* p) {
   if (!p) return;

@@ -183,6 +183,31 @@ def test_fast_inner_schedule_reaches_the_oracle_optimum():
         assert O.sin_theta_max(X, Y.cpu().numpy()) < 1e-8
 
 
+def test_hooi_parity_and_agreement_with_bks():
+    """General HOOI on the GPU against the oracle's (same start, same
+    iteration count at the 10-iteration gradient cadence, same optimum),
+    and the BKS optimum on the same tensor."""
+    bk = _bk()
+    c = synth.general_noisy_planted(34, (45, 35, 14), (2, 3, 2), 0.4)
+    A, T = _pair(bk, c)
+    U0, V0, W0 = _starts(35, (45, 35, 14), (2, 3, 2))
+    U, V, W, F, info = bk.bks_gen_hooi_solve(T, bk.BksGenHooiParams(r1=2, r2=3, r3=2, tol=1e-10),
+                                             _t(U0), _t(V0), _t(W0))
+    ref = O.gen_hooi(A, U0, V0, W0, tol=1e-10)
+    assert info["converged"] and ref.converged
+    assert info["iters"] == ref.iters
+    assert abs(info["normF"] - ref.normF) <= 1e-10 * ref.normF
+    Ug, Vg, Wg, Fg = (x.cpu().numpy() for x in (U, V, W, F))
+    for X, Y in ((ref.U, Ug), (ref.V, Vg), (ref.W, Wg)):
+        assert O.sin_theta_max(X, Y) < 1e-8
+    _check_at_point(A, Ug, Vg, Wg, Fg, 1e-10)
+    Ub, Vb, Wb, Fb, ib = bk.bks_gen_solve(T, bk.BksGenParams(r1=2, r2=3, r3=2, block_p=2, tol=1e-10),
+                                          _t(U0), _t(V0), _t(W0))
+    assert ib["converged"] and abs(ib["normF"] - info["normF"]) <= 1e-10 * info["normF"]
+    for X, Y in ((Ub, U), (Vb, V), (Wb, W)):
+        assert O.sin_theta_max(X.cpu().numpy(), Y.cpu().numpy()) < 1e-7
+
+
 def test_planted_exact_rank_and_matrix_case():
     bk = _bk()
     T0, Ut, Vt, Wt, F0 = synth.general_dense_planted(23, 26, 19, 9, (2, 3, 2))
