@@ -851,6 +851,30 @@ def main():
         paper[nm]["subspace_sin_vs_ref"] = max(
             float(np.linalg.norm(Up - Uref @ (Uref.T @ Up), 2)),
             float(np.linalg.norm(Wp - Wref @ (Wref.T @ Wp), 2)))
+    # ---- HOOI (Section 6.1) from the same start to the same scale-free
+    # tolerance (its test is ||grad||/||F|| <= tol: tol = 1e-9 ||F||) ----
+    hooi = {}
+    nf_ref = inf64[-1]["normF"]
+    for nm, prec in (("mixed", bk.BKS_PREC_MIXED), ("fp64", bk.BKS_PREC_FP64)):
+        hp = bk.HooiParams(r1=w["r"], r3=w["r"], tol=w["tol"] * nf_ref, max_iter=20000,
+                           precision=prec)
+        hl = []
+        for rep in range(2):
+            flush.fill_(float(rep))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            Uh, Wh, _, hinfo = bk.hooi_solve(T, hp, U0, W0, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            hl.append(e0.elapsed_time(e1) / 1e3)
+        Uh, Wh = Uh.cpu().numpy(), Wh.cpu().numpy()
+        hooi[nm] = {"solves_per_s": 1.0 / hl[-1], "iters": hinfo["iters"],
+                    "converged": hinfo["converged"], "normF": hinfo["normF"],
+                    "subspace_sin_vs_ref": max(
+                        float(np.linalg.norm(Uh - Uref @ (Uref.T @ Uh), 2)),
+                        float(np.linalg.norm(Wh - Wref @ (Wref.T @ Wh), 2)))}
     # subspace agreement mixed vs FP64: sin of the largest principal angle
     def sin_max(A, B):
         D = B - A @ (A.T @ B)
@@ -955,6 +979,7 @@ def main():
         "grad_rel": {"mixed": inf_mixed[-1]["grad_rel"], "fp64": inf64[-1]["grad_rel"]},
         "phase_ms": {"mixed": inf_mixed[-1]["phase_ms"], "fp64": inf64[-1]["phase_ms"]},
         "paper_inner_schedule": paper,
+        "hooi_same_tol": hooi,
         "roofline": roofline,
         "roofline_workload": roofline_workload,
         "large_workload": {"workload": roofline["workload"], "kernels": large_kernels,
