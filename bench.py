@@ -294,10 +294,12 @@ def cpu_baseline_leg(coo, nnz_full, gpu_fp64_iters):
 
 
 # ---------------------------------------------------------------------------
-# DRAM bytes (read + write) of k_contract<float,float,4,4,0,1> in one ncu
-# capture of the 500,000 x 500,000 x 200 case (`--ncu-case mode1 --size mid`)
-MID_TRAFFIC_BYTES = 184_253_952 + 27_801_856
-MID_NNZ = 11_777_770
+# DRAM bytes (read + write) of one k_contract<float,float,4,4,0,1> launch on
+# the 48.5M-entry tensor of `large_workload`, the roofline call's own kernel
+# and size (`--ncu-case mode1 --size large`, dram__bytes_read.sum +
+# dram__bytes_write.sum, a one-pass capture)
+LARGE_TRAFFIC_BYTES = 691_628_032 + 80_291_584
+LARGE_TRAFFIC_NNZ = 48_545_500
 LARGE = {"m": 1_000_000, "n": 200, "draws": 60_000_000, "zipf_s": 1.2, "seed": 3, "r": 5}
 
 
@@ -346,8 +348,7 @@ def large_workload(bk, torch, stream, flush, hbm, peak_kind):
     kernel, the piece reduction of long rows and the zero rows; algorithmic
     bytes = index and value streams + row pointers + operands read once +
     output written once (gathers served by L2 not counted).  `traffic`: DRAM
-    bytes of k_contract from an ncu capture of the 500,000 x 500,000 x 200
-    case (same kernel), scaled to this launch by stored entries."""
+    bytes of one k_contract launch on this tensor from an ncu capture."""
     L = LARGE
     coo = synth.zipf_tensor(L["seed"], L["m"], L["n"], L["draws"], L["zipf_s"],
                             values="absnormal", vdtype=np.float32)
@@ -392,9 +393,10 @@ def large_workload(bk, torch, stream, flush, hbm, peak_kind):
                             f"({L['draws']} draws mirrored, duplicates summed), X 4 cols, Y 4 cols",
                 "bound": "hbm", "achieved": r44["GB_per_s"], "peak": hbm, "unit": "GB/s",
                 "frac": r44["frac"], "peak_kind": peak_kind,
-                "traffic": int(MID_TRAFFIC_BYTES * nnz / MID_NNZ),
-                "traffic_note": "ncu dram bytes of k_contract<float,float,4,4,0,1> on the 11.8M-entry "
-                                "case, scaled by stored entries",
+                "traffic": LARGE_TRAFFIC_BYTES if nnz == LARGE_TRAFFIC_NNZ else None,
+                "traffic_note": "ncu dram bytes (read + write) of one k_contract<float,float,4,4,0,1> "
+                                "launch on this tensor (one-pass capture); the pack and the piece "
+                                "reduction of the timed call are not included",
                 "alg_bytes_per_launch": r44["alg_bytes"], "median_launch_s": r44["us"] * 1e-6,
                 "nnz_stored": nnz}
     kernels = [mode1(5, 5), mode1(5, 4), mode1(4, 5), mode3(5, None), mode3(5, 4)]
@@ -565,7 +567,9 @@ def ncu_case(args):
         L = LARGE
         coo = synth.zipf_tensor(L["seed"], L["m"], L["n"], L["draws"], L["zipf_s"],
                                 values="absnormal", vdtype=np.float32)
-        r, p = L["r"], 4
+        # mode 1 at the roofline shape (X and Y with 4 columns); the other
+        # cases at the solve's rank
+        r, p = (4 if args.ncu_case == "mode1" else L["r"]), 4
     elif args.size == "mid":
         coo = synth.zipf_tensor(3, 500_000, 200, 12_000_000, 1.2, values="absnormal",
                                 vdtype=np.float32)

@@ -29,8 +29,10 @@
  *
  * Limits: 2*ceil(log2 m) + ceil(log2 n) <= 64 bits (the ingest sort key),
  * at most 2^31 - 1024 entries after mirroring (input plus mirrors, before
- * duplicates are summed), contraction widths p, q <= 8 per call for the
- * mode-1 and mode-3 contractions.
+ * duplicates are summed).  The contraction kernels take widths up to 8;
+ * wider operands of bks_contract_mode1 / mode3 are cut into chunks of at
+ * most 8 columns of X per column of the second operand (one tensor pass
+ * each).
  */
 #ifndef BKS_GB300_H
 #define BKS_GB300_H
@@ -119,7 +121,11 @@ int bks_tensor_export_coo(const bks_tensor* t, int32_t* i, int32_t* j,
  * bks_contract_mode1: out = unfold_1(A.(X,Y)_{2,3}),
  *     out[i + ldo*(a + p*b)] = sum over stored (i,j,k) of v X[j,a] Y[k,b]
  *   X: m x p (ldx), Y: n x q (ldy), out: m x (p*q) (ldo); dtype-typed;
- *   1 <= p, q <= 8.  `out` is overwritten (rows without entries get 0).
+ *   p, q >= 1.  Up to p = 8 one pass over the tensor per group of at most
+ *   8 (p <= 4), 5 (p = 5) or 4 (p > 5) columns of Y; above p = 8 one pass
+ *   per column of Y and chunk of at most 8 columns of X, each chunk summed
+ *   as a p <= 8 call would.  `out` is overwritten (rows without entries
+ *   get 0).
  *   dtype BKS_F64 computes in FP64; BKS_F32 computes in FP32 with FP32
  *   accumulation (blocked summation: short sequential runs combined by a
  *   fixed-order tree). Deterministic: the same call gives the same bits. */
@@ -164,7 +170,10 @@ int bks_contract_mode1_noalloc(const bks_tensor* t, const void* X, int64_t ldx,
  *   X2 == NULL: the (1,2)-symmetric case X2 = X stored as triunfold_3
  *     (Section 4.3.1): out[k + ldo*(a + b(b+1)/2)] for a <= b; out is
  *     n x p(p+1)/2.
- *   1 <= p, q <= 8; dtype-typed; out overwritten; deterministic. */
+ *   p, q >= 1; above p = 8 the columns are computed as full products of
+ *   chunks of at most 8 columns of X with one column of X2 (or of X, a <= b,
+ *   in the triangle case), one tensor pass each.  dtype-typed; out
+ *   overwritten; deterministic. */
 int bks_contract_mode3(const bks_tensor* t, const void* X, int64_t ldx, int p,
                        const void* X2, int64_t ldx2, int q, void* out,
                        int64_t ldo, int dtype, void* stream);

@@ -41,12 +41,48 @@ namespace bks {
 namespace {
 
 // ---- pack a column-major m x p block into row-major m x PB (zero padded)
+// Rows whose packed width is a multiple of 16 bytes (and a 16-byte aligned
+// destination) are written with 16-byte stores.
+template <typename IT, typename T>
+__device__ __forceinline__ void pack_row(const IT* __restrict__ X, int64_t ldx, int64_t r, int p,
+                                         int PB, T* __restrict__ out, bool vec) {
+  constexpr int V = (int)(16 / sizeof(T));
+  if (vec) {
+    for (int a0 = 0; a0 < PB; a0 += V) {
+      union { T v[V]; uint4 q; } u;
+#pragma unroll
+      for (int t = 0; t < V; ++t) u.v[t] = a0 + t < p ? (T)X[r + ldx * (a0 + t)] : T(0);
+      reinterpret_cast<uint4*>(out + r * PB + a0)[0] = u.q;
+    }
+  } else {
+    for (int a = 0; a < PB; ++a) out[r * PB + a] = a < p ? (T)X[r + ldx * a] : T(0);
+  }
+}
+template <typename T>
+__device__ __forceinline__ bool vec_ok(int PB, const T* out) {
+  return (PB % (int)(16 / sizeof(T))) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+}
+
 template <typename IT, typename T>
 __global__ void k_pack(const IT* __restrict__ X, int64_t ldx, int64_t rows, int p, int PB,
                        T* __restrict__ out) {
+  const bool vec = vec_ok(PB, out);
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x)
+    pack_row(X, ldx, r, p, PB, out, vec);
+}
+
+// Both operands of a contraction in one launch: rows [0, rows1) of the
+// first, then the rows of the second.
+template <typename IT, typename T>
+__global__ void k_pack2(const IT* __restrict__ X, int64_t ldx, int64_t rows1, int p, int PB,
+                        T* __restrict__ out1, const IT* __restrict__ Y, int64_t ldy,
+                        int64_t rows2, int q, int QB, T* __restrict__ out2) {
+  const bool vec1 = vec_ok(PB, out1), vec2 = vec_ok(QB, out2);
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows1 + rows2;
        r += (int64_t)gridDim.x * blockDim.x) {
-    for (int a = 0; a < PB; ++a) out[r * PB + a] = a < p ? (T)X[r + ldx * a] : T(0);
+    if (r < rows1) pack_row(X, ldx, r, p, PB, out1, vec1);
+    else pack_row(Y, ldy, r - rows1, q, QB, out2, vec2);
   }
 }
 
@@ -126,13 +162,21 @@ int mode1_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
   T* Xp = reinterpret_cast<T*>(base);
   T* Yp = reinterpret_cast<T*>(base + xb);
   T* part = t->m1.nslots > 0 ? reinterpret_cast<T*>(base + xb + yb) : nullptr;
-  BKS_TRY((pack_into<T, IT>(X, ldx, t->m, p, row_stride<T>(PB), Xp, s)));
+  if (q <= qchunk) {  // one chunk of Y columns: both packs in one launch
+    k_pack2<IT, T><<<grid_for(t->m + t->n), 256, 0, s>>>(X, ldx, t->m, p, row_stride<T>(PB), Xp,
+                                                         Y, ldy, t->n, q,
+                                                         row_stride<T>(QBmax), Yp); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+  } else {
+    BKS_TRY((pack_into<T, IT>(X, ldx, t->m, p, row_stride<T>(PB), Xp, s)));
+  }
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
     const int QB = bucket_t<T>(qq);
     // stream order: the previous chunk's kernels have read Yp and the
     // partial sums before this pack overwrites them
-    BKS_TRY((pack_into<T, IT>(Y + ldy * q0, ldy, t->n, qq, row_stride<T>(QB), Yp, s)));
+    if (q > qchunk)
+      BKS_TRY((pack_into<T, IT>(Y + ldy * q0, ldy, t->n, qq, row_stride<T>(QB), Yp, s)));
     // columns a + p*(q0 + b) of the full output start at column p*q0
     BKS_TRY((dispatch<T, OT>(t->m1, t->vdtype, t->m1.c1.as<int32_t>(), t->m1.c0.as<int32_t>(),
                              Xp, PB, Yp, QB, t->n, false, p, qq, out + ldo * (p * q0), ldo, s,
@@ -155,11 +199,23 @@ int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
                 int q, OT* out, int64_t ldo, cudaStream_t s) {
   const int PB = bucket_t<T>(p);
   DevBuf Xp;
+  const int qchunk = qchunk_of(PB);
+  if (X2 && q <= qchunk) {  // one chunk of X2 columns: both packs in one launch
+    const int QB = bucket_t<T>(q);
+    const size_t xb = align256(sizeof(T) * (size_t)t->m * row_stride<T>(PB));
+    BKS_TRY(Xp.alloc(xb + sizeof(T) * (size_t)t->m * row_stride<T>(QB), s));
+    T* X2p = reinterpret_cast<T*>(static_cast<unsigned char*>(Xp.p) + xb);
+    k_pack2<IT, T><<<grid_for(2 * t->m), 256, 0, s>>>(X, ldx, t->m, p, row_stride<T>(PB),
+                                                      Xp.as<T>(), X2, ldx2, t->m, q,
+                                                      row_stride<T>(QB), X2p); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+    return dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
+                           Xp.as<T>(), PB, X2p, QB, t->m, false, p, q, out, ldo, s);
+  }
   BKS_TRY((pack<T, IT>(X, ldx, t->m, p, row_stride<T>(PB), Xp, s)));
   if (!X2)
     return dispatch<T, OT>(t->m3, t->vdtype, t->m3.c0.as<int32_t>(), t->m3.c1.as<int32_t>(),
                            Xp.as<T>(), PB, Xp.as<T>(), PB, t->m, true, p, p, out, ldo, s);
-  const int qchunk = qchunk_of(PB);
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
     const int QB = bucket_t<T>(qq);
@@ -174,14 +230,16 @@ int mode3_typed(const bks_tensor* t, const IT* X, int64_t ldx, int p, const IT* 
 
 // ---- cores ----------------------------------------------------------------
 // Small rank (r1 <= 8): F[a,b,c] = sum_k W[k,c] T[k, tri(a,b)] with T the
-// triangle mode-3 contraction A.(U,U)_{1,2}.
+// triangle mode-3 contraction A.(U,U)_{1,2}.  Blocks of kTriThreads threads
+// (the size of the shared reduction array).
+constexpr int kTriThreads = 256;
 template <typename T, typename IT, typename OT>
-__global__ void k_core_from_tri(const T* __restrict__ Tm, int64_t n, int r1, const IT* __restrict__ W,
+__global__ void __launch_bounds__(kTriThreads) k_core_from_tri(const T* __restrict__ Tm, int64_t n, int r1, const IT* __restrict__ W,
                                 int64_t ldw, int r3, OT* __restrict__ F) {
   const int ntri = r1 * (r1 + 1) / 2;
   for (int o = blockIdx.x; o < ntri * r3; o += gridDim.x) {
     const int tcol = o % ntri, c = o / ntri;
-    __shared__ T sh[256];
+    __shared__ T sh[kTriThreads];
     T acc = T(0);
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) acc += (T)W[k + ldw * c] * Tm[k + n * tcol];
     sh[threadIdx.x] = acc;
@@ -400,7 +458,7 @@ int core_typed(const bks_tensor* t, const IT* U, int64_t ldu, int r1, const IT* 
     DevBuf Tm;
     BKS_TRY(Tm.alloc(sizeof(T) * (size_t)t->n * ntri, s));
     BKS_TRY((mode3_typed<T, IT, T>(t, U, ldu, r1, nullptr, 0, r1, Tm.as<T>(), t->n, s)));
-    k_core_from_tri<T, IT, OT><<<std::min(ntri * r3, 1024), 256, 0, s>>>(Tm.as<T>(), t->n, r1, W,
+    k_core_from_tri<T, IT, OT><<<std::min(ntri * r3, 1024), kTriThreads, 0, s>>>(Tm.as<T>(), t->n, r1, W,
                                                                          ldw, r3, F); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
     return BKS_OK;
@@ -472,8 +530,20 @@ int gen_contract_typed(const bks_tensor* t, int md, const IT* B1, int64_t ld1, i
   const int64_t rows2 = md == 3 ? t->m : t->n;
   const int PB = bucket_t<T>(p);
   DevBuf Ap;
-  BKS_TRY((pack<T, IT>(B1, ld1, rows1, p, row_stride<T>(PB), Ap, s)));
   const int qchunk = qchunk_of(PB);
+  if (q <= qchunk) {  // one chunk of B2 columns: both packs in one launch
+    const int QB = bucket_t<T>(q);
+    const size_t ab = align256(sizeof(T) * (size_t)rows1 * row_stride<T>(PB));
+    BKS_TRY(Ap.alloc(ab + sizeof(T) * (size_t)rows2 * row_stride<T>(QB), s));
+    T* Bp = reinterpret_cast<T*>(static_cast<unsigned char*>(Ap.p) + ab);
+    k_pack2<IT, T><<<grid_for(rows1 + rows2), 256, 0, s>>>(B1, ld1, rows1, p, row_stride<T>(PB),
+                                                           Ap.as<T>(), B2, ld2, rows2, q,
+                                                           row_stride<T>(QB), Bp); ::bks::note_launch();
+    BKS_CUDA_TRY(cudaGetLastError());
+    return dispatch<T, OT>(P, t->vdtype, ia, ib, Ap.as<T>(), PB, Bp, QB, rows2, false, p, q, out,
+                           ldo, s);
+  }
+  BKS_TRY((pack<T, IT>(B1, ld1, rows1, p, row_stride<T>(PB), Ap, s)));
   for (int q0 = 0; q0 < q; q0 += qchunk) {
     const int qq = std::min(qchunk, q - q0);
     const int QB = bucket_t<T>(qq);
@@ -785,8 +855,55 @@ int build_core_plan(const Part& m3, int64_t n, int64_t nnz, CorePlan& cp, cudaSt
   return BKS_OK;
 }
 
+// First operands wider than the largest kernel bucket (8 columns): for each
+// column b of the second operand, the first operand in chunks of at most 8
+// columns [a0, a0 + pp).  Output columns a + p*b, a in the chunk, are then
+// the columns of a pp x 1 product written from column a0 + p*b on (mode 1
+// and full mode 3), or from a0 + b(b+1)/2 on with the chunks cut at b
+// (triangle: a <= b).  One tensor pass per chunk and column: a completeness
+// path for wide operands, not the solvers' path.
+constexpr int kWideChunk = 8;
+
+template <typename T>
+int mode1_wide(const bks_tensor* t, const T* X, int64_t ldx, int p, const T* Y, int64_t ldy,
+               int q, T* out, int64_t ldo, cudaStream_t s) {
+  for (int b = 0; b < q; ++b)
+    for (int a0 = 0; a0 < p; a0 += kWideChunk) {
+      const int pp = std::min(kWideChunk, p - a0);
+      BKS_TRY((mode1_typed<T, T, T>(t, X + ldx * a0, ldx, pp, Y + ldy * b, ldy, 1,
+                                    out + ldo * (a0 + (int64_t)p * b), ldo, s)));
+    }
+  return BKS_OK;
+}
+
+template <typename T>
+int mode3_wide(const bks_tensor* t, const T* X, int64_t ldx, int p, const T* X2, int64_t ldx2,
+               int q, T* out, int64_t ldo, cudaStream_t s) {
+  const bool tri = X2 == nullptr;
+  const int nb = tri ? p : q;
+  for (int b = 0; b < nb; ++b) {
+    const int alim = tri ? b + 1 : p;
+    const int64_t col0 = tri ? (int64_t)b * (b + 1) / 2 : (int64_t)p * b;
+    const T* xb = tri ? X + ldx * b : X2 + ldx2 * b;
+    const int64_t ldb = tri ? ldx : ldx2;
+    for (int a0 = 0; a0 < alim; a0 += kWideChunk) {
+      const int pp = std::min(kWideChunk, alim - a0);
+      BKS_TRY((mode3_typed<T, T, T>(t, X + ldx * a0, ldx, pp, xb, ldb, 1,
+                                    out + ldo * (col0 + a0), ldo, s)));
+    }
+  }
+  return BKS_OK;
+}
+
 int contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p, const void* Y,
                    int64_t ldy, int q, void* out, int64_t ldo, int dtype, cudaStream_t s) {
+  if (p > kWideChunk) {
+    if (dtype == BKS_F64)
+      return mode1_wide<double>(t, (const double*)X, ldx, p, (const double*)Y, ldy, q,
+                                (double*)out, ldo, s);
+    return mode1_wide<float>(t, (const float*)X, ldx, p, (const float*)Y, ldy, q, (float*)out,
+                             ldo, s);
+  }
   if (dtype == BKS_F64)
     return mode1_typed<double, double, double>(t, (const double*)X, ldx, p, (const double*)Y, ldy,
                                                q, (double*)out, ldo, s);
@@ -796,6 +913,13 @@ int contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p, const
 
 int contract_mode3(const bks_tensor* t, const void* X, int64_t ldx, int p, const void* X2,
                    int64_t ldx2, int q, void* out, int64_t ldo, int dtype, cudaStream_t s) {
+  if (p > kWideChunk) {
+    if (dtype == BKS_F64)
+      return mode3_wide<double>(t, (const double*)X, ldx, p, (const double*)X2, ldx2, q,
+                                (double*)out, ldo, s);
+    return mode3_wide<float>(t, (const float*)X, ldx, p, (const float*)X2, ldx2, q, (float*)out,
+                             ldo, s);
+  }
   if (dtype == BKS_F64)
     return mode3_typed<double, double, double>(t, (const double*)X, ldx, p, (const double*)X2,
                                                ldx2, q, (double*)out, ldo, s);
@@ -860,7 +984,6 @@ extern "C" int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ld
   BKS_TRY(check_common(t, X, ldx, p, dtype, t ? t->m : 0));
   BKS_TRY(check_common(t, Y, ldy, q, dtype, t->n));
   if (!out || ldo < t->m) return fail(BKS_EINVAL, "bad output");
-  if (p > 8 || q > 8) return fail(BKS_EUNSUPPORTED, "mode-1 widths p, q must be <= 8");
   return contract_mode1(t, X, ldx, p, Y, ldy, q, out, ldo, dtype, (cudaStream_t)stream);
 }
 
@@ -871,7 +994,6 @@ extern "C" int bks_contract_mode3(const bks_tensor* t, const void* X, int64_t ld
   BKS_TRY(check_common(t, X, ldx, p, dtype, t ? t->m : 0));
   if (X2) BKS_TRY(check_common(t, X2, ldx2, q, dtype, t->m));
   if (!out || ldo < t->n) return fail(BKS_EINVAL, "bad output");
-  if (p > 8 || (X2 && q > 8)) return fail(BKS_EUNSUPPORTED, "mode-3 widths p, q must be <= 8");
   return contract_mode3(t, X, ldx, p, X2, ldx2, q, out, ldo, dtype, (cudaStream_t)stream);
 }
 

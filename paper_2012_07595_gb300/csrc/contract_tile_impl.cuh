@@ -133,6 +133,8 @@ struct TileArgs {
   const int32_t* sia;  // the same for the lane-interleaved copy of the short rows
   const int32_t* sib;
   int32_t nbs;         // rows of operand B held in shared memory (0: gathered from global)
+  const int32_t* empty_rows;  // rows without entries: their wcols output columns are zeroed
+  int32_t nempty, wcols;
 };
 
 template <typename T, typename OT, int PB, int QB, bool TRI>
@@ -324,6 +326,16 @@ k_contract(TileArgs ta, const T* __restrict__ vals, const T* __restrict__ svals,
     for (int64_t x = threadIdx.x; x < cnt; x += blockDim.x) Bs[x] = Bp[x];
     __syncthreads();
   }
+  // rows without entries get zeros, spread over the whole grid before the
+  // items (these scattered stores overlap the items' loads)
+  {
+    const int64_t tot = (int64_t)ta.nempty * ta.wcols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+      const int r = (int)(t % ta.nempty), c = (int)(t / ta.nempty);
+      out[ta.empty_rows[r] + ldo * c] = OT(0);
+    }
+  }
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * kTileWarps;
   const int total = ta.nvec + (ta.nshortv + 31) / 32;
@@ -431,6 +443,7 @@ __global__ void k_split_reduce(const int32_t* __restrict__ split_row,
                                const T* __restrict__ partial, int p, int q, OT* __restrict__ out,
                                int64_t ldo) {
   constexpr int W = Shape<PB, QB, TRI>::W;
+  static_assert(W <= 256, "one output column per thread of the 256-thread block");
   __shared__ T sh[256], shc[256];
   const int s = blockIdx.x;
   if (s >= nsplit) return;
@@ -438,8 +451,22 @@ __global__ void k_split_reduce(const int32_t* __restrict__ split_row,
   const int groups = 256 / W;
   const int c = threadIdx.x % W, g = threadIdx.x / W;
   T acc = T(0), cmp = T(0);
-  if (g < groups)
-    for (int f = f0 + g; f < f1; f += groups) two_sum_acc(acc, cmp, partial[(int64_t)f * W + c]);
+  if (g < groups) {
+    // four loads issued before their four additions (the same order of
+    // additions as one piece at a time)
+    int f = f0 + g;
+    for (; f + 3 * groups < f1; f += 4 * groups) {
+      const T y0 = partial[(int64_t)f * W + c];
+      const T y1 = partial[(int64_t)(f + groups) * W + c];
+      const T y2 = partial[(int64_t)(f + 2 * groups) * W + c];
+      const T y3 = partial[(int64_t)(f + 3 * groups) * W + c];
+      two_sum_acc(acc, cmp, y0);
+      two_sum_acc(acc, cmp, y1);
+      two_sum_acc(acc, cmp, y2);
+      two_sum_acc(acc, cmp, y3);
+    }
+    for (; f < f1; f += groups) two_sum_acc(acc, cmp, partial[(int64_t)f * W + c]);
+  }
   sh[threadIdx.x] = acc;
   shc[threadIdx.x] = cmp;
   __syncthreads();
@@ -487,9 +514,18 @@ int launch_tiles(const TileArgs& ta, int items, size_t smem, const T* vals, cons
   if (attr != cudaSuccess)
     return fail(BKS_ECUDA, std::string("k_contract shared-memory limit: ") +
                                cudaGetErrorString(attr));
-  int per_sm = 0;
-  BKS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, k_contract<T, OT, PB, QB, TRI, BSM>, kTileWarps * 32, smem));
+  // resident blocks per SM, cached per device for the last shared-memory size
+  static std::atomic<int64_t> occ[kMaxDevices];
+  const int dev = current_device();
+  const int64_t key = (int64_t)(smem + 1) << 8;
+  int64_t hit = dev >= 0 ? occ[dev].load(std::memory_order_relaxed) : 0;
+  int per_sm = (hit & ~int64_t(255)) == key ? (int)(hit & 255) : 0;
+  if (per_sm == 0) {
+    BKS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_contract<T, OT, PB, QB, TRI, BSM>, kTileWarps * 32, smem));
+    if (dev >= 0 && per_sm > 0 && per_sm < 256)
+      occ[dev].store(key | per_sm, std::memory_order_relaxed);
+  }
   const int64_t fit = (int64_t)std::max(1, per_sm) * num_sms();
   const int blocks = (int)std::max<int64_t>(
       1, std::min<int64_t>(fit, ((int64_t)items + kTileWarps - 1) / kTileWarps));
@@ -512,9 +548,10 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
   const size_t bbytes = sizeof(T) * (size_t)brows * row_stride<T>(NB);
   const int nbs = bbytes <= kBSmemMax ? (int)brows : 0;
   const size_t smem = nbs > 0 ? bbytes : 0;
+  const int w = TRI ? p * (p + 1) / 2 : p * q;
   TileArgs ta{P.vitems.as<int4>(), P.vorder.as<int32_t>(), P.vptr.as<int32_t>(),
               P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib,
-              sell_of(P, ia), sell_of(P, ib), nbs};
+              sell_of(P, ia), sell_of(P, ib), nbs, P.empty_rows.as<int32_t>(), P.nempty, w};
   DevBuf partial;
   if (P.nslots > 0 && !part) {
     BKS_TRY(partial.alloc(sizeof(T) * (size_t)P.nslots * W, s));
@@ -538,8 +575,7 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
         out, ldo); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
-  if (P.nempty > 0) {
-    const int w = TRI ? p * (p + 1) / 2 : p * q;
+  if (P.nempty > 0 && P.nv == 0) {  // else the tile kernel zeroes them
     k_zero_rows<OT><<<grid_for((int64_t)P.nempty * w), 256, 0, s>>>(P.empty_rows.as<int32_t>(),
                                                                     P.nempty, w, out, ldo); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());

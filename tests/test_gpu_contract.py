@@ -63,6 +63,50 @@ def test_mode3_fp64(name, p, q):
     assert np.all(np.abs(tri - O.mode3(A, X)) <= 1e-13 * O.mode3(Aabs, np.abs(X)) + 1e-300)
 
 
+@pytest.mark.parametrize("name", ["uniform_small", "long_rows", "zipf_mid"])
+@pytest.mark.parametrize("p,q", [(9, 2), (12, 11), (17, 3)])
+def test_wide_operands_fp64(name, p, q):
+    """Operands wider than the kernels' 8-column bucket: the front end cuts
+    X into chunks of at most 8 columns per column of the second operand
+    (mode 1, full mode 3, and the triangle with chunks cut at a <= b);
+    every column against the oracle, the output buffer's other columns
+    untouched."""
+    import torch
+    bk, A, T = _setup(name)
+    g = synth.rng(18)
+    X = g.standard_normal((A.m, p)); Y = g.standard_normal((A.n, q)); X2 = g.standard_normal((A.m, q))
+    tX = torch.tensor(X, device="cuda")
+    Aabs = O.SymTensor(A.m, A.n, A.i, A.j, A.k, np.abs(A.v))
+    Obig = torch.full((p * q + 2, A.m), float("nan"), device="cuda", dtype=torch.float64).t()
+    got = Obig[:, 1:1 + p * q]
+    bk.bks_contract_mode1(T, tX, torch.tensor(Y, device="cuda"), out=got)
+    absref = O.mode1(Aabs, np.abs(X), np.abs(Y))
+    assert np.all(np.abs(got.cpu().numpy() - O.mode1(A, X, Y)) <= 1e-13 * absref + 1e-300)
+    ob = Obig.cpu().numpy()
+    assert np.all(np.isnan(ob[:, 0])) and np.all(np.isnan(ob[:, -1]))
+    g3 = bk.bks_contract_mode3(T, tX, torch.tensor(X2, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(g3 - O.mode3(A, X, X2)) <= 1e-13 * O.mode3(Aabs, np.abs(X), np.abs(X2)) + 1e-300)
+    tri = bk.bks_contract_mode3(T, tX).cpu().numpy()
+    assert tri.shape == (A.n, p * (p + 1) // 2)
+    assert np.all(np.abs(tri - O.mode3(A, X)) <= 1e-13 * O.mode3(Aabs, np.abs(X)) + 1e-300)
+
+
+def test_wide_operands_fp32_within_blocked_sum_bound():
+    import torch
+    bk, A, T = _setup("zipf_mid", np.float32)
+    g = synth.rng(19)
+    X = g.standard_normal((A.m, 10)).astype(np.float32); Y = g.standard_normal((A.n, 9)).astype(np.float32)
+    Aabs = O.SymTensor(A.m, A.n, A.i, A.j, A.k, np.abs(A.v))
+    tX = torch.tensor(X, device="cuda")
+    got = bk.bks_contract_mode1(T, tX, torch.tensor(Y, device="cuda")).cpu().numpy()
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    bound = fp32_bound(O.mode1(Aabs, np.abs(X64), np.abs(Y64)))
+    assert np.all(np.abs(got - O.mode1(A, X64, Y64)) <= bound)
+    tri = bk.bks_contract_mode3(T, tX).cpu().numpy()
+    bound3 = fp32_bound(O.mode3(Aabs, np.abs(X64)), 512.0)
+    assert np.all(np.abs(tri - O.mode3(A, X64)) <= bound3)
+
+
 @pytest.mark.parametrize("name", ["uniform_small", "zipf", "long_rows"])
 def test_contractions_fp32_within_blocked_sum_bound(name):
     import torch
