@@ -69,6 +69,14 @@ __global__ void k_seg_starts(const int32_t* f, const int32_t* pos, int64_t N, in
 }
 
 // One thread per run of equal keys: sum the values left to right in V.
+// Long runs (the heaviest duplicated keys of a power-law input) load eight
+// values ahead of their additions; the order of the additions is the same.
+template <typename V>
+__device__ __forceinline__ V run_value(const uint32_t* pay, int64_t t, const V* vin,
+                                       const uint32_t* mirror_src, int64_t nnz_in) {
+  const uint32_t p = pay[t];
+  return (p < (uint64_t)nnz_in) ? vin[p] : vin[mirror_src[p - nnz_in]];
+}
 template <typename V>
 __global__ void k_sum_runs(const uint64_t* keys, const uint32_t* pay, const int32_t* starts,
                            int64_t nseg, int64_t N, const V* vin, const uint32_t* mirror_src,
@@ -78,12 +86,16 @@ __global__ void k_sum_runs(const uint64_t* keys, const uint32_t* pay, const int3
        u += (int64_t)gridDim.x * blockDim.x) {
     int64_t s = starts[u];
     int64_t e = (u + 1 < nseg) ? starts[u + 1] : N;
-    V acc = V(0);
-    for (int64_t t = s; t < e; ++t) {
-      uint32_t p = pay[t];
-      V x = (p < (uint64_t)nnz_in) ? vin[p] : vin[mirror_src[p - nnz_in]];
-      acc = (t == s) ? x : add_rn(acc, x);
+    V acc = run_value(pay, s, vin, mirror_src, nnz_in);  // the first value as it is
+    int64_t t = s + 1;
+    for (; t + 8 <= e; t += 8) {
+      V x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = run_value(pay, t + q, vin, mirror_src, nnz_in);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc = add_rn(acc, x[q]);
     }
+    for (; t < e; ++t) acc = add_rn(acc, run_value(pay, t, vin, mirror_src, nnz_in));
     uint64_t key = keys[s];
     row[u] = (int32_t)(key >> (bj + bk));
     jj[u] = (int32_t)((key >> bk) & ((1ull << bj) - 1ull));
