@@ -297,7 +297,13 @@ struct RegBlocks {
                                   (Shape<PB, QB, TRI>::W + 4 * (PB + (BSM ? 0 : NB))) + 32;
   static constexpr int regs = (live + 7) / 8 * 8;
   static constexpr int by_regs = 65536 / (kTileWarps * 32 * regs);
-  static constexpr int v = by_regs < 1 ? 1 : (by_regs > 8 ? 8 : by_regs);
+  static constexpr int v0 = by_regs < 1 ? 1 : (by_regs > 8 ? 8 : by_regs);
+  // The FP32 3-column triangle with operand B gathered spills 40 bytes at
+  // four blocks (64 registers); at three blocks it ran 4% (5.0M entries)
+  // and 12% (48.5M entries) faster on GB300.  One block fewer lost 1-8% on
+  // every other measured shape (mode 1, 3 x 3 to 5 x 5, FP32 and FP64).
+  static constexpr bool spills = sizeof(T) == 4 && TRI && !BSM && PB == 3;
+  static constexpr int v = spills && v0 > 1 ? v0 - 1 : v0;
 };
 
 // Mode-1 / mode-3 contraction over the work plan (see common.cuh).  The
