@@ -153,7 +153,8 @@ int bks_contract_mode1(const bks_tensor* t, const void* X, int64_t ldx, int p,
  *   1024 below 32M, 2048 from 32M, unless bks_tensor_autotune / set_tiles
  *   chose another) are cut, about nnz / split on power-law tensors.  The
  *   worst case is 64*m + 64*n + 256*nslots bytes in FP64.  A call needing
- *   more than 32 MiB returns BKS_EUNSUPPORTED before launching anything.
+ *   more than 32 MiB, or with p or q above 8, returns BKS_EUNSUPPORTED
+ *   before launching anything.
  *   The call allocates nothing.  Its first call on a device looks up the
  *   array's device address (cudaGetSymbolAddress) with that device current;
  *   make that first call before any stream capture.  All calls share the
