@@ -60,6 +60,7 @@ class Clocks:
 
     def __init__(self):
         self.samples = []
+        self.mark = 0
         self.proc = None
         self.thread = None
 
@@ -69,7 +70,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={idx}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
                                          text=True)
         except Exception:
@@ -77,6 +78,13 @@ class Clocks:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi takes a moment to start: wait (at most 3 s) for its first
+        # sample, so that the samples kept (those after this point) cover the
+        # timed region from its start
+        t0 = time.perf_counter()
+        while not self.samples and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.mark = len(self.samples)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -97,7 +105,8 @@ class Clocks:
         mx = 0.0
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for s in self.samples:
+        kept = self.samples[self.mark:] or self.samples
+        for s in kept:
             try:
                 sm.append(float(s[1]))
                 mx = max(mx, float(s[2]))
