@@ -316,7 +316,8 @@ int bks_tensor_set_tiles(bks_tensor* t, int tile, int split, void* stream);
  *   info[njobs] (host, nullable): per-job info; status[njobs] (host,
  *     nullable): per-job return code.
  * Returns BKS_OK when every job returned BKS_OK, else the first failing
- * job's code (the other jobs still ran).  The caller's `stream` is made to
+ * job's code (the other jobs still ran).  The jobs start after the work
+ * queued on the caller's `stream` before the call, and `stream` is made to
  * wait for all jobs. */
 #define BKS_BATCH_AUTOTUNE 1
 int bks_batch_solve(int njobs, bks_tensor* const* T, const bks_params* P,

@@ -76,6 +76,15 @@ extern "C" int bks_batch_solve(int njobs, bks_tensor* const* T, const bks_params
   nstreams = std::max(1, std::min(nstreams, njobs));
   int dev = 0;
   BKS_CUDA_TRY(cudaGetDevice(&dev));
+  // the jobs start after the work the caller queued on `stream` (their
+  // inputs may still be in flight there)
+  cudaEvent_t ready = nullptr;
+  BKS_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  const cudaError_t rec = cudaEventRecord(ready, (cudaStream_t)stream);
+  if (rec != cudaSuccess) {
+    cudaEventDestroy(ready);
+    return fail(BKS_ECUDA, std::string("batch: ") + cudaGetErrorString(rec));
+  }
   std::vector<int> rc(njobs, BKS_OK);
   std::atomic<int> next{0};
   TileCache cache;
@@ -84,7 +93,9 @@ extern "C" int bks_batch_solve(int njobs, bks_tensor* const* T, const bks_params
   auto worker = [&](int w) {
     cudaSetDevice(dev);
     cudaStream_t st = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamWaitEvent(st, ready, 0) != cudaSuccess) {
+      if (st) cudaStreamDestroy(st);
       for (int q; (q = next.fetch_add(1)) < njobs;) rc[q] = fail(BKS_ECUDA, "batch: stream");
       return;
     }
@@ -105,6 +116,7 @@ extern "C" int bks_batch_solve(int njobs, bks_tensor* const* T, const bks_params
   std::vector<std::thread> th;
   for (int w = 0; w < nstreams; ++w) th.emplace_back(worker, w);
   for (auto& x : th) x.join();
+  cudaEventDestroy(ready);
   for (int w = 0; w < nstreams; ++w) {
     if (done[w]) {
       cudaStreamWaitEvent((cudaStream_t)stream, done[w], 0);
