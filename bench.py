@@ -354,7 +354,8 @@ def large_workload(bk, torch, stream, flush, hbm, peak_kind):
         core F = A.(U,U,W) at (5, 5, 5);
       * `solve`: a full mixed-precision solve with its FP64 refinement.
     One timed contraction call = pack of the operands, the contraction
-    kernel, the piece reduction of long rows and the zero rows; algorithmic
+    kernel (which also zeroes the rows without entries) and the piece
+    reduction of long rows; algorithmic
     bytes = index and value streams + row pointers + operands read once +
     output written once (gathers served by L2 not counted).  `traffic`: DRAM
     bytes of one k_contract launch on this tensor from an ncu capture."""
@@ -396,8 +397,8 @@ def large_workload(bk, torch, stream, flush, hbm, peak_kind):
                 "frac": alg / t / 1e9 / hbm}
 
     r44 = mode1(4, 4)
-    roofline = {"kernel": "bks_contract_mode1 FP32 (pack + k_contract<float,float,4,4,0,1> + "
-                          "piece reduction + zero rows)",
+    roofline = {"kernel": "bks_contract_mode1 FP32 (operand packs + k_contract<float,float,4,4,0,1>, "
+                          "which also zeroes the rows without entries, + piece reduction)",
                 "workload": f"zipf1.2 (1,2)-symmetric 1e6 x 1e6 x 200, {nnz} stored "
                             f"({L['draws']} draws mirrored, duplicates summed), X 4 cols, Y 4 cols",
                 "bound": "hbm", "achieved": r44["GB_per_s"], "peak": hbm, "unit": "GB/s",
@@ -930,8 +931,9 @@ def main():
     alg_bytes = nnz * (4 + 4 + 4) + (w["m"] + 1) * 4 + w["m"] * w["r"] * 4 + w["n"] * 4 * 4 \
         + w["m"] * 12 * 4
     achieved = alg_bytes / kt / 1e9
-    roofline_workload = {"kernel": "bks_contract_mode1 FP32 3 x 4 (pack + k_contract<float,float,"
-                                   "3,4,0,1> + piece reduction + zero rows)",
+    roofline_workload = {"kernel": "bks_contract_mode1 FP32 3 x 4 (operand packs + k_contract<float,"
+                                   "float,3,4,0,1>, which also zeroes the rows without entries, + "
+                                   "piece reduction)",
                          "workload": w["workload"],
                          "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
