@@ -555,9 +555,19 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
   const int nbs = bbytes <= kBSmemMax ? (int)brows : 0;
   const size_t smem = nbs > 0 ? bbytes : 0;
   const int w = TRI ? p * (p + 1) / 2 : p * q;
+  // The tile kernel zeroes the rows without entries when its grid is large
+  // enough for them: at most 64 stores per thread of the smallest grid it
+  // can get (one block per 8 items, at most one block per SM).  A tensor
+  // with few entries and many empty rows gets the separate zero kernel,
+  // sized by its own work.
+  const int64_t min_blocks =
+      std::min<int64_t>(((int64_t)plan_warps(P) + kTileWarps - 1) / kTileWarps, num_sms());
+  const bool fused_zero =
+      P.nv > 0 && (int64_t)P.nempty * w <= 64 * (int64_t)kTileWarps * 32 * min_blocks;
   TileArgs ta{P.vitems.as<int4>(), P.vorder.as<int32_t>(), P.vptr.as<int32_t>(),
               P.vrow.as<int32_t>(), P.vslot.as<int32_t>(), P.nvec, P.nshortv, ia, ib,
-              sell_of(P, ia), sell_of(P, ib), nbs, P.empty_rows.as<int32_t>(), P.nempty, w};
+              sell_of(P, ia), sell_of(P, ib), nbs, P.empty_rows.as<int32_t>(),
+              fused_zero ? P.nempty : 0, w};
   DevBuf partial;
   if (P.nslots > 0 && !part) {
     BKS_TRY(partial.alloc(sizeof(T) * (size_t)P.nslots * W, s));
@@ -581,7 +591,7 @@ int launch_contract(const Part& P, int vdtype, const int32_t* ia, const int32_t*
         out, ldo); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
   }
-  if (P.nempty > 0 && P.nv == 0) {  // else the tile kernel zeroes them
+  if (P.nempty > 0 && !fused_zero) {
     k_zero_rows<OT><<<grid_for((int64_t)P.nempty * w), 256, 0, s>>>(P.empty_rows.as<int32_t>(),
                                                                     P.nempty, w, out, ldo); ::bks::note_launch();
     BKS_CUDA_TRY(cudaGetLastError());
