@@ -46,6 +46,46 @@ def _gold():
         return json.load(f)
 
 
+def test_orth_block_projected_block_orthogonal_when_nearly_dependent():
+    """Projecting twice leaves the projected block orthogonal to Q to
+    working precision relative to its own norm, even when the block lies in
+    span(Q) but for a 1e-10 residual (the stage-1 block near convergence,
+    whose residual carries the gradient).  One classical Gram-Schmidt round
+    would leave about eps ||B|| / ||P|| = 1e-6 of it in span(Q)."""
+    g = synth.rng(13)
+    m = 300
+    Q = np.linalg.qr(g.standard_normal((m, 9)))[0]
+    N = g.standard_normal((m, 4))
+    N -= Q @ (Q.T @ N)
+    B = Q @ g.standard_normal((9, 4)) + 1e-10 * N
+    Qn, H, R, kept, P = O.orth_block(Q, B, 1e-14)
+    for c in range(4):
+        assert np.linalg.norm(Q.T @ P[:, c]) <= 1e-12 * np.linalg.norm(P[:, c])
+    assert np.linalg.norm(P - 1e-10 * N) <= 1e-5 * np.linalg.norm(1e-10 * N)
+    assert kept == [0, 1, 2, 3]
+
+
+def test_orth_block_drop_rule_is_relative():
+    """The drop rule compares a column's residual with its own raw norm, so
+    the kept columns do not depend on the scale of the block: a tiny
+    independent column is kept, a huge nearly dependent one is dropped."""
+    g = synth.rng(14)
+    m = 120
+    Q = np.linalg.qr(g.standard_normal((m, 5)))[0]
+    N = g.standard_normal((m, 3))
+    N -= Q @ (Q.T @ N)
+    B = Q @ g.standard_normal((5, 3)) + N
+    ref = O.orth_block(Q, B, 1e-12)[3]
+    assert ref == [0, 1, 2]
+    for scale in (1e-20, 1.0, 1e20):
+        assert O.orth_block(Q, scale * B, 1e-12)[3] == ref
+    # column 1 dependent on Q up to a 1e-14 relative residual, at a large scale
+    B2 = B.copy()
+    B2[:, 1] = Q @ g.standard_normal(5) + 1e-14 * N[:, 1]
+    for scale in (1e-20, 1.0, 1e20):
+        assert O.orth_block(Q, scale * B2, 1e-12)[3] == [0, 2]
+
+
 def test_schedule_tables():
     gold = _gold()
     for t in gold["tables"]:
