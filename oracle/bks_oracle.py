@@ -742,6 +742,22 @@ def ng_step(C: np.ndarray, Uh: np.ndarray, Wh: np.ndarray):
 INNER_INIT_SWEEPS = 5
 
 
+def _ng_try(C: np.ndarray, Uh: np.ndarray, Wh: np.ndarray, nf: float):
+    """One Newton-Grassmann step from (Uh, Wh), kept only when ``ng_step``
+    takes it (-H positive definite) and ||F|| does not drop below ``nf``
+    (relative 1e-14): this library's safeguard away from a maximum.
+    Returns (Uh', Wh', grad', normF', taken); a refused step returns the
+    old point."""
+    Un, Wn, ok = ng_step(C, Uh, Wh)
+    if not ok:
+        return Uh, Wh, None, nf, False
+    T1, T3 = _c_t1(C, Un, Wn), _c_t3(C, Un)
+    gn, nfn, _ = _inner_grad(Un, Wn, T1, T3)
+    if nfn < nf * (1.0 - 1e-14):
+        return Uh, Wh, None, nf, False
+    return Un, Wn, gn, nfn, True
+
+
 def inner_solve(C: np.ndarray, r1: int, r3: int, tol: float, max_inner: int = 1000,
                 init_sweeps: int = INNER_INIT_SWEEPS, method: str = "ng"):
     """Best rank-(r1,r1,r3) approximation of the dense (1,2)-symmetric core
@@ -778,11 +794,7 @@ def inner_solve(C: np.ndarray, r1: int, r3: int, tol: float, max_inner: int = 10
     g, nf = start[2], start[3]
     sweeps, steps = pre, 0
     while g > tol * nf and steps + sweeps - pre < max_inner:
-        Un, Wn, ok = ng_step(C, Uh, Wh)
-        if ok:
-            T1, T3 = _c_t1(C, Un, Wn), _c_t3(C, Un)
-            gn, nfn, _ = _inner_grad(Un, Wn, T1, T3)
-            ok = nfn >= nf * (1.0 - 1e-14)
+        Un, Wn, gn, nfn, ok = _ng_try(C, Uh, Wh, nf)
         if ok:
             Uh, Wh, g, nf = Un, Wn, gn, nfn
             steps += 1

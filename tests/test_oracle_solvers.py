@@ -369,3 +369,48 @@ def test_inner_solve_ng_takes_few_steps():
         assert i_h["sweeps"] > 3 * (i_ng["ng_steps"] + i_ng["sweeps"])
         if abs(i_ng["normF"] - i_h["normF"]) < 1e-12 * i_h["normF"]:
             assert O.sin_theta_max(U1, U2) < 1e-8 and O.sin_theta_max(W1, W2) < 1e-8
+
+
+def test_newton_step_refused_where_it_lowers_F():
+    """The inner solve's Newton-Grassmann safeguard: a step that ng_step
+    takes (-H positive definite) but that lowers ||F|| is refused and the
+    point kept; a step that raises ||F|| is taken.  Far from a maximum the
+    quadratic model can overshoot, so the walk below meets both kinds."""
+    from oracle import bks_oracle as B
+    lowered = raised = 0
+    for seed in range(12):
+        g = synth.rng(500 + seed)
+        C = g.standard_normal((8, 8, 5)); C = C + C.transpose(1, 0, 2)
+        Uh = np.linalg.qr(g.standard_normal((8, 2)))[0]
+        Wh = np.linalg.qr(g.standard_normal((5, 2)))[0]
+        for _ in range(6):
+            _, nf, _ = B._inner_grad(Uh, Wh, B._c_t1(C, Uh, Wh), B._c_t3(C, Uh))
+            Un, Wn, taken_raw = B.ng_step(C, Uh, Wh)
+            U2, W2, g2, nf2, taken = B._ng_try(C, Uh, Wh, nf)
+            if not taken_raw:
+                assert not taken and U2 is Uh and W2 is Wh
+                Uh, Wh, *_ = B._hooi_sweeps(C, Uh, Wh, 1, 0.0)
+                continue
+            _, nfn, _ = B._inner_grad(Un, Wn, B._c_t1(C, Un, Wn), B._c_t3(C, Un))
+            if nfn < nf * (1.0 - 1e-14):
+                lowered += 1
+                assert not taken and U2 is Uh and nf2 == nf
+                break
+            raised += 1
+            assert taken and np.array_equal(U2, Un) and nf2 == nfn
+            Uh, Wh = Un, Wn
+    assert lowered >= 1 and raised >= 1
+
+
+def test_hooi_gradient_is_the_global_gradient():
+    """The gradient HOOI tests every 10 iterations is the G-gradient of
+    Section 2.5 (mode 1 counted twice for the mode-2 copy), which
+    gradient_global computes and the finite-difference pin fixes."""
+    A = _sym_sparse(22, 30, 7, 700)
+    g = synth.rng(4)
+    for r1, r3 in [(2, 2), (3, 2)]:
+        U = synth.orthonormal(g, A.m, r1); W = synth.orthonormal(g, A.n, r3)
+        res = O.hooi(A, U, W, tol=0.0, max_iter=0)
+        gg, nfg, _ = O.gradient_global(A, U, W)
+        assert abs(res.history[0]["grad_rel"] - gg / nfg) <= 1e-12 * gg / nfg
+        assert abs(res.history[0]["normF"] - nfg) <= 1e-13 * nfg
