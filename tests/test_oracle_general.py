@@ -49,6 +49,18 @@ def test_contractions_and_core_by_einsum():
     assert np.allclose(O.gunfold(C, 2), W.T @ e3, atol=1e-12)
 
 
+def test_gcore_by_einsum_over_several_entry_blocks():
+    """The core over more stored entries than one of the oracle's entry
+    blocks (2048): every entry counted exactly once."""
+    c = synth.general_random_coo(6, 20, 18, 16, 9000)
+    A = _gen(c)
+    assert A.nnz > 2 * 2048
+    g = synth.rng(6)
+    X, Y, Z = g.standard_normal((20, 3)), g.standard_normal((18, 4)), g.standard_normal((16, 2))
+    ref = np.einsum("ijk,ia,jb,kc->abc", A.dense(), X, Y, Z)
+    assert np.allclose(O.gcore(A, X, Y, Z), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
 def test_schedule_counts_first_stages():
     # stage 1 adds r_a r_b columns per mode; stage 2 of BK adds the two
     # off-diagonal pairs (0,1), (1,0) of p-column bars
@@ -206,3 +218,19 @@ def test_inner_solve_takes_the_better_start():
     T2 = np.einsum("ia,jb,kc,abc->ijk", E[0], E[1], E[2], F0)
     Uh, Vh, Wh, info = O.gen_inner_solve(T2, (2, 2, 2), 1e-12, max_inner=0)
     assert abs(info["normF"] - np.linalg.norm(F0)) <= 1e-12 * np.linalg.norm(F0)
+
+
+def test_inner_gradient_is_the_global_gradient_of_the_core():
+    """The general inner solve's gradient on a dense core C is the
+    three-term G-gradient of C itself (gen_gradient_global on C stored as
+    a sparse tensor)."""
+    from oracle import bks_general_oracle as G
+    g = synth.rng(24)
+    for k, r in [((9, 8, 6), (2, 3, 2)), ((7, 10, 5), (3, 2, 2))]:
+        C = g.standard_normal(k)
+        facs = tuple(np.linalg.qr(g.standard_normal((k[d], r[d])))[0] for d in range(3))
+        gi, nfi = G._ginner_grad(C, facs)
+        ii, jj, kk = np.meshgrid(*(np.arange(x) for x in k), indexing="ij")
+        A = O.gen_tensor(*k, ii.ravel(), jj.ravel(), kk.ravel(), C.ravel())
+        gg, nfg, _ = O.gen_gradient_global(A, *facs)
+        assert abs(gi - gg) <= 1e-12 * gg and abs(nfi - nfg) <= 1e-13 * nfg

@@ -414,3 +414,18 @@ def test_hooi_gradient_is_the_global_gradient():
         gg, nfg, _ = O.gradient_global(A, U, W)
         assert abs(res.history[0]["grad_rel"] - gg / nfg) <= 1e-12 * gg / nfg
         assert abs(res.history[0]["normF"] - nfg) <= 1e-13 * nfg
+
+
+def test_inner_gradient_is_the_global_gradient_of_the_core():
+    """The inner solve's gradient on a dense (1,2)-symmetric core C is the
+    G-gradient of Section 2.5 of C itself at (Uh, Uh, Wh): the oracle's
+    gradient_global applied to C stored as a sparse tensor."""
+    from oracle import bks_oracle as B
+    g = synth.rng(23)
+    for k1, k3, r1, r3 in [(9, 6, 2, 2), (12, 7, 3, 2)]:
+        C = g.standard_normal((k1, k1, k3)); C = C + C.transpose(1, 0, 2)
+        Uh = np.linalg.qr(g.standard_normal((k1, r1)))[0]
+        Wh = np.linalg.qr(g.standard_normal((k3, r3)))[0]
+        gi, nfi, _ = B._inner_grad(Uh, Wh, B._c_t1(C, Uh, Wh), B._c_t3(C, Uh))
+        gg, nfg, _ = O.gradient_global(_from_dense(C), Uh, Wh)
+        assert abs(gi - gg) <= 1e-12 * gg and abs(nfi - nfg) <= 1e-13 * nfg
