@@ -86,6 +86,25 @@ def test_orth_block_drop_rule_is_relative():
         assert O.orth_block(Q, scale * B2, 1e-12)[3] == [0, 2]
 
 
+def test_bk_block_numbering_follows_the_printed_diagrams():
+    """The order in which the BK schedule generates its blocks (within a
+    stage U-blocks first, then W-blocks) numbers them as Table 3's
+    diagrams do; later stages take the first p columns of blocks by these
+    numbers, so the order fixes the bases from stage 3 on."""
+    with open(os.path.join(GOLD, "bk_block_numbering.json")) as f:
+        gold = json.load(f)
+    from oracle import bks_oracle as B
+    done_u, done_w = set(), set()
+    U, W = [], []
+    for stage in range(1, 5):
+        us, ws = B._stage_pairs("bk", stage, 100, 100, done_u, done_w)
+        U += [(a, b) for a, b, _ in us]
+        W += [(a, b) for a, b, _ in ws]
+        assert [t for _, _, t in ws] == ([True] if stage == 1 else [False] * len(ws))
+    assert [[a, b, k + 1] for k, (a, b) in enumerate(U)] == gold["U"]
+    assert [[a, b, k + 1] for k, (a, b) in enumerate(W)] == gold["W"]
+
+
 def test_schedule_tables():
     gold = _gold()
     for t in gold["tables"]:
