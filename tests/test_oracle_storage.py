@@ -148,3 +148,29 @@ def test_openmp_contraction_loop_equals_the_oracle():
         ref = O.mode1(A, X, Y)
         assert np.allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
     assert omp.threads() >= 1
+
+
+def test_openmp_mode1_loop_matches_einsum():
+    """The OpenMP build of the oracle's mode-1 loop (the all-cores column of
+    the benchmark's CPU baseline) against the dense definition, on a dense
+    tensor and on a sparse one with empty rows."""
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    from oracle import omp
+    try:
+        omp.build()
+    except RuntimeError as e:
+        pytest.skip(f"OpenMP build failed: {e}")
+    T, A = _dense_case(3, 9, 5, False)
+    g = synth.rng(8)
+    for p, q in [(1, 1), (3, 2), (4, 4)]:
+        X = g.standard_normal((9, p)); Y = g.standard_normal((5, q))
+        ref = np.einsum("ijk,ja,kb->iab", T, X, Y).reshape(9, -1, order="F")
+        assert np.allclose(omp.mode1_omp(A, X, Y), ref, rtol=1e-13, atol=1e-12)
+    c = synth.random_coo(9, 40, 6, 15)
+    S = O.symmetrise(c.m, c.n, c.i, c.j, c.k, c.v)
+    assert np.unique(S.i).size < 40             # some rows are empty
+    X = g.standard_normal((40, 3)); Y = g.standard_normal((6, 4))
+    ref = np.einsum("ijk,ja,kb->iab", S.dense(), X, Y).reshape(40, -1, order="F")
+    assert np.allclose(omp.mode1_omp(S, X, Y), ref, rtol=1e-13, atol=1e-12)
