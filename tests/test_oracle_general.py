@@ -234,3 +234,32 @@ def test_inner_gradient_is_the_global_gradient_of_the_core():
         A = O.gen_tensor(*k, ii.ravel(), jj.ravel(), kk.ravel(), C.ravel())
         gg, nfg, _ = O.gen_gradient_global(A, *facs)
         assert abs(gi - gg) <= 1e-12 * gg and abs(nfi - nfg) <= 1e-13 * nfg
+
+
+def test_expansion_sizes_follow_the_bar_rule():
+    """With blocks wider than p after stage 1 (r_a r_b = 6 > p = 4), later
+    stages contract only the first p columns of each block but U_0, V_0,
+    W_0 (the bars of Tables 1-3 in their general form): on a tensor large
+    enough that nothing is dropped, the bases have the sizes the pair and
+    bar rule gives."""
+    A = _gen(synth.general_random_coo(14, 90, 80, 70, 60000))
+    g = synth.rng(12)
+    r = (2, 3, 2)
+    facs = [synth.orthonormal(g, d, rr) for d, rr in zip((90, 80, 70), r)]
+    for s in (2, 3):
+        X, Y, Z, _, _ = O.gen_expand(A, *facs, s, 4)
+        assert (X.shape[1], Y.shape[1], Z.shape[1]) == O.gen_schedule_counts(r, s, 4, dims=(90, 80, 70))[-1]
+
+
+def test_general_schedule_in_modes_1_and_2_is_the_symmetric_u_schedule():
+    """Modes 1 and 2 of the general BK schedule pair blocks of the other two
+    factors as the (1,2)-symmetric schedule pairs (U, W) blocks, in the same
+    order, which Table 3's diagrams number."""
+    from oracle import bks_oracle as B
+    done_s, done_w = set(), set()
+    done_g = [set(), set(), set()]
+    for stage in range(1, 5):
+        us, _ = B._stage_pairs("bk", stage, 100, 100, done_s, done_w)
+        gp = O.gen_stage_pairs("bk", stage, (100, 100, 100), done_g)
+        sym = [(a, b) for a, b, _ in us]
+        assert gp[0] == sym and gp[1] == sym
