@@ -263,3 +263,27 @@ def test_general_schedule_in_modes_1_and_2_is_the_symmetric_u_schedule():
         gp = O.gen_stage_pairs("bk", stage, (100, 100, 100), done_g)
         sym = [(a, b) for a, b, _ in us]
         assert gp[0] == sym and gp[1] == sym
+
+
+def test_general_inner_solve_runs_five_start_sweeps():
+    g = synth.rng(25)
+    C = g.standard_normal((9, 8, 7))
+    _, _, _, info = O.gen_inner_solve(C, (2, 2, 2), 1e-14, max_inner=0)
+    assert info["hosvd_won"] and info["sweeps"] == 5
+
+
+def test_hosvd_of_exact_rank_cube():
+    """Equal dimensions in all three modes, a different factor in each: the
+    HOSVD takes each mode's own unfolding."""
+    T, U0, V0, W0, F0 = synth.general_dense_planted(5, 10, 10, 10, (3, 2, 2))
+    Uh, Vh, Wh = O.gen_hosvd(T, (3, 2, 2))
+    for X, Y in ((U0, Uh), (V0, Vh), (W0, Wh)):
+        assert O.sin_theta_max(X, Y) < 1e-12
+
+
+def test_general_hooi_checks_the_gradient_every_ten_iterations():
+    A = _gen(synth.general_random_coo(15, 20, 18, 6, 500))
+    g = synth.rng(13)
+    facs = [synth.orthonormal(g, d, 2) for d in (20, 18, 6)]
+    res = O.gen_hooi(A, *facs, tol=0.0, max_iter=25)
+    assert [h["iter"] for h in res.history] == [0, 10, 20, 25]

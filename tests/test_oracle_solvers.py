@@ -429,3 +429,39 @@ def test_inner_gradient_is_the_global_gradient_of_the_core():
         gi, nfi, _ = B._inner_grad(Uh, Wh, B._c_t1(C, Uh, Wh), B._c_t3(C, Uh))
         gg, nfg, _ = O.gradient_global(_from_dense(C), Uh, Wh)
         assert abs(gi - gg) <= 1e-12 * gg and abs(nfi - nfg) <= 1e-13 * nfg
+
+
+def test_inner_solve_runs_five_start_sweeps():
+    """Section 6.2's 5 HOOI iterations after the HOSVD start, counted: with
+    no continuation allowed (max_inner = 0) the inner solve reports exactly
+    the start sweeps when the HOSVD start wins."""
+    g = synth.rng(85)
+    C = g.standard_normal((12, 12, 8)); C = C + C.transpose(1, 0, 2)
+    _, _, info = O.inner_solve(C, 2, 2, 1e-14, max_inner=0, method="hooi")
+    assert info["hosvd_won"] and info["sweeps"] == 5
+
+
+def test_hooi_checks_the_gradient_every_ten_iterations():
+    """Section 6.1: the gradient is computed every 10 iterations (and at
+    the last one)."""
+    A = _sym_sparse(24, 30, 7, 600)
+    g = synth.rng(5)
+    U = synth.orthonormal(g, A.m, 2); W = synth.orthonormal(g, A.n, 2)
+    res = O.hooi(A, U, W, tol=0.0, max_iter=25)
+    assert [h["iter"] for h in res.history] == [0, 10, 20, 25]
+
+
+def test_hooi_updates_w_from_the_new_u():
+    """The HOOI reading of this library (Gauss-Seidel): after one iteration
+    W spans the leading left singular vectors of unfold_3(A.(U1,U1)) with
+    the new U1, which here differs from the subspace the old U gives."""
+    A = _sym_sparse(25, 30, 9, 800)
+    g = synth.rng(6)
+    U0 = synth.orthonormal(g, A.m, 2); W0 = synth.orthonormal(g, A.n, 2)
+    res = O.hooi(A, U0, W0, tol=0.0, max_iter=1)
+    U1 = O.top_left_singular(O.mode1(A, U0, W0), 2)
+    assert O.sin_theta_max(U1, res.U) < 1e-12
+    W_new = O.top_left_singular(O.mode3(A, U1, U1), 2)
+    W_old = O.top_left_singular(O.mode3(A, U0, U0), 2)
+    assert O.sin_theta_max(W_new, W_old) > 1e-3
+    assert O.sin_theta_max(W_new, res.W) < 1e-12
