@@ -49,6 +49,10 @@ def test_symmetrise_keeps_zeros_and_diagonal():
     assert A.nnz == 3
     assert list(zip(A.i, A.j)) == [(0, 0), (1, 2), (2, 1)]
     assert np.all(A.v == 0.0)
+    # an explicit zero that is not the first key of the list keeps its own entry
+    B = O.symmetrise(2, 1, np.array([0, 1]), np.array([1, 1]), np.array([0, 0]),
+                     np.array([2.0, 0.0]))
+    assert list(zip(B.i, B.j, B.v)) == [(0, 1, 2.0), (1, 0, 2.0), (1, 1, 0.0)]
 
 
 def test_symmetrise_errors():
@@ -62,6 +66,10 @@ def test_symmetrise_errors():
     A = O.symmetrise(3, 2, np.array([0, 1]), np.array([1, 0]), np.array([0, 0]),
                      np.array([2.5, 2.5]), mirror=False, validate=True)
     assert A.nnz == 2
+    # both halves present, values one rounding apart: not (1,2)-symmetric
+    with pytest.raises(ValueError):
+        O.symmetrise(3, 2, np.array([0, 1]), np.array([1, 0]), np.array([0, 0]),
+                     np.array([2.5, np.nextafter(2.5, 3.0)]), mirror=False, validate=True)
 
 
 def test_empty():
