@@ -6,22 +6,30 @@ module.  Every function cites the passage of the paper it follows.
 Pins (what fixes each function other than itself) live in
 ``tests/test_oracle_*.py``:
 
-* ``symmetrise``          -- dict model of the mirror/sum rule, bitwise.
+* ``symmetrise``          -- dict model of the mirror/sum rule, bitwise;
+                             explicit zeros kept; validation refuses values
+                             one rounding apart.
 * ``mode1/mode3/core``    -- brute-force dense ``einsum`` on tiny tensors.
 * ``mode1_rows_from_input`` -- equals the rows of ``mode1`` of the stored
                              tensor (duplicates, diagonal entries, mirrors).
 * ``orth_block``          -- orthonormality, reconstruction B = Q H + Qn R,
-                             exact rank drops on planted dependent columns.
+                             exact rank drops on planted dependent columns;
+                             near dependence the projected block orthogonal
+                             to Q to working precision (two rounds); the
+                             same kept columns at any scale (relative drop).
 * ``schedule_counts``     -- every k1/k3 printed in Tables 1-3 and in the
                              figure captions of Section 6.2 (three printed
-                             values disagree with the rule; see the tests).
+                             values disagree with the rule; see the tests);
+                             the BK block numbering printed in Table 3's
+                             diagrams.
 * ``gradient_prop2``      -- equals ``gradient_global`` (two derivations).
 * ``hosvd_truncated``     -- returns the exact factor subspaces of a core of
                              exact multilinear rank (U,U,W).F0.
 * ``sin_theta_max``       -- sin of a known planted principal angle.
 * ``ng_model``/``ng_step`` -- finite differences of the pulled-back
                              objective; quadratic convergence; the same
-                             optimum as HOOI.
+                             optimum as HOOI; the safeguard refuses a step
+                             that lowers ||F||.
 * ``s_values_gaps``        -- brute force with an explicit orthogonal
                              complement and einsum; S-values of a planted
                              exact-rank tensor are those of F0 with zero
@@ -34,7 +42,13 @@ Pins (what fixes each function other than itself) live in
 * ``inner_solve``/``bks``/``hooi`` -- closed forms n=1 (Eckart-Young) and
                              rank-one slices, exact recovery of a planted
                              multilinear-rank tensor, monotone ||F||, and
-                             BKS/HOOI agreement.
+                             BKS/HOOI agreement; the five start sweeps
+                             counted; the inner and HOOI gradients equal
+                             ``gradient_global``; HOOI's gradient every 10
+                             iterations and W from the new U.
+
+``tests/test_oracle_mutations.py`` plants one plausible mistake at a time
+in a copy of this package and checks that the named pin catches it.
 """
 from __future__ import annotations
 
