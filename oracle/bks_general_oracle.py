@@ -35,7 +35,11 @@ multilinear-rank (r1, r2, r3) tensor with l, m, n all different; on a
 (1,2)-symmetric tensor with V = U the gradient equals the symmetric
 oracle's and the solve reaches the symmetric optimum; Lemma 1 on the
 expansion; Proposition 2 against the global gradient; monotone inner
-sweeps; BKS and HOOI agreement.
+sweeps; BKS and HOOI agreement; the core over several entry blocks; basis
+sizes from the pair and bar rule; modes 1 and 2 in the symmetric
+schedule's order; the inner gradient equal to the global gradient of the
+core; the five start sweeps counted; the HOSVD of a core with equal
+dimensions; HOOI's gradient every 10 iterations.
 """
 from __future__ import annotations
 
